@@ -1,0 +1,426 @@
+"""Benchmark: projection beamforming + NCC localisation of one 300-frame
+paper-scale RCA ensemble per step (128 + 128 elements, 8 transmissions,
+1024 samples, 250 x 128 planes, P = 8), on synthetic seeded channel data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (one
+ensemble per rank; the path has no exchange step), launched by torchrun.
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+method has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "projection frames/s & ms per 300-frame ensemble vs plain FP32; % HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "reduced"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-frames", type=int, default=4)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 8 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 8 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch
+# ---------------------------------------------------------------------------
+def stage1_terms(R, L, t, geom, F):
+    """valid (pixel, element) interpolate-and-accumulate terms of Stage 1 for
+    F frames: for every transmission k and slice row r, lateral distance d up
+    to the aperture limit with the delay inside the record, times the number
+    of (pixel, element) pairs at that distance (N for d = 0, 2 (N - d) else)."""
+    import numpy as np
+    txq = R.rca_tables_download(t, L.RCA_TAB_TX_Q16).astype(np.int64)     # [2K][nzs]
+    rxq = R.rca_tables_download(t, L.RCA_TAB_RX_Q16).astype(np.int64)     # [nzs][N]
+    dmax = R.rca_tables_download(t, L.RCA_TAB_DMAX)
+    N = geom.n_el
+    d = np.arange(N)
+    pairs = np.where(d == 0, N, 2 * (N - d))
+    qmax = (geom.ns - 1) << 16
+    total = 0
+    for k in range(txq.shape[0]):
+        q = txq[k][:, None] + rxq                                          # [nzs][N]
+        ok = (q >= 0) & (q <= qmax) & (d[None, :] <= dmax[:, None])
+        total += int((ok * pairs[None, :]).sum())
+    return total * F
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_init(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2511_21647_gb300 import _lib as L
+    from paper_2511_21647_gb300 import rca as R
+    from paper_2511_21647_gb300.pipeline import RcaSession, complex_buffer
+    from synth import generate, quantize_int16, workload
+
+    w = workload(args.workload, seed=workload(args.workload).seed + rank)
+    g = w.geom
+    F = w.n_frames
+    t_gen = time.time()
+    G = generate(w, device=str(dev), dtype=torch.float32, with_noise=True)
+    rf = G.rf.contiguous()
+    gen_s = time.time() - t_gen
+    reduced = args.precision == "reduced"
+    if reduced:
+        rf_dev, scale = quantize_int16(rf)
+        rf_dev = rf_dev.contiguous()
+        scale = scale.contiguous()
+        rf_t, iq_t, pl_t = L.RCA_I16, L.RCA_C16F, L.RCA_C16BF
+    else:
+        rf_dev, scale = rf, None
+        rf_t, iq_t, pl_t = L.RCA_F32, L.RCA_C32, L.RCA_C32
+
+    sess = RcaSession(g, device=local)
+    stream = torch.cuda.current_stream(dev)
+    R.rca_reserve(sess.h, sess.g, F)
+    nt = 2 * g.K
+    iq = complex_buffer((F, nt, g.ns, g.n_el), iq_t, dev)
+    slices = complex_buffer((F, nt, g.nzs, g.n_el), L.RCA_C32, dev)
+    planes = complex_buffer(sess.planes_shape(F), pl_t, dev)
+    A = torch.empty(sess.a_shape(F), dtype=torch.float32, device=dev)
+    M = torch.empty(F, dtype=torch.float32, device=dev)
+    cap2d, cap3d = 1 << 21, 1 << 19
+    out2d, n2d, out3d, n3d = sess.loc_buffers(cap2d, cap3d)
+    prm = R.make_ulm_params(d=w.ncc_d, sig_z=0.81, sig_lat=1.45, alpha=0.1, ncc_min=0.5)
+    h, t = sess.h, sess.t
+
+    stages = ["ingest", "stage1", "stage2", "enhance", "detect2d", "pair3d"]
+    launches = {"ingest": 2, "stage1": 1, "stage2": 1, "enhance": 1, "detect2d": 3, "pair3d": 5}
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        R.rca_ingest(h, t, rf_dev, rf_t, scale, F, L.RCA_CLUTTER_MEAN, iq, iq_t)
+        mark(1)
+        R.rca_stage1(h, t, iq, iq_t, F, slices)
+        mark(2)
+        R.rca_stage2_project(h, t, slices, F, planes, pl_t)
+        mark(3)
+        R.ulm_enhance(h, t, planes, pl_t, F, L.ULM_ENH_XDOPPLER, A, M)
+        mark(4)
+        R.ulm_detect2d(h, t, A, M, F, prm, out2d, cap2d, n2d)
+        mark(5)
+        R.ulm_pair3d(h, t, out2d, n2d, cap2d, F, out3d, cap3d, n3d)
+        mark(6)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    dev_status = R.rca_sync_status(h)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            step(evs[k])
+        torch.cuda.synchronize()
+    barrier(world)
+    per_stage = {s: [] for s in stages}
+    totals = []
+    for k in range(K):
+        for i, s in enumerate(stages):
+            per_stage[s].append(evs[k][i].elapsed_time(evs[k][i + 1]))
+        totals.append(evs[k][0].elapsed_time(evs[k][6]))
+    ms_total = sum(totals)
+    ms_max = max_over_ranks(ms_total, world)
+    ms_step = ms_max / K
+    value = world * F * K / (ms_max / 1e3)
+    stage_ms = {s: sum(v) / K for s, v in per_stage.items()}
+    n2d_v, n3d_v = int(n2d.item()), int(n3d.item())
+
+    # -- roofline of the dominant kernel -----------------------------------
+    import json as _json
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    esz_rf = 2 if reduced else 4
+    esz_iq = 4 if reduced else 8
+    esz_pl = 4 if reduced else 8
+    n_rf = F * nt * g.n_el * g.ns
+    n_sl = F * nt * g.nzs * g.n_el
+    n_pl = F * 4 * g.n_slab * g.nz * g.n_el
+    n_a = F * 2 * g.n_slab * g.nz * g.n_el
+    bytes_alg = {
+        "ingest": 2 * n_rf * esz_rf + n_rf * esz_iq,
+        "stage1": n_rf * esz_iq + n_sl * 8,
+        "stage2": n_sl * 8 + n_pl * esz_pl,
+        "enhance": n_pl * esz_pl + n_a * 4,
+        "detect2d": n_a * 4 + n2d_v * 40,
+        "pair3d": n2d_v * 40 + n3d_v * 40,
+    }
+    terms = stage1_terms(R, L, t, g, F)
+    flops_stage1 = 14.0 * terms
+    dominant = max(stage_ms, key=stage_ms.get)
+    if dominant == "stage1":
+        ach = flops_stage1 / (stage_ms["stage1"] / 1e3) / 1e12
+        roof = {"kernel": "k_stage1", "bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak_tflops, 1),
+                "unit": "TFLOP/s", "frac": round(ach / fp32_peak_tflops, 4), "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
+    else:
+        ach = bytes_alg[dominant] / (stage_ms[dominant] / 1e3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    stage_roof = {}
+    for s in stages:
+        gbs = bytes_alg[s] / (stage_ms[s] / 1e3) / 1e9
+        stage_roof[s] = {"ms": round(stage_ms[s], 4), "alg_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
+    stage_roof["stage1"]["alg_TFLOPs"] = round(flops_stage1 / (stage_ms["stage1"] / 1e3) / 1e12, 2)
+    stage_roof["stage1"]["fp32_frac"] = round(flops_stage1 / (stage_ms["stage1"] / 1e3) / 1e12 / fp32_peak_tflops, 4)
+    stage_roof["stage1"]["terms"] = terms
+
+    # -- end to end through the public calls, host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        rf_host = rf_dev.cpu().pin_memory()
+        scale_host = scale.cpu().pin_memory() if scale is not None else None
+        rf_stage = torch.empty_like(rf_dev)
+        sc_stage = torch.empty_like(scale) if scale is not None else None
+        out_host = torch.empty((cap3d, 10), dtype=torch.int32).pin_memory()
+        cnt_host = torch.empty(2, dtype=torch.int32).pin_memory()
+        cnt_dev = torch.empty(2, dtype=torch.int32, device=dev)
+
+        def e2e_step():
+            rf_stage.copy_(rf_host, non_blocking=True)
+            if sc_stage is not None:
+                sc_stage.copy_(scale_host, non_blocking=True)
+            R.rca_beamform_projections(h, t, rf_stage, rf_t, sc_stage, F, R.bf_params(iq_dtype=iq_t), planes, pl_t)
+            R.ulm_localize(h, t, planes, pl_t, F, prm, out2d, cap2d, n2d, out3d, cap3d, n3d)
+            cnt_dev[0:1].copy_(n2d)
+            cnt_dev[1:2].copy_(n3d)
+            cnt_host.copy_(cnt_dev, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+            m = min(int(cnt_host[1]), cap3d)
+            if m:
+                out_host[:m].copy_(out3d[:m], non_blocking=True)
+            return m
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d2h = 0
+        for _ in range(K):
+            d2h += e2e_step() * 40 + 8
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e = {"value": round(world * F * K / (e_ms / 1e3), 1), "unit": "frames/s",
+               "ms_per_ensemble": round(e_ms / K, 3),
+               "h2d_bytes_per_step": int(rf_dev.numel() * rf_dev.element_size() + (scale.numel() * 4 if scale is not None else 0)),
+               "d2h_bytes_per_step": int(d2h // K)}
+
+    status_after = R.rca_sync_status(h)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": round(value, 1),
+            "unit": "frames/s",
+            "n_gpus": world,
+            "steps": K,
+            "warmup": max(3, args.warmup),
+            "ms_per_step": round(ms_step, 4),
+            "ms_per_ensemble": round(ms_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "i16/f16/bf16+f32acc" if reduced else "f32",
+            "data": "synthetic (seeded point scatterers; paper's in-vivo / Field II data unavailable)",
+            "config": {"workload": f"{w.name}: RCA {g.n_el}+{g.n_el} el, {nt} tx, {F} frames, {g.ns} samples, "
+                                   f"planes {g.nz}x{g.n_el}, P={g.P}, NCC d={w.ncc_d}",
+                       "frames": F, "n_el": g.n_el, "n_tx": nt, "ns": g.ns, "nz": g.nz, "us": g.us,
+                       "precision": args.precision,
+                       "l2": "inputs larger than L2 (RF %.2f GB, planes %.2f GB)" % (
+                           rf_dev.numel() * rf_dev.element_size() / 1e9, planes.numel() * planes.element_size() / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "stages": stage_roof,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": K * sum(launches.values()),
+            "clocks": clk.summary(),
+            "localisations": {"n2d": n2d_v, "n3d": n3d_v},
+            "device_status": [dev_status, status_after],
+            "generate_s": round(gen_s, 1),
+        }
+        print(json.dumps(line), flush=True)
+    sess.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, rf_tensor, n_frames):
+    """The FP64 oracle as it stands on the host cores: ensemble mean over all
+    frames, then demodulation, Stage 1, Stage 2 + projection for a sample of
+    frames, XDoppler + NCC + peaks + pairing for those frames."""
+    import numpy as np
+    import oracle as O
+    rf = rf_tensor.cpu().numpy()
+    g = w.geom
+    frames = list(range(1, 1 + n_frames))
+    t0 = time.time()
+    planes = O.beamform_projections(g, rf, frames=[0] + frames + [1 + n_frames])
+    O.localize(planes, w.ncc_d, 0.81, 1.45, 0.1, 0.5, g.P)
+    dt = time.time() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    nf = len(frames) + 2
+    return {"value": round(nf / dt, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nf} of {w.n_frames} frames of the same ensemble (mean over all {w.n_frames}), {dt:.1f} s"}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle timed on this host (the method has no other
+    reference implementation); rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    from synth import generate, workload
+    w = workload(args.workload)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    G = generate(w, device=dev, dtype=torch.float32 if dev == "cuda" else torch.float64)
+    nfr = max(1, args.cpu_sample_frames // 2)
+    times = []
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline(w, G.rf, nfr)
+    res = None
+    for _ in range(max(1, min(args.steps, 3))):
+        res = cpu_baseline(w, G.rf, nfr)
+        times.append(res["value"])
+    value = statistics.median(times)
+    F = w.n_frames
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": round(F / value * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "frames": F},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

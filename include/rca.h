@@ -1,0 +1,306 @@
+/*
+ * rca.h -- C ABI of librca: projection-based row-column-array (RCA) 3D
+ * ultrasound localization microscopy on one GPU (sm_103a).
+ *
+ * Method (arXiv 2511.21647):
+ *   Sec. II-A1  two-stage RCA beamforming: Stage 1 beamforms one reference
+ *               slice per steered RC / CR transmission from channel data;
+ *               Stage 2 extrapolates it along the transmit direction by a
+ *               rigid axial shift and compounds (Fig. 1b-c).
+ *   Sec. II-A4  the volume is cut into P x P x N sub-blocks and sum-projected
+ *               onto x-z and y-z planes (Sec. II-A5 counts 2N/P planes); the
+ *               RC and CR stacks are combined by XDoppler (3-frame window);
+ *               each plane is normalised-cross-correlated with a Gaussian PSF
+ *               using separable 1D correlations (Fig. 1g); sub-pixel regional
+ *               peaks are paired across the XZ and YZ planes into 3D by an
+ *               axial tolerance of one pixel and an intensity ratio in
+ *               [0.9, 1.11] with mutual minimum ratio.
+ *   Sec. II-C   acquisition constants (pitch 0.214 mm, 128 + 128 elements,
+ *               400 Hz, P = 8, 11-tap 1D kernels).
+ * The library never materialises the N x N x nz volume.
+ *
+ * Conventions for every entry point
+ *   Ownership   the caller owns all data buffers (channel data, scales,
+ *               planes, lists, counts): plain device pointers, 256-byte
+ *               alignment recommended, 16 bytes required.  The library owns
+ *               handles, geometries, tables, CNNs and its internal workspace
+ *               and frees them in the matching *_destroy call.
+ *   Execution   all GPU work is enqueued on the handle's stream (the legacy
+ *               default stream until rca_set_stream) and returns without
+ *               synchronising, except where a function says it synchronises.
+ *   Errors      argument, shape and dtype errors are detected on the host
+ *               before anything is enqueued: the call returns a non-zero
+ *               rca_status and rca_last_error() describes it.  Conditions
+ *               only the GPU can see (output capacity overflow, a bounded
+ *               wait that ran out, a checked-build bounds violation) set bits
+ *               of a device status word that rca_sync_status() reads and
+ *               clears; no kernel traps or asserts.
+ *   Threads     one handle per host thread.
+ *
+ * Array layouts (row-major; complex = interleaved re, im):
+ *   rf      [F][2K][E][ns]           F frames, 2K transmissions (RC first),
+ *                                    E = n_el receive elements, ns samples
+ *   iq      [F][2K][E][ns] complex   baseband IQ after clutter removal
+ *   slices  [F][2K][nzs][N] complex  Stage-1 reference slices, N = n_el
+ *                                    lateral pixels, nzs = (nz-1)*us + 1
+ *   planes  [F][2][2][S][nz][N] complex   [axis][family][slab]:
+ *                                    axis 0 = XZ (slab over y, lateral x),
+ *                                    axis 1 = YZ (slab over x, lateral y),
+ *                                    family 0 = RC, 1 = CR, S = N / P
+ *   A       [F][2][S][nz][N] float   XDoppler amplitude
+ */
+#ifndef RCA_H
+#define RCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RCA_VERSION_MAJOR 0
+#define RCA_VERSION_MINOR 1
+#define RCA_MAX_K 8            /* transmissions per family */
+
+typedef enum {
+    RCA_OK = 0,
+    RCA_ERR_INVALID_ARG = 1,  /* null pointer, bad enum, value out of range */
+    RCA_ERR_SHAPE = 2,        /* sizes inconsistent with the geometry */
+    RCA_ERR_UNSUPPORTED = 3,  /* valid but not implemented (dtype combination, K > 8) */
+    RCA_ERR_CUDA = 4,         /* a CUDA runtime call failed; see rca_last_error */
+    RCA_ERR_CAPACITY = 5,     /* (device) an output list overflowed its capacity */
+    RCA_ERR_TIMEOUT = 6,      /* (device) a bounded wait gave up */
+    RCA_ERR_BOUNDS = 7        /* (device, checked builds) an index left its buffer */
+} rca_status;
+
+typedef enum {
+    RCA_F32 = 0,    /* float */
+    RCA_I16 = 1,    /* int16 with a per-channel float scale */
+    RCA_F16 = 2,    /* IEEE half */
+    RCA_C32 = 3,    /* complex float (8 bytes) */
+    RCA_C16F = 4,   /* complex half (4 bytes) */
+    RCA_C16BF = 5   /* complex bfloat16 (4 bytes) */
+} rca_dtype;
+
+typedef struct rca_handle rca_handle;
+typedef struct rca_geometry rca_geometry;
+typedef struct rca_tables rca_tables;
+
+/* ---------------------------------------------------------------------- */
+/* Handle, stream, status                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Library version as (major << 16) | minor. */
+int rca_version(void);
+
+/* Static text for a status code; never NULL. */
+const char* rca_status_string(rca_status s);
+
+/* Create a handle bound to CUDA device `device` (made current for the call).
+ * Allocates the device status word.  Errors: INVALID_ARG (h NULL), CUDA. */
+rca_status rca_create(rca_handle** h, int device);
+
+/* Free the handle and its workspace (synchronises its stream first). */
+rca_status rca_destroy(rca_handle* h);
+
+/* Use a caller-owned cudaStream_t (passed as void*) for all later work;
+ * NULL selects the legacy default stream.  The library never destroys it. */
+rca_status rca_set_stream(rca_handle* h, void* cuda_stream);
+
+/* Host-side text of the last error on this handle ("" if none). */
+const char* rca_last_error(const rca_handle* h);
+
+/* Synchronise the handle's stream, then read and clear the device status
+ * word.  *device_status receives RCA_OK or the first device-side error
+ * (CAPACITY, TIMEOUT, BOUNDS).  Returns CUDA if the stream reported a fault. */
+rca_status rca_sync_status(rca_handle* h, rca_status* device_status);
+
+/* Reserve workspace for ensembles of up to n_frames frames of `g` so that no
+ * allocation happens later (needed before CUDA graph capture). Synchronises. */
+rca_status rca_reserve(rca_handle* h, const rca_geometry* g, int n_frames);
+
+/* ---------------------------------------------------------------------- */
+/* Geometry and delay tables (Sec. II-A1, Sec. II-C)                       */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int n_el;          /* elements per array (rows = columns); N lateral pixels */
+    int nz;            /* axial pixels of the projection planes */
+    int ns;            /* RF samples per channel */
+    int P;             /* sub-block / slab size in pixels (paper: 8); n_el % P == 0 */
+    int K;             /* transmissions per family: K RC then K CR (1..8) */
+    int us;            /* Stage-1 axial oversampling (slice rows per plane pixel, 1..8) */
+    double pitch_m;    /* element pitch = lateral pixel size */
+    double fc_hz;      /* demodulation / carrier frequency */
+    double fs_hz;      /* RF sampling rate */
+    double c_mps;      /* speed of sound */
+    double z0_m;       /* depth of plane row 0; first RF sample at t0 = 2 z0 / c */
+    double dz_m;       /* axial pixel size of the planes */
+    double fnum;       /* receive F-number (Hann apodisation over z / fnum) */
+    const double* ang_rc_rad;  /* K steering angles of the RC transmissions */
+    const double* ang_cr_rad;  /* K steering angles of the CR transmissions */
+} rca_geometry_desc;
+
+/* Copy and validate a geometry (host only; nothing is enqueued).
+ * Model: element / pixel centres u_e = (e - (N-1)/2) pitch; RC transmission
+ * k delays (z cos th + y sin th + (L/2)|sin th|)/c and receives on columns
+ * with sqrt((x-u_e)^2 + z^2)/c (CR swaps x and y), L = N pitch.
+ * Errors: INVALID_ARG (non-positive sizes, n_el % P != 0), UNSUPPORTED (K > 8). */
+rca_status rca_geometry_create(rca_handle* h, const rca_geometry_desc* desc, rca_geometry** out);
+rca_status rca_geometry_destroy(rca_geometry* g);
+
+/* Build the per-geometry tables on the GPU in FP64 (sub-nanosecond delays)
+ * and store them as Q16 fixed-point sample delays and FP32 complex weights:
+ * transmit and receive delays, Hann x carrier weights, aperture limits,
+ * Stage-2 axial shifts and carrier terms, and the Stage-2 slab-sum
+ * coefficients.  Synchronises once (to size the Stage-1 sample windows). */
+rca_status rca_delay_tables(rca_handle* h, const rca_geometry* g, rca_tables** out);
+rca_status rca_tables_destroy(rca_tables* t);
+
+/* Table identifiers for rca_tables_query / rca_tables_download. */
+typedef enum {
+    RCA_TAB_TX_F64 = 0,   /* double [2K][nzs]: (tau_tx(k, 0, z_r) - t0) fs, samples */
+    RCA_TAB_RX_F64 = 1,   /* double [N][nzs] : tau_rx(d pitch, z_r) fs, d = |lateral - element| */
+    RCA_TAB_TX_Q16 = 2,   /* int32  [2K][nzs]: rint(TX_F64 * 65536) */
+    RCA_TAB_RX_Q16 = 3,   /* int32  [nzs][N] : rint(RX_F64 * 65536), row-major by r */
+    RCA_TAB_W = 4,        /* float2 [nzs][N] : hann(d pitch, z_r) exp(j 2 pi fc (tau_rx - z_r / c)) */
+    RCA_TAB_DMAX = 5,     /* int32  [nzs]    : largest d inside the F-number aperture */
+    RCA_TAB_S2_SHIFT = 6, /* double [2K][N]  : Stage-2 shift in slice rows, dz_k(u) us / dz */
+    RCA_TAB_S2_PSI = 7,   /* float2 [2K][N]  : exp(j 2 pi fc (1 + cos th) dz_k(u) / c) */
+    RCA_TAB_S2_EC = 8,    /* float2 [2K][nz] : exp(j 2 pi fc tau_c,k(z_i)) */
+    RCA_TAB_S2_COEF = 9,  /* float2 [2K][S][nz][T]: transverse-slab sum coefficients */
+    RCA_TAB_S2_TMIN = 10, /* int32  [2K][S]  : first slice-row offset of the coefficients */
+    RCA_TAB_COUNT = 11
+} rca_table_id;
+
+/* Size in bytes and up to 4 dimensions (unused = 0) of one table. */
+rca_status rca_tables_query(const rca_tables* t, int table_id, size_t* bytes, int dims[4]);
+/* Copy one table to host memory (synchronises).  SHAPE if bytes is too small. */
+rca_status rca_tables_download(const rca_tables* t, int table_id, void* host_dst, size_t bytes);
+
+/* ---------------------------------------------------------------------- */
+/* Beamforming into projection planes (Sec. II-A1, II-A4, II-A5)           */
+/* ---------------------------------------------------------------------- */
+
+typedef enum { RCA_MODE_TWO_STAGE = 0, RCA_MODE_DIRECT = 1 } rca_bf_mode;
+typedef enum { RCA_CLUTTER_NONE = 0, RCA_CLUTTER_MEAN = 1 } rca_clutter;
+
+typedef struct {
+    int mode;      /* rca_bf_mode: TWO_STAGE (the method) or DIRECT (exact slab
+                      sums of conventional 3D DAS, no volume; validation and
+                      the "what it replaces" baseline) */
+    int clutter;   /* rca_clutter: MEAN removes each channel sample's mean over
+                      the ensemble's frames before demodulation */
+    int iq_dtype;  /* internal IQ storage: RCA_C32, RCA_C16F or RCA_C16BF */
+    int reserved[5];
+} rca_bf_params;
+
+/* Channel data -> IQ: optional mean clutter removal over the F frames, then
+ * demodulation b[n] = 2 sum_m h[m] r~[n-m] exp(-j 2 pi fc t_{n-m}) with a
+ * 31-tap half-band Hamming low-pass h (cut-off fs/4).
+ *   rf: [F][2K][E][ns] RCA_F32, RCA_F16 or RCA_I16 (then scale[2K][E] float,
+ *       value = q * scale); iq: [F][2K][E][ns] RCA_C32 / C16F / C16BF. */
+rca_status rca_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca_dtype rf_dtype,
+                      const float* scale, int n_frames, int clutter, void* iq, rca_dtype iq_dtype);
+
+/* Stage 1 (Sec. II-A1): one baseband reference slice per transmission,
+ *   S_k(l, r) = sum_e w * IQ_{k,e}(tau0) * exp(j 2 pi fc (tau0 - tau_c,k(z_r))),
+ *   tau0 = tau_tx(k, 0, z_r) + tau_rx(u_l - u_e, z_r), IQ linear in time and
+ *   zero outside the record.  slices: [F][2K][nzs][N] RCA_C32. */
+rca_status rca_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_dtype,
+                      int n_frames, void* slices);
+
+/* Stage 2 + block sum-projection (Sec. II-A1, II-A4): each slice is shifted
+ * axially by dz_k(u) = u sin th / (1 + cos th), the carrier exp(j 2 pi fc
+ * tau_c,k(z')) re-applied, the K transmissions of a family summed and the
+ * result sum-projected over P-pixel slabs, written straight to the planes.
+ * slices: [F][2K][nzs][N] RCA_C32; planes: RCA_C32, RCA_C16F or RCA_C16BF. */
+rca_status rca_stage2_project(rca_handle* h, const rca_tables* t, const void* slices, int n_frames,
+                              void* planes, rca_dtype planes_dtype);
+
+/* Exact projection of conventional 3D DAS: every plane pixel sums the DAS
+ * voxels of its slab, computed from IQ with no volume (Sec. II-A1's
+ * "conventional" path).  iq as for rca_stage1; planes as for stage 2. */
+rca_status rca_direct_project(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_dtype,
+                              int n_frames, void* planes, rca_dtype planes_dtype);
+
+/* The whole beamforming path: ingest -> Stage 1 -> Stage 2 + projection (or
+ * ingest -> direct) using library workspace for IQ and slices.
+ *   rf: [F][2K][E][ns] (F32, F16, or I16 + scale[2K][E]); planes as above.
+ * Errors: INVALID_ARG / SHAPE / UNSUPPORTED on the host. */
+rca_status rca_beamform_projections(rca_handle* h, const rca_tables* t, const void* rf,
+                                    rca_dtype rf_dtype, const float* scale, int n_frames,
+                                    const rca_bf_params* prm, void* planes, rca_dtype planes_dtype);
+
+/* ---------------------------------------------------------------------- */
+/* Localisation (Sec. II-A4, Fig. 1e, Fig. 1g)                             */
+/* ---------------------------------------------------------------------- */
+
+typedef enum { ULM_ENH_XDOPPLER = 0, ULM_ENH_COHERENT = 1 } ulm_enhance_mode;
+
+typedef struct {
+    int d;            /* NCC kernel length (odd, 3..15; paper 11) */
+    float sig_z;      /* Gaussian PSF sigma along z, pixels */
+    float sig_lat;    /* Gaussian PSF sigma along the lateral axis, pixels */
+    float alpha;      /* amplitude threshold as a fraction of the frame maximum */
+    float ncc_min;    /* NCC threshold */
+    int enh;          /* ulm_enhance_mode */
+    int reserved[4];
+} ulm_params;
+
+/* One 2D localisation.  Lists are ordered by (frame, axis, slab, iz, ilat). */
+typedef struct {
+    int32_t frame, axis, slab;  /* plane */
+    int32_t iz, ilat;           /* integer peak pixel */
+    float z, lat;               /* sub-pixel position (pixels) */
+    float ncc, amp;             /* NCC value and amplitude A at the peak pixel */
+    int32_t reserved;
+} ulm_loc2d;                    /* 40 bytes */
+
+/* One paired 3D localisation; ordered by i_xz. */
+typedef struct {
+    int32_t frame, i_xz, i_yz;  /* indices into the 2D list */
+    int32_t reserved;
+    float x, y, z;              /* x from the XZ entry, y from YZ, z the mean (pixels) */
+    float amp_xz, amp_yz;
+    float reserved2;
+} ulm_loc3d;                    /* 40 bytes */
+
+/* XDoppler enhancement: A_t = sqrt(| sum_{t' = t-1}^{t+1} P_RC,t' conj(P_CR,t') |)
+ * over a centred 3-frame window clipped at the ensemble ends (or the
+ * coherent |P_RC + P_CR|), and the per-frame maximum M_t of A.
+ * planes: [F][2][2][S][nz][N] (C32 / C16F / C16BF); A: [F][2][S][nz][N]
+ * float; M: [F] float.  Geometry sizes come from t. */
+rca_status ulm_enhance(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype planes_dtype,
+                       int n_frames, int enh, float* A, float* M);
+
+/* NCC against the d x d Gaussian PSF via separable 1D correlations, then
+ * sub-pixel 3x3 regional peaks with NCC >= ncc_min and A >= alpha M_t (ties
+ * to the earlier raster pixel), parabolic sub-pixel refinement.
+ *   out: capacity cap2d; *n2d_dev (device int) receives the true count even
+ *   when it exceeds cap2d (then the status word gets CAPACITY).
+ *   ncc_out: optional [F][2][S][nz][N] float copy of the NCC maps (NULL = none).
+ *   plane_offsets: optional device int [F*2*S + 1] list offset of each plane. */
+rca_status ulm_detect2d(rca_handle* h, const rca_tables* t, const float* A, const float* M,
+                        int n_frames, const ulm_params* prm, ulm_loc2d* out2d, int cap2d,
+                        int* n2d_dev, float* ncc_out, int* plane_offsets);
+
+/* Pair XZ and YZ localisations into 3D (sub-block membership by integer
+ * pixel, |z_xz - z_yz| <= 1 pixel, I_xz / I_yz in [0.9, 1.11], mutual minimum
+ * of max(I)/min(I), ties to the lower index; decisions in double precision).
+ *   list2d: sorted as ulm_detect2d writes it; n2d_dev: device count (entries
+ *   beyond cap2d are ignored).  out3d: capacity cap3d; *n3d_dev true count. */
+rca_status ulm_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* list2d, const int* n2d_dev,
+                      int cap2d, int n_frames, ulm_loc3d* out3d, int cap3d, int* n3d_dev);
+
+/* The whole localisation path: ulm_enhance -> ulm_detect2d -> ulm_pair3d with
+ * library workspace for A and M. */
+rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype planes_dtype,
+                        int n_frames, const ulm_params* prm, ulm_loc2d* out2d, int cap2d, int* n2d_dev,
+                        ulm_loc3d* out3d, int cap3d, int* n3d_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCA_H */

@@ -81,7 +81,7 @@ def lib():
                 "or_tau_c": (_D, [_P, _I, _D]),
                 "or_shift_dz": (_D, [_P, _I, _D]),
                 "or_fir_taps": (None, [_P]),
-                "or_demod": (None, [_P, _I, _P, _I, _P]),
+                "or_demod": (None, [_P, _I, _P, _I, _I, _P, _P]),
                 "or_das_volume": (None, [_P, _P, _I, _P]),
                 "or_project_volume": (None, [_P, _P, _I, _P]),
                 "or_project_direct": (None, [_P, _P, _I, _P]),
@@ -169,13 +169,19 @@ def fir_taps() -> np.ndarray:
 
 # --- beamforming --------------------------------------------------------------
 
-def demod(g, rf, remove_mean: bool = True) -> np.ndarray:
-    """rf [F][2K][E][ns] (any real dtype) -> IQ complex128, same shape."""
-    rf = np.ascontiguousarray(rf, dtype=np.float64)
+def demod(g, rf, remove_mean: bool = True, frames=None) -> np.ndarray:
+    """rf [F][2K][E][ns] float32 -> IQ complex128 [F'][2K][E][ns] for the listed
+    frames (all by default); the mean is taken over all F frames."""
+    rf = np.ascontiguousarray(rf, dtype=np.float32)
     F = rf.shape[0]
     assert rf.shape == (F, g.n_tx, g.n_el, g.ns), rf.shape
-    iq = np.zeros(rf.shape, dtype=np.complex128)
-    lib().or_demod(_byref(geom(g)), F, _ptr(rf), int(remove_mean), _ptr(iq))
+    if frames is None:
+        iq = np.zeros(rf.shape, dtype=np.complex128)
+        lib().or_demod(_byref(geom(g)), F, _ptr(rf), int(remove_mean), F, None, _ptr(iq))
+    else:
+        sel = np.ascontiguousarray(list(frames), dtype=np.int32)
+        iq = np.zeros((len(sel),) + rf.shape[1:], dtype=np.complex128)
+        lib().or_demod(_byref(geom(g)), F, _ptr(rf), int(remove_mean), len(sel), _ptr(sel), _ptr(iq))
     return iq
 
 
@@ -231,22 +237,22 @@ def beamform_projections(g, rf, mode: str = "two_stage", remove_mean: bool = Tru
                          frames=None, return_slices: bool = False):
     """RF -> projection planes [F'][2][2][S][nz][N] (complex128) for the listed
     frames (all by default).  The mean is always taken over every frame of rf."""
-    iq = demod(g, rf, remove_mean)
-    frames = range(iq.shape[0]) if frames is None else list(frames)
+    frames = range(rf.shape[0]) if frames is None else list(frames)
+    iq = demod(g, rf, remove_mean, frames)
     planes = np.zeros((len(frames), 2, 2, g.n_slab, g.nz, g.n_el), dtype=np.complex128)
     slices = np.zeros((len(frames), g.n_tx, g.nzs, g.n_el), dtype=np.complex128) if return_slices else None
-    for q, f in enumerate(frames):
+    for q in range(len(frames)):
         if mode == "two_stage":
-            S = stage1(g, iq[f])
+            S = stage1(g, iq[q])
             if slices is not None:
                 slices[q] = S
             planes[q] = stage2_project(g, S)
         elif mode == "direct":
-            project_direct(g, iq[f], 0, planes[q])
-            project_direct(g, iq[f], 1, planes[q])
+            project_direct(g, iq[q], 0, planes[q])
+            project_direct(g, iq[q], 1, planes[q])
         elif mode == "volume":
             for fam in (0, 1):
-                project_volume(g, das_volume(g, iq[f], fam), fam, planes[q])
+                project_volume(g, das_volume(g, iq[q], fam), fam, planes[q])
         else:
             raise ValueError(mode)
     return (planes, slices) if return_slices else planes

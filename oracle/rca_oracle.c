@@ -112,7 +112,8 @@ void or_fir_taps(double h[OR_FIR_TAPS])
  * tissue), then
  *   b[n] = 2 sum_m h[m] r~[n-m] exp(-j 2 pi fc t_{n-m}),  t_n = t0 + n / fs,
  * with samples outside [0, ns) taken as zero. */
-void or_demod(const or_geom* g, int F, const double* rf, int remove_mean, double* iq)
+void or_demod(const or_geom* g, int F, const float* rf, int remove_mean, int n_sel, const int* sel,
+              double* iq)
 {
     const int nt = 2 * g->K, E = g->n_el, ns = g->ns;
     const int half = (OR_FIR_TAPS - 1) / 2;
@@ -122,19 +123,22 @@ void or_demod(const or_geom* g, int F, const double* rf, int remove_mean, double
     double* mean = (double*)calloc((size_t)nt * E * ns, sizeof(double));
     if (remove_mean) {
         for (int f = 0; f < F; ++f)
-            for (size_t q = 0; q < (size_t)nt * E * ns; ++q) mean[q] += rf[(size_t)f * nt * E * ns + q];
+            for (size_t q = 0; q < (size_t)nt * E * ns; ++q) mean[q] += (double)rf[(size_t)f * nt * E * ns + q];
         for (size_t q = 0; q < (size_t)nt * E * ns; ++q) mean[q] /= (double)F;
     }
+    if (!sel) n_sel = F;
 #pragma omp parallel for collapse(3) schedule(static)
-    for (int f = 0; f < F; ++f)
+    for (int q = 0; q < n_sel; ++q)
         for (int k = 0; k < nt; ++k)
             for (int e = 0; e < E; ++e) {
+                int f = sel ? sel[q] : q;
                 double* mre = (double*)malloc(sizeof(double) * ns);
                 double* mim = (double*)malloc(sizeof(double) * ns);
+                size_t ich = (((size_t)q * nt + k) * E + e) * ns;
                 size_t ch = (((size_t)f * nt + k) * E + e) * ns;
                 size_t mch = ((size_t)k * E + e) * ns;
                 for (int n = 0; n < ns; ++n) {
-                    double r = rf[ch + n] - mean[mch + n];
+                    double r = (double)rf[ch + n] - mean[mch + n];
                     double ph = -TWO_PI * g->fc * (t0 + (double)n / g->fs);
                     mre[n] = r * cos(ph);
                     mim[n] = r * sin(ph);
@@ -147,8 +151,8 @@ void or_demod(const or_geom* g, int F, const double* rf, int remove_mean, double
                         re += h[m + half] * mre[s];
                         im += h[m + half] * mim[s];
                     }
-                    iq[2 * (ch + n)] = 2.0 * re;
-                    iq[2 * (ch + n) + 1] = 2.0 * im;
+                    iq[2 * (ich + n)] = 2.0 * re;
+                    iq[2 * (ich + n) + 1] = 2.0 * im;
                 }
                 free(mre);
                 free(mim);

@@ -70,9 +70,12 @@ double or_apod(const or_geom* g, double lat_off, double z);
 double or_tau_c(const or_geom* g, int k, double z);
 double or_shift_dz(const or_geom* g, int k, double u);
 
-/* RF -> IQ (mean clutter removal + demodulation) */
+/* RF -> IQ (mean clutter removal + demodulation).  The mean always runs over
+ * all F frames; IQ is produced for the n_sel frames listed in sel (all F
+ * frames, in order, when sel is NULL), iq [n_sel][2K][E][ns][2]. */
 void or_fir_taps(double h[OR_FIR_TAPS]);
-void or_demod(const or_geom* g, int F, const double* rf, int remove_mean, double* iq);
+void or_demod(const or_geom* g, int F, const float* rf, int remove_mean, int n_sel, const int* sel,
+              double* iq);
 
 /* conventional full 3D DAS of one family, one frame */
 void or_das_volume(const or_geom* g, const double* iq_frame, int fam, double* V);

@@ -1,0 +1,110 @@
+"""ctypes declarations of librca (include/rca.h).  Loading fails loudly if the
+library has not been built: there is no fallback implementation."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librca.so")
+
+RCA_MAX_K = 8
+
+# rca_status
+RCA_OK = 0
+RCA_ERR_INVALID_ARG = 1
+RCA_ERR_SHAPE = 2
+RCA_ERR_UNSUPPORTED = 3
+RCA_ERR_CUDA = 4
+RCA_ERR_CAPACITY = 5
+RCA_ERR_TIMEOUT = 6
+RCA_ERR_BOUNDS = 7
+
+# rca_dtype
+RCA_F32, RCA_I16, RCA_F16, RCA_C32, RCA_C16F, RCA_C16BF = range(6)
+
+RCA_MODE_TWO_STAGE, RCA_MODE_DIRECT = 0, 1
+RCA_CLUTTER_NONE, RCA_CLUTTER_MEAN = 0, 1
+ULM_ENH_XDOPPLER, ULM_ENH_COHERENT = 0, 1
+
+(RCA_TAB_TX_F64, RCA_TAB_RX_F64, RCA_TAB_TX_Q16, RCA_TAB_RX_Q16, RCA_TAB_W, RCA_TAB_DMAX,
+ RCA_TAB_S2_SHIFT, RCA_TAB_S2_PSI, RCA_TAB_S2_EC, RCA_TAB_S2_COEF, RCA_TAB_S2_TMIN) = range(11)
+
+
+class rca_geometry_desc(C.Structure):
+    _fields_ = [("n_el", C.c_int), ("nz", C.c_int), ("ns", C.c_int), ("P", C.c_int), ("K", C.c_int),
+                ("us", C.c_int),
+                ("pitch_m", C.c_double), ("fc_hz", C.c_double), ("fs_hz", C.c_double),
+                ("c_mps", C.c_double), ("z0_m", C.c_double), ("dz_m", C.c_double), ("fnum", C.c_double),
+                ("ang_rc_rad", C.POINTER(C.c_double)), ("ang_cr_rad", C.POINTER(C.c_double))]
+
+
+class rca_bf_params(C.Structure):
+    _fields_ = [("mode", C.c_int), ("clutter", C.c_int), ("iq_dtype", C.c_int), ("reserved", C.c_int * 5)]
+
+
+class ulm_params(C.Structure):
+    _fields_ = [("d", C.c_int), ("sig_z", C.c_float), ("sig_lat", C.c_float), ("alpha", C.c_float),
+                ("ncc_min", C.c_float), ("enh", C.c_int), ("reserved", C.c_int * 4)]
+
+
+LOC2D = np.dtype([("frame", "<i4"), ("axis", "<i4"), ("slab", "<i4"), ("iz", "<i4"), ("ilat", "<i4"),
+                  ("z", "<f4"), ("lat", "<f4"), ("ncc", "<f4"), ("amp", "<f4"), ("reserved", "<i4")])
+LOC3D = np.dtype([("frame", "<i4"), ("i_xz", "<i4"), ("i_yz", "<i4"), ("reserved", "<i4"),
+                  ("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("amp_xz", "<f4"), ("amp_yz", "<f4"),
+                  ("reserved2", "<f4")])
+assert LOC2D.itemsize == 40 and LOC3D.itemsize == 40
+
+_P = C.c_void_p
+_I = C.c_int
+_S = C.c_int  # rca_status
+_SZ = C.c_size_t
+
+# name -> (restype, argtypes); every symbol declared in include/rca.h
+SIGNATURES = {
+    "rca_version": (_I, []),
+    "rca_status_string": (C.c_char_p, [_S]),
+    "rca_create": (_S, [C.POINTER(_P), _I]),
+    "rca_destroy": (_S, [_P]),
+    "rca_set_stream": (_S, [_P, _P]),
+    "rca_last_error": (C.c_char_p, [_P]),
+    "rca_sync_status": (_S, [_P, C.POINTER(_I)]),
+    "rca_reserve": (_S, [_P, _P, _I]),
+    "rca_geometry_create": (_S, [_P, C.POINTER(rca_geometry_desc), C.POINTER(_P)]),
+    "rca_geometry_destroy": (_S, [_P]),
+    "rca_delay_tables": (_S, [_P, _P, C.POINTER(_P)]),
+    "rca_tables_destroy": (_S, [_P]),
+    "rca_tables_query": (_S, [_P, _I, C.POINTER(_SZ), C.POINTER(_I)]),
+    "rca_tables_download": (_S, [_P, _I, _P, _SZ]),
+    "rca_ingest": (_S, [_P, _P, _P, _I, _P, _I, _I, _P, _I]),
+    "rca_stage1": (_S, [_P, _P, _P, _I, _I, _P]),
+    "rca_stage2_project": (_S, [_P, _P, _P, _I, _P, _I]),
+    "rca_direct_project": (_S, [_P, _P, _P, _I, _I, _P, _I]),
+    "rca_beamform_projections": (_S, [_P, _P, _P, _I, _P, _I, C.POINTER(rca_bf_params), _P, _I]),
+    "ulm_enhance": (_S, [_P, _P, _P, _I, _I, _I, _P, _P]),
+    "ulm_detect2d": (_S, [_P, _P, _P, _P, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _P]),
+    "ulm_pair3d": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
+    "ulm_localize": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _I, _P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librca.so and declare every entry point.  Raises if missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"librca not built ({path} missing); run `python -m paper_2511_21647_gb300.build`")
+            L = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib

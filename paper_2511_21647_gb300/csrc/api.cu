@@ -1,0 +1,522 @@
+// api.cu -- host side of the librca C ABI (argument checks, workspace,
+// launches).  Every entry point validates on the host before enqueuing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rca_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+rca_status set_error(rca_handle* h, rca_status s, const char* fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->last_error = buf;
+    }
+    return s;
+}
+
+rca_status cuda_check(rca_handle* h, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return RCA_OK;
+    return set_error(h, RCA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static bool capturing(rca_handle* h)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(h->stream, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+void* ws_get(rca_handle* h, WsSlot slot, size_t bytes, rca_status* st)
+{
+    WsBuf& b = h->ws[slot];
+    if (b.bytes >= bytes && b.p) return b.p;
+    if (capturing(h)) {
+        *st = set_error(h, RCA_ERR_CAPACITY, "workspace slot %d needs %zu bytes during stream capture; call rca_reserve first",
+                        (int)slot, bytes);
+        return nullptr;
+    }
+    if (b.p) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        *st = cuda_check(h, e, "workspace cudaMalloc");
+        return nullptr;
+    }
+    b.bytes = want;
+    return b.p;
+}
+
+size_t dtype_size(rca_dtype t)
+{
+    switch (t) {
+    case RCA_F32: return 4;
+    case RCA_I16: return 2;
+    case RCA_F16: return 2;
+    case RCA_C32: return 8;
+    case RCA_C16F: return 4;
+    case RCA_C16BF: return 4;
+    }
+    return 0;
+}
+
+static bool is_complex(int t) { return t == RCA_C32 || t == RCA_C16F || t == RCA_C16BF; }
+static bool is_real_rf(int t) { return t == RCA_F32 || t == RCA_F16 || t == RCA_I16; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CHECK_HANDLE(h)                                                                                     \
+    do {                                                                                                     \
+        if (!(h)) return RCA_ERR_INVALID_ARG;                                                                \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+extern "C" int rca_version(void) { return (RCA_VERSION_MAJOR << 16) | RCA_VERSION_MINOR; }
+
+extern "C" const char* rca_status_string(rca_status s)
+{
+    switch (s) {
+    case RCA_OK: return "ok";
+    case RCA_ERR_INVALID_ARG: return "invalid argument";
+    case RCA_ERR_SHAPE: return "shape mismatch";
+    case RCA_ERR_UNSUPPORTED: return "unsupported";
+    case RCA_ERR_CUDA: return "CUDA error";
+    case RCA_ERR_CAPACITY: return "output capacity exceeded";
+    case RCA_ERR_TIMEOUT: return "bounded wait timed out";
+    case RCA_ERR_BOUNDS: return "index out of bounds";
+    }
+    return "unknown status";
+}
+
+extern "C" rca_status rca_create(rca_handle** out, int device)
+{
+    if (!out) return RCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RCA_ERR_CUDA;
+    rca_handle* h = new (std::nothrow) rca_handle();
+    if (!h) return RCA_ERR_CUDA;
+    h->device = device;
+    DeviceGuard dg(device);
+    if (cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        delete h;
+        return RCA_ERR_CUDA;
+    }
+    *out = h;
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_destroy(rca_handle* h)
+{
+    CHECK_HANDLE(h);
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto& b : h->ws)
+        if (b.p) cudaFree(b.p);
+    cudaFree(h->d_status);
+    delete h;
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_set_stream(rca_handle* h, void* stream)
+{
+    CHECK_HANDLE(h);
+    h->stream = (cudaStream_t)stream;
+    return RCA_OK;
+}
+
+extern "C" const char* rca_last_error(const rca_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+extern "C" rca_status rca_sync_status(rca_handle* h, rca_status* dev)
+{
+    CHECK_HANDLE(h);
+    DeviceGuard dg(h->device);
+    if (dev) *dev = RCA_OK;
+    rca_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (st != RCA_OK) return st;
+    unsigned w = 0;
+    st = cuda_check(h, cudaMemcpy(&w, h->d_status, sizeof w, cudaMemcpyDeviceToHost), "status read");
+    if (st != RCA_OK) return st;
+    st = cuda_check(h, cudaMemset(h->d_status, 0, sizeof(unsigned)), "status clear");
+    if (dev) {
+        if (w & ST_BOUNDS) *dev = RCA_ERR_BOUNDS;
+        else if (w & ST_TIMEOUT) *dev = RCA_ERR_TIMEOUT;
+        else if (w & ST_CAPACITY) *dev = RCA_ERR_CAPACITY;
+    }
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// geometry and tables
+// ---------------------------------------------------------------------------
+extern "C" rca_status rca_geometry_create(rca_handle* h, const rca_geometry_desc* d, rca_geometry** out)
+{
+    CHECK_HANDLE(h);
+    if (!d || !out) return set_error(h, RCA_ERR_INVALID_ARG, "null descriptor or output");
+    *out = nullptr;
+    if (d->n_el <= 0 || d->nz <= 1 || d->ns <= 1 || d->P <= 0 || d->K <= 0 || d->us <= 0)
+        return set_error(h, RCA_ERR_INVALID_ARG, "sizes must be positive (nz, ns > 1)");
+    if (d->K > RCA_MAX_K) return set_error(h, RCA_ERR_UNSUPPORTED, "K = %d > %d transmissions per family", d->K, RCA_MAX_K);
+    if (d->us > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "us = %d > 8", d->us);
+    if (d->n_el % d->P != 0) return set_error(h, RCA_ERR_INVALID_ARG, "n_el %% P != 0");
+    if (d->n_el > 256) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256");
+    if ((long)d->ns * 65536L >= (1L << 31)) return set_error(h, RCA_ERR_UNSUPPORTED, "ns too large for Q16 delays");
+    if (!(d->pitch_m > 0) || !(d->fc_hz > 0) || !(d->fs_hz > 0) || !(d->c_mps > 0) || !(d->dz_m > 0) || !(d->fnum > 0) ||
+        !(d->z0_m > 0))
+        return set_error(h, RCA_ERR_INVALID_ARG, "physical parameters must be positive");
+    if (!d->ang_rc_rad || !d->ang_cr_rad) return set_error(h, RCA_ERR_INVALID_ARG, "null angle arrays");
+    rca_geometry* g = new (std::nothrow) rca_geometry();
+    if (!g) return set_error(h, RCA_ERR_CUDA, "out of host memory");
+    g->desc = *d;
+    g->ang.assign(d->ang_rc_rad, d->ang_rc_rad + d->K);
+    g->ang.insert(g->ang.end(), d->ang_cr_rad, d->ang_cr_rad + d->K);
+    g->desc.ang_rc_rad = g->ang.data();
+    g->desc.ang_cr_rad = g->ang.data() + d->K;
+    GeomDev& gd = g->gd;
+    gd.N = d->n_el;
+    gd.nz = d->nz;
+    gd.us = d->us;
+    gd.nzs = (d->nz - 1) * d->us + 1;
+    gd.ns = d->ns;
+    gd.P = d->P;
+    gd.S = d->n_el / d->P;
+    gd.K = d->K;
+    gd.pitch = d->pitch_m;
+    gd.fc = d->fc_hz;
+    gd.fs = d->fs_hz;
+    gd.c = d->c_mps;
+    gd.z0 = d->z0_m;
+    gd.dz = d->dz_m;
+    gd.fnum = d->fnum;
+    gd.t0 = 2.0 * d->z0_m / d->c_mps;
+    gd.L = (double)d->n_el * d->pitch_m;
+    for (int k = 0; k < 2 * d->K; ++k) {
+        double a = g->ang[k];
+        if (!(std::fabs(a) < 1.4)) {
+            delete g;
+            return set_error(h, RCA_ERR_INVALID_ARG, "steering angle %d out of range", k);
+        }
+        gd.sin_th[k] = std::sin(a);
+        gd.cos_th[k] = std::cos(a);
+    }
+    *out = g;
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_geometry_destroy(rca_geometry* g)
+{
+    delete g;
+    return RCA_OK;
+}
+
+static void free_tables(rca_tables* t)
+{
+    void* ptrs[] = {t->tx_f64, t->rx_f64, t->tx_q16, t->rx_q16, t->W, t->dmax, t->s2_shift, t->s2_sfl,
+                    t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin, t->dtx_q16, t->dtx_ph, t->mix,
+                    t->s1.d_chunks};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" rca_status rca_delay_tables(rca_handle* h, const rca_geometry* g, rca_tables** out)
+{
+    CHECK_HANDLE(h);
+    if (!g || !out) return set_error(h, RCA_ERR_INVALID_ARG, "null geometry or output");
+    *out = nullptr;
+    if (capturing(h)) return set_error(h, RCA_ERR_INVALID_ARG, "rca_delay_tables cannot run during stream capture");
+    DeviceGuard dg(h->device);
+    rca_tables* t = new (std::nothrow) rca_tables();
+    if (!t) return set_error(h, RCA_ERR_CUDA, "out of host memory");
+    t->h = h;
+    t->gd = g->gd;
+    rca_status st = launch_tables(h, t);
+    if (st != RCA_OK) {
+        free_tables(t);
+        delete t;
+        return st;
+    }
+    *out = t;
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_tables_destroy(rca_tables* t)
+{
+    if (!t) return RCA_ERR_INVALID_ARG;
+    DeviceGuard dg(t->h->device);
+    cudaStreamSynchronize(t->h->stream);
+    free_tables(t);
+    delete t;
+    return RCA_OK;
+}
+
+static rca_status table_info(const rca_tables* t, int id, const void** ptr, size_t* bytes, int dims[4])
+{
+    const GeomDev& g = t->gd;
+    const int nt = 2 * g.K;
+    int d[4] = {0, 0, 0, 0};
+    size_t es = 0;
+    const void* p = nullptr;
+    switch (id) {
+    case RCA_TAB_TX_F64: p = t->tx_f64; es = 8; d[0] = nt; d[1] = g.nzs; break;
+    case RCA_TAB_RX_F64: p = t->rx_f64; es = 8; d[0] = g.N; d[1] = g.nzs; break;
+    case RCA_TAB_TX_Q16: p = t->tx_q16; es = 4; d[0] = nt; d[1] = g.nzs; break;
+    case RCA_TAB_RX_Q16: p = t->rx_q16; es = 4; d[0] = g.nzs; d[1] = g.N; break;
+    case RCA_TAB_W: p = t->W; es = 8; d[0] = g.nzs; d[1] = g.N; break;
+    case RCA_TAB_DMAX: p = t->dmax; es = 4; d[0] = g.nzs; break;
+    case RCA_TAB_S2_SHIFT: p = t->s2_shift; es = 8; d[0] = nt; d[1] = g.N; break;
+    case RCA_TAB_S2_PSI: p = t->s2_psi; es = 8; d[0] = nt; d[1] = g.N; break;
+    case RCA_TAB_S2_EC: p = t->s2_ec; es = 8; d[0] = nt; d[1] = g.nz; break;
+    case RCA_TAB_S2_COEF: p = t->s2_coef; es = 8; d[0] = nt; d[1] = g.S; d[2] = g.nz; d[3] = t->T; break;
+    case RCA_TAB_S2_TMIN: p = t->s2_tmin; es = 4; d[0] = nt; d[1] = g.S; break;
+    default: return RCA_ERR_INVALID_ARG;
+    }
+    size_t n = 1;
+    for (int q = 0; q < 4; ++q)
+        if (d[q]) n *= (size_t)d[q];
+    if (ptr) *ptr = p;
+    if (bytes) *bytes = n * es;
+    if (dims)
+        for (int q = 0; q < 4; ++q) dims[q] = d[q];
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_tables_query(const rca_tables* t, int id, size_t* bytes, int dims[4])
+{
+    if (!t) return RCA_ERR_INVALID_ARG;
+    return table_info(t, id, nullptr, bytes, dims);
+}
+
+extern "C" rca_status rca_tables_download(const rca_tables* t, int id, void* dst, size_t bytes)
+{
+    if (!t || !dst) return RCA_ERR_INVALID_ARG;
+    const void* p = nullptr;
+    size_t need = 0;
+    rca_status st = table_info(t, id, &p, &need, nullptr);
+    if (st != RCA_OK) return set_error(t->h, st, "unknown table id %d", id);
+    if (bytes < need) return set_error(t->h, RCA_ERR_SHAPE, "table %d needs %zu bytes, got %zu", id, need, bytes);
+    DeviceGuard dg(t->h->device);
+    st = cuda_check(t->h, cudaStreamSynchronize(t->h->stream), "sync before download");
+    if (st != RCA_OK) return st;
+    return cuda_check(t->h, cudaMemcpy(dst, p, need, cudaMemcpyDeviceToHost), "table download");
+}
+
+extern "C" rca_status rca_reserve(rca_handle* h, const rca_geometry* g, int F)
+{
+    CHECK_HANDLE(h);
+    if (!g || F <= 0) return set_error(h, RCA_ERR_INVALID_ARG, "null geometry or F <= 0");
+    DeviceGuard dg(h->device);
+    const GeomDev& gd = g->gd;
+    const size_t nt = 2 * gd.K;
+    rca_status st = RCA_OK;
+    const int nstrip = (gd.nz + DET_RS - 1) / DET_RS;
+    const size_t nslots = (size_t)F * 2 * gd.S * nstrip;
+    struct {
+        WsSlot s;
+        size_t b;
+    } want[] = {
+        {WS_MEAN, nt * gd.N * gd.ns * sizeof(float)},
+        {WS_IQ, (size_t)F * nt * gd.N * gd.ns * sizeof(float2)},
+        {WS_SLICES, (size_t)F * nt * gd.nzs * gd.N * sizeof(float2)},
+        {WS_A, (size_t)F * 2 * gd.S * gd.nz * gd.N * sizeof(float)},
+        {WS_M, (size_t)F * sizeof(float)},
+        {WS_CAND, nslots * CAND_CAP * sizeof(ulm_loc2d)},
+        {WS_CANDCNT, nslots * sizeof(int)},
+        {WS_SCAN, (nslots + 1) * sizeof(int)},
+        {WS_PLANEOFF, ((size_t)F * 2 * gd.S + 1) * sizeof(int)},
+    };
+    for (auto& w : want)
+        if (!ws_get(h, w.s, w.b, &st)) return st;
+    return cuda_check(h, cudaStreamSynchronize(h->stream), "reserve");
+}
+
+// ---------------------------------------------------------------------------
+// beamforming
+// ---------------------------------------------------------------------------
+static rca_status check_tables(rca_handle* h, const rca_tables* t, int F)
+{
+    if (!t) return set_error(h, RCA_ERR_INVALID_ARG, "null tables");
+    if (t->h->device != h->device) return set_error(h, RCA_ERR_INVALID_ARG, "tables belong to another device");
+    if (F <= 0) return set_error(h, RCA_ERR_SHAPE, "n_frames must be positive");
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca_dtype rf_t, const float* scale,
+                                 int F, int clutter, void* iq, rca_dtype iq_t)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!rf || !iq) return set_error(h, RCA_ERR_INVALID_ARG, "null rf or iq");
+    if (!is_real_rf(rf_t)) return set_error(h, RCA_ERR_UNSUPPORTED, "rf dtype must be F32, F16 or I16");
+    if (rf_t == RCA_I16 && !scale) return set_error(h, RCA_ERR_INVALID_ARG, "int16 rf needs a scale array");
+    if (!is_complex(iq_t)) return set_error(h, RCA_ERR_UNSUPPORTED, "iq dtype must be C32, C16F or C16BF");
+    if (clutter != RCA_CLUTTER_NONE && clutter != RCA_CLUTTER_MEAN) return set_error(h, RCA_ERR_INVALID_ARG, "bad clutter mode");
+    DeviceGuard dg(h->device);
+    return launch_ingest(h, t, rf, rf_t, scale, F, clutter, iq, iq_t);
+}
+
+extern "C" rca_status rca_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F, void* slices)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!iq || !slices) return set_error(h, RCA_ERR_INVALID_ARG, "null iq or slices");
+    if (!is_complex(iq_t)) return set_error(h, RCA_ERR_UNSUPPORTED, "iq dtype must be C32, C16F or C16BF");
+    DeviceGuard dg(h->device);
+    return launch_stage1(h, t, iq, iq_t, F, (float2*)slices);
+}
+
+extern "C" rca_status rca_stage2_project(rca_handle* h, const rca_tables* t, const void* slices, int F, void* planes,
+                                         rca_dtype pt)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!slices || !planes) return set_error(h, RCA_ERR_INVALID_ARG, "null slices or planes");
+    if (!is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
+    DeviceGuard dg(h->device);
+    return launch_stage2(h, t, (const float2*)slices, F, planes, pt);
+}
+
+extern "C" rca_status rca_direct_project(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
+                                         void* planes, rca_dtype pt)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!iq || !planes) return set_error(h, RCA_ERR_INVALID_ARG, "null iq or planes");
+    if (!is_complex(iq_t) || !is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "complex dtypes required");
+    DeviceGuard dg(h->device);
+    return launch_direct(h, t, iq, iq_t, F, planes, pt);
+}
+
+extern "C" rca_status rca_beamform_projections(rca_handle* h, const rca_tables* t, const void* rf, rca_dtype rf_t,
+                                               const float* scale, int F, const rca_bf_params* prm, void* planes,
+                                               rca_dtype pt)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!rf || !planes || !prm) return set_error(h, RCA_ERR_INVALID_ARG, "null rf, planes or params");
+    if (prm->mode != RCA_MODE_TWO_STAGE && prm->mode != RCA_MODE_DIRECT) return set_error(h, RCA_ERR_INVALID_ARG, "bad mode");
+    if (!is_real_rf(rf_t)) return set_error(h, RCA_ERR_UNSUPPORTED, "rf dtype must be F32, F16 or I16");
+    if (rf_t == RCA_I16 && !scale) return set_error(h, RCA_ERR_INVALID_ARG, "int16 rf needs a scale array");
+    if (!is_complex(prm->iq_dtype) || !is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "complex dtypes required");
+    if (prm->clutter != RCA_CLUTTER_NONE && prm->clutter != RCA_CLUTTER_MEAN) return set_error(h, RCA_ERR_INVALID_ARG, "bad clutter mode");
+    DeviceGuard dg(h->device);
+    const GeomDev& g = t->gd;
+    const rca_dtype iq_t = (rca_dtype)prm->iq_dtype;
+    void* iq = ws_get(h, WS_IQ, (size_t)F * 2 * g.K * g.N * g.ns * dtype_size(iq_t), &st);
+    if (!iq) return st;
+    if ((st = launch_ingest(h, t, rf, rf_t, scale, F, prm->clutter, iq, iq_t)) != RCA_OK) return st;
+    if (prm->mode == RCA_MODE_DIRECT) return launch_direct(h, t, iq, iq_t, F, planes, pt);
+    float2* slices = (float2*)ws_get(h, WS_SLICES, (size_t)F * 2 * g.K * g.nzs * g.N * sizeof(float2), &st);
+    if (!slices) return st;
+    if ((st = launch_stage1(h, t, iq, iq_t, F, slices)) != RCA_OK) return st;
+    return launch_stage2(h, t, slices, F, planes, pt);
+}
+
+// ---------------------------------------------------------------------------
+// localisation
+// ---------------------------------------------------------------------------
+static rca_status check_ulm(rca_handle* h, const ulm_params* p)
+{
+    if (!p) return set_error(h, RCA_ERR_INVALID_ARG, "null ulm_params");
+    if (p->d < 3 || p->d > RCA_MAX_NCC_D || p->d % 2 == 0) return set_error(h, RCA_ERR_INVALID_ARG, "d must be odd in [3, 15]");
+    if (!(p->sig_z > 0) || !(p->sig_lat > 0)) return set_error(h, RCA_ERR_INVALID_ARG, "PSF sigmas must be positive");
+    if (!(p->alpha >= 0) || !(p->ncc_min > -1.0f)) return set_error(h, RCA_ERR_INVALID_ARG, "bad thresholds");
+    if (p->enh != ULM_ENH_XDOPPLER && p->enh != ULM_ENH_COHERENT) return set_error(h, RCA_ERR_INVALID_ARG, "bad enhancement mode");
+    return RCA_OK;
+}
+
+extern "C" rca_status ulm_enhance(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F, int enh,
+                                  float* A, float* M)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!planes || !A || !M) return set_error(h, RCA_ERR_INVALID_ARG, "null planes, A or M");
+    if (!is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
+    DeviceGuard dg(h->device);
+    return launch_enhance(h, t, planes, pt, F, enh, A, M);
+}
+
+extern "C" rca_status ulm_detect2d(rca_handle* h, const rca_tables* t, const float* A, const float* M, int F,
+                                   const ulm_params* prm, ulm_loc2d* out, int cap, int* n2d, float* ncc_out,
+                                   int* plane_off)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if ((st = check_ulm(h, prm)) != RCA_OK) return st;
+    if (!A || !M || !n2d || (cap > 0 && !out) || cap < 0) return set_error(h, RCA_ERR_INVALID_ARG, "null A, M, list or count");
+    if (t->gd.N < prm->d || t->gd.nz < prm->d) return set_error(h, RCA_ERR_SHAPE, "plane smaller than the NCC kernel");
+    DeviceGuard dg(h->device);
+    return launch_detect2d(h, t, A, M, F, prm, out, cap, n2d, ncc_out, plane_off);
+}
+
+extern "C" rca_status ulm_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d, int cap2d, int F,
+                                 ulm_loc3d* out, int cap3d, int* n3d)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!n2d || !n3d || cap2d < 0 || cap3d < 0 || (cap2d > 0 && !L) || (cap3d > 0 && !out))
+        return set_error(h, RCA_ERR_INVALID_ARG, "null list or count");
+    DeviceGuard dg(h->device);
+    return launch_pair3d(h, t, L, n2d, cap2d, F, out, cap3d, n3d);
+}
+
+extern "C" rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
+                                   const ulm_params* prm, ulm_loc2d* out2d, int cap2d, int* n2d, ulm_loc3d* out3d,
+                                   int cap3d, int* n3d)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if ((st = check_ulm(h, prm)) != RCA_OK) return st;
+    if (!planes || !n2d || !n3d || cap2d < 0 || cap3d < 0 || (cap2d > 0 && !out2d) || (cap3d > 0 && !out3d))
+        return set_error(h, RCA_ERR_INVALID_ARG, "null planes, list or count");
+    if (!is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
+    if (t->gd.N < prm->d || t->gd.nz < prm->d) return set_error(h, RCA_ERR_SHAPE, "plane smaller than the NCC kernel");
+    DeviceGuard dg(h->device);
+    const GeomDev& g = t->gd;
+    float* A = (float*)ws_get(h, WS_A, (size_t)F * 2 * g.S * g.nz * g.N * sizeof(float), &st);
+    if (!A) return st;
+    float* M = (float*)ws_get(h, WS_M, (size_t)F * sizeof(float), &st);
+    if (!M) return st;
+    if ((st = launch_enhance(h, t, planes, pt, F, prm->enh, A, M)) != RCA_OK) return st;
+    if ((st = launch_detect2d(h, t, A, M, F, prm, out2d, cap2d, n2d, nullptr, nullptr)) != RCA_OK) return st;
+    return launch_pair3d(h, t, out2d, n2d, cap2d, F, out3d, cap3d, n3d);
+}

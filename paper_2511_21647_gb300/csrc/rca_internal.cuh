@@ -1,0 +1,198 @@
+// rca_internal.cuh -- internal types shared by librca's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rca.h"
+
+// ---------------------------------------------------------------------------
+// device status word bits (read by rca_sync_status)
+// ---------------------------------------------------------------------------
+enum : unsigned {
+    ST_CAPACITY = 1u << 0,
+    ST_TIMEOUT = 1u << 1,
+    ST_BOUNDS = 1u << 2,
+};
+
+// Geometry as seen by kernels (plain values, passed by value).
+struct GeomDev {
+    int N;       // elements per array = lateral pixels
+    int nz;      // plane rows
+    int nzs;     // slice rows = (nz - 1) * us + 1
+    int ns;      // samples per channel
+    int P;       // slab size
+    int S;       // slabs per axis = N / P
+    int K;       // transmissions per family
+    int us;      // slice oversampling
+    double pitch, fc, fs, c, z0, dz, fnum, t0, L;
+    double sin_th[2 * RCA_MAX_K];
+    double cos_th[2 * RCA_MAX_K];
+};
+
+// Workspace slots owned by a handle.
+enum WsSlot {
+    WS_MEAN = 0,   // float [2K][E][ns] clutter mean
+    WS_IQ,         // IQ of the current ensemble
+    WS_SLICES,     // float2 [F][2K][nzs][N]
+    WS_A,          // float [F][2][S][nz][N]
+    WS_M,          // float [F]
+    WS_CAND,       // ulm_loc2d [strips][CAND_CAP]
+    WS_CANDCNT,    // int [strips]
+    WS_PLANEOFF,   // int [planes + 1]
+    WS_FLAGS,      // int [n]
+    WS_SCAN,       // int [n + 1]
+    WS_N2D,        // int [1]
+    WS_MISC,       // small scratch
+    WS_COUNT
+};
+
+struct WsBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct rca_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    unsigned* d_status = nullptr;
+    std::string last_error;
+    WsBuf ws[WS_COUNT];
+};
+
+struct rca_geometry {
+    rca_geometry_desc desc{};
+    std::vector<double> ang;  // 2K angles, RC first
+    GeomDev gd{};
+};
+
+// Stage-1 launch shape chosen at table-build time.  A CTA owns `zt` slice
+// rows of one (frame, transmission) and walks the lateral distance d in
+// chunks of `dc`; chunk c of row tile t needs the contiguous sample rows
+// [nlo, nlo + nrows) of the [ns][E] IQ block (element innermost).
+struct Stage1Plan {
+    int zt = 0;               // slice rows per CTA
+    int dc = 0;               // lateral distances per chunk
+    int n_tiles = 0;
+    int nch = 0;              // chunks per tile
+    int win = 0;              // max nrows over all chunks
+    int4* d_chunks = nullptr; // [2K][n_tiles][nch] {nlo, nrows, d0, d1}
+};
+
+struct Stage2Plan {
+    int zp = 0;           // plane rows per CTA
+    int n_tiles = 0;
+    int rows = 0;         // slice rows held per transmission
+    int smin[2] = {0, 0}; // per family: min floor shift (slice rows)
+    int smax[2] = {0, 0};
+};
+
+struct rca_tables {
+    rca_handle* h = nullptr;
+    GeomDev gd{};
+    // Stage-1 / DAS tables
+    double* tx_f64 = nullptr;   // [2K][nzs]
+    double* rx_f64 = nullptr;   // [N][nzs]
+    int* tx_q16 = nullptr;      // [2K][nzs]
+    int* rx_q16 = nullptr;      // [nzs][N]
+    float2* W = nullptr;        // [nzs][N]
+    int* dmax = nullptr;        // [nzs]
+    // Stage-2 tables
+    double* s2_shift = nullptr; // [2K][N]
+    int* s2_sfl = nullptr;      // [2K][N] floor of the shift
+    float* s2_sfr = nullptr;    // [2K][N] fractional part
+    float2* s2_psi = nullptr;   // [2K][N]
+    float2* s2_ec = nullptr;    // [2K][nz]
+    float2* s2_coef = nullptr;  // [2K][S][nz][T]
+    int* s2_tmin = nullptr;     // [2K][S]
+    int T = 0;
+    // direct (conventional 3D) tables
+    int* dtx_q16 = nullptr;     // [2K][N][nz] transmit delay at transverse u, plane depth
+    float2* dtx_ph = nullptr;   // [2K][N][nz] exp(j 2 pi fc (tau_tx + z / c))
+    // demodulation
+    float2* mix = nullptr;      // [ns] exp(-j 2 pi fc t_n)
+    float fir[31] = {0};        // half-band taps (host copy; passed by value)
+    Stage1Plan s1;
+    Stage2Plan s2;
+    int direct_win = 0;         // window for direct mode (rows of samples)
+    int direct_zt = 0;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define RCA_MAX_NCC_D 15
+#define CAND_CAP 64       // 2D candidates per (plane, row strip)
+#define DET_RS 16         // rows per detect strip
+
+struct NccConst {
+    int d, h;
+    float gz[RCA_MAX_NCC_D];
+    float gl[RCA_MAX_NCC_D];
+    float muG, inv_ssG_sqrt, flat_coef;  // flat_coef = 1e-5 d^2
+    float alpha, ncc_min;
+};
+
+rca_status set_error(rca_handle* h, rca_status s, const char* fmt, ...);
+rca_status cuda_check(rca_handle* h, cudaError_t e, const char* what);
+void* ws_get(rca_handle* h, WsSlot slot, size_t bytes, rca_status* st);
+
+// size in bytes of one element of a dtype
+size_t dtype_size(rca_dtype t);
+
+// launchers (implemented in the .cu files)
+rca_status launch_tables(rca_handle* h, rca_tables* t);
+rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca_dtype rf_t,
+                         const float* scale, int F, int clutter, void* iq, rca_dtype iq_t);
+rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
+                         float2* slices);
+rca_status launch_stage2(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes,
+                         rca_dtype pt);
+rca_status launch_direct(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
+                         void* planes, rca_dtype pt);
+rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
+                          int enh, float* A, float* M);
+rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, const float* M, int F,
+                           const ulm_params* prm, ulm_loc2d* out, int cap, int* n2d, float* ncc_out,
+                           int* plane_off);
+rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d, int cap2d,
+                         int F, ulm_loc3d* out, int cap3d, int* n3d);
+
+// ---------------------------------------------------------------------------
+// device-side element access for the supported complex / real dtypes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 load_c(const void* p, size_t i, int dt)
+{
+    if (dt == RCA_C32) return reinterpret_cast<const float2*>(p)[i];
+    if (dt == RCA_C16F) return __half22float2(reinterpret_cast<const __half2*>(p)[i]);
+    return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(p)[i]);
+}
+
+__device__ __forceinline__ void store_c(void* p, size_t i, int dt, float2 v)
+{
+    if (dt == RCA_C32) {
+        reinterpret_cast<float2*>(p)[i] = v;
+    } else if (dt == RCA_C16F) {
+        reinterpret_cast<__half2*>(p)[i] = __float22half2_rn(v);
+    } else {
+        reinterpret_cast<__nv_bfloat162*>(p)[i] = __float22bfloat162_rn(v);
+    }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void cfma(float2& acc, float2 w, float2 v)
+{
+    acc.x = fmaf(w.x, v.x, acc.x);
+    acc.x = fmaf(-w.y, v.y, acc.x);
+    acc.y = fmaf(w.x, v.y, acc.y);
+    acc.y = fmaf(w.y, v.x, acc.y);
+}

@@ -1,0 +1,365 @@
+// tables.cu -- per-geometry delay / weight tables, computed on the GPU in FP64.
+//
+// Built with -fmad=false so every double expression rounds exactly as
+// written (the transmit / receive delays are then bit-reproducible).
+//
+// Geometry (Sec. II-A1, Sec. II-C): element / pixel centres
+// u = (e - (N-1)/2) pitch; RC transmission k has the plane-wave delay
+// (z cos th + trans sin th + (L/2)|sin th|)/c and receives on line elements
+// with sqrt(off^2 + z^2)/c.  Stage 1 works on slice rows z_r = z0 + r dz/us;
+// the planes on rows z_i = z0 + i dz.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "rca_internal.cuh"
+
+#define TWO_PI_D 6.283185307179586476925286766559
+#define PI_D 3.1415926535897932384626433832795
+
+namespace {
+
+__device__ __forceinline__ double elem_pos(const GeomDev& g, int e)
+{
+    return ((double)e - 0.5 * (g.N - 1)) * g.pitch;
+}
+
+__device__ __forceinline__ double slice_z(const GeomDev& g, int r) { return g.z0 + (double)r * (g.dz / (double)g.us); }
+
+__device__ __forceinline__ double plane_z(const GeomDev& g, int i) { return g.z0 + (double)i * g.dz; }
+
+__device__ __forceinline__ double tau_tx(const GeomDev& g, int k, double trans, double z)
+{
+    return (z * g.cos_th[k] + trans * g.sin_th[k] + 0.5 * g.L * fabs(g.sin_th[k])) / g.c;
+}
+
+__device__ __forceinline__ double tau_rx(const GeomDev& g, double off, double z) { return sqrt(off * off + z * z) / g.c; }
+
+__device__ __forceinline__ double tau_c(const GeomDev& g, int k, double z)
+{
+    return (z * (1.0 + g.cos_th[k]) + 0.5 * g.L * fabs(g.sin_th[k])) / g.c;
+}
+
+__device__ __forceinline__ double hann(const GeomDev& g, double off, double z)
+{
+    double a = z / g.fnum;
+    if (fabs(off) > 0.5 * a) return 0.0;
+    double ct = cos(PI_D * off / a);
+    return ct * ct;
+}
+
+__device__ __forceinline__ float2 cis(double ph)
+{
+    double s, c;
+    sincos(ph, &s, &c);
+    return make_float2((float)c, (float)s);
+}
+
+__device__ __forceinline__ int q16(double samples) { return __double2int_rn(samples * 65536.0); }
+
+// Stage-1 / DAS tables.  One thread per (r, d) of the [nzs][N] grid also
+// fills the [2K][nzs] transmit tables and dmax for d == 0.
+__global__ void k_tables_das(GeomDev g, double* tx_f64, double* rx_f64, int* tx_q16, int* rx_q16, float2* W,
+                             int* dmax)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.nzs * g.N) return;
+    int r = idx / g.N, d = idx % g.N;
+    double z = slice_z(g, r);
+    double off = (double)d * g.pitch;
+    double trx = tau_rx(g, off, z);
+    rx_f64[(size_t)d * g.nzs + r] = trx * g.fs;
+    rx_q16[idx] = q16(trx * g.fs);
+    double w = hann(g, off, z);
+    float2 ph = cis(TWO_PI_D * g.fc * (trx - z / g.c));
+    W[idx] = make_float2((float)(w * (double)ph.x), (float)(w * (double)ph.y));
+    if (d == 0) {
+        double t0 = 2.0 * g.z0 / g.c;
+        for (int k = 0; k < 2 * g.K; ++k) {
+            double x = (tau_tx(g, k, 0.0, z) - t0) * g.fs;
+            tx_f64[(size_t)k * g.nzs + r] = x;
+            tx_q16[(size_t)k * g.nzs + r] = q16(x);
+        }
+        // largest lateral distance inside the aperture (hann() is non-zero there)
+        double a = z / g.fnum;
+        int m = -1;
+        for (int dd = 0; dd < g.N; ++dd)
+            if (!(fabs((double)dd * g.pitch) > 0.5 * a)) m = dd;
+        dmax[r] = m;
+    }
+}
+
+// Stage-2 per-(k, u) shift and carrier, per-(k, i) carrier.
+__global__ void k_tables_s2(GeomDev g, double* shift, int* sfl, float* sfr, float2* psi, float2* ec)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int nt = 2 * g.K;
+    if (idx < nt * g.N) {
+        int k = idx / g.N, m = idx % g.N;
+        double u = elem_pos(g, m);
+        double sh = u * g.sin_th[k] / (1.0 + g.cos_th[k]);
+        double s = sh * (double)g.us / g.dz;
+        double fl = floor(s);
+        shift[idx] = s;
+        sfl[idx] = (int)fl;
+        sfr[idx] = (float)(s - fl);
+        psi[idx] = cis(TWO_PI_D * g.fc * ((1.0 + g.cos_th[k]) * sh / g.c));
+    }
+    if (idx < nt * g.nz) {
+        int k = idx / g.nz, i = idx % g.nz;
+        ec[idx] = cis(TWO_PI_D * g.fc * tau_c(g, k, plane_z(g, i)));
+    }
+}
+
+// Transverse-slab sum coefficients: for plane row i of slab b,
+//   sum_{u in slab} valid(zeta) exp(j 2 pi fc tau_c,k(z_i + dz_k(u))) lerp_weights(zeta)
+// gathered onto slice rows us*i + tmin[k][b] + t, t < T.
+__global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, int T, float2* coef,
+                              unsigned* status)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int nt = 2 * g.K;
+    if (idx >= nt * g.S * g.nz) return;
+    int i = idx % g.nz;
+    int b = (idx / g.nz) % g.S;
+    int k = idx / (g.nz * g.S);
+    double accr[16], acci[16];
+    for (int t = 0; t < T; ++t) accr[t] = acci[t] = 0.0;
+    int base = g.us * i + tmin[k * g.S + b];
+    for (int m = b * g.P; m < (b + 1) * g.P; ++m) {
+        double s = shift[(size_t)k * g.N + m];
+        double zeta = (double)(g.us * i) + s;
+        if (!(zeta >= 0.0) || zeta > (double)(g.nzs - 1)) continue;
+        int n0 = (int)floor(zeta);
+        double fr = zeta - (double)n0;
+        double sh = elem_pos(g, m) * g.sin_th[k] / (1.0 + g.cos_th[k]);
+        double ph = TWO_PI_D * g.fc * tau_c(g, k, plane_z(g, i) + sh);
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        int t = n0 - base;
+        if (t < 0 || t + (fr > 0.0 ? 1 : 0) >= T) {
+            atomicOr(status, ST_BOUNDS);
+            continue;
+        }
+        accr[t] += (1.0 - fr) * cs;
+        acci[t] += (1.0 - fr) * sn;
+        if (fr > 0.0) {
+            accr[t + 1] += fr * cs;
+            acci[t + 1] += fr * sn;
+        }
+    }
+    for (int t = 0; t < T; ++t) coef[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
+}
+
+// Conventional-DAS transmit tables at every transverse position and plane row.
+__global__ void k_tables_direct(GeomDev g, int* dtx_q16, float2* dtx_ph)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int nt = 2 * g.K;
+    if (idx >= nt * g.N * g.nz) return;
+    int i = idx % g.nz;
+    int m = (idx / g.nz) % g.N;
+    int k = idx / (g.nz * g.N);
+    double z = plane_z(g, i);
+    double ttx = tau_tx(g, k, elem_pos(g, m), z);
+    double t0 = 2.0 * g.z0 / g.c;
+    dtx_q16[idx] = q16((ttx - t0) * g.fs);
+    dtx_ph[idx] = cis(TWO_PI_D * g.fc * (ttx + z / g.c));
+}
+
+__global__ void k_tables_mix(GeomDev g, float2* mix)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.ns) return;
+    double t0 = 2.0 * g.z0 / g.c;
+    mix[n] = cis(-TWO_PI_D * g.fc * (t0 + (double)n / g.fs));
+}
+
+// Half-band Hamming low-pass, 31 taps, cut-off fs/4: centre 1/2, even
+// offsets 0, odd offsets sinc(m/2) * hamming(m) scaled to sum to 1/2.
+void fir_taps(float out[31])
+{
+    double h[31];
+    double odd = 0.0;
+    for (int m = -15; m <= 15; ++m) {
+        double v = 0.0;
+        if (m % 2 != 0) {
+            double x = 0.5 * PI_D * m;
+            v = 0.5 * (std::sin(x) / x) * (0.54 + 0.46 * std::cos(PI_D * m / 15.0));
+            odd += v;
+        }
+        h[m + 15] = v;
+    }
+    for (int m = -15; m <= 15; ++m) out[m + 15] = (m == 0) ? 0.5f : (float)(h[m + 15] * (0.5 / odd));
+}
+
+template <typename T>
+T* dalloc(rca_handle* h, size_t n, rca_status* st)
+{
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        *st = cuda_check(h, e, "cudaMalloc(tables)");
+        return nullptr;
+    }
+    return (T*)p;
+}
+
+}  // namespace
+
+rca_status launch_tables(rca_handle* h, rca_tables* t)
+{
+    const GeomDev& g = t->gd;
+    const int nt = 2 * g.K;
+    rca_status st = RCA_OK;
+    t->tx_f64 = dalloc<double>(h, (size_t)nt * g.nzs, &st);
+    t->rx_f64 = dalloc<double>(h, (size_t)g.N * g.nzs, &st);
+    t->tx_q16 = dalloc<int>(h, (size_t)nt * g.nzs, &st);
+    t->rx_q16 = dalloc<int>(h, (size_t)g.N * g.nzs, &st);
+    t->W = dalloc<float2>(h, (size_t)g.N * g.nzs, &st);
+    t->dmax = dalloc<int>(h, (size_t)g.nzs, &st);
+    t->s2_shift = dalloc<double>(h, (size_t)nt * g.N, &st);
+    t->s2_sfl = dalloc<int>(h, (size_t)nt * g.N, &st);
+    t->s2_sfr = dalloc<float>(h, (size_t)nt * g.N, &st);
+    t->s2_psi = dalloc<float2>(h, (size_t)nt * g.N, &st);
+    t->s2_ec = dalloc<float2>(h, (size_t)nt * g.nz, &st);
+    t->s2_tmin = dalloc<int>(h, (size_t)nt * g.S, &st);
+    t->dtx_q16 = dalloc<int>(h, (size_t)nt * g.N * g.nz, &st);
+    t->dtx_ph = dalloc<float2>(h, (size_t)nt * g.N * g.nz, &st);
+    t->mix = dalloc<float2>(h, (size_t)g.ns, &st);
+    if (st != RCA_OK) return st;
+    fir_taps(t->fir);
+
+    cudaStream_t s = h->stream;
+    const int B = 256;
+    k_tables_das<<<(g.nzs * g.N + B - 1) / B, B, 0, s>>>(g, t->tx_f64, t->rx_f64, t->tx_q16, t->rx_q16, t->W,
+                                                          t->dmax);
+    int n2 = std::max(nt * g.N, nt * g.nz);
+    k_tables_s2<<<(n2 + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec);
+    k_tables_direct<<<(nt * g.N * g.nz + B - 1) / B, B, 0, s>>>(g, t->dtx_q16, t->dtx_ph);
+    k_tables_mix<<<(g.ns + B - 1) / B, B, 0, s>>>(g, t->mix);
+    if ((st = cuda_check(h, cudaGetLastError(), "table kernels")) != RCA_OK) return st;
+
+    // Download what the host needs to size the launches.
+    std::vector<int> txq((size_t)nt * g.nzs), rxq((size_t)g.N * g.nzs), dm(g.nzs), sfl((size_t)nt * g.N),
+        dtx((size_t)nt * g.N * g.nz);
+    cudaMemcpyAsync(txq.data(), t->tx_q16, txq.size() * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(rxq.data(), t->rx_q16, rxq.size() * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(dm.data(), t->dmax, dm.size() * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(sfl.data(), t->s2_sfl, sfl.size() * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(dtx.data(), t->dtx_q16, dtx.size() * 4, cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_check(h, cudaStreamSynchronize(s), "table download")) != RCA_OK) return st;
+
+    // Stage-2: slab coefficient offsets and the shift range per family.
+    std::vector<int> tmin((size_t)nt * g.S);
+    int T = 2;
+    for (int k = 0; k < nt; ++k)
+        for (int b = 0; b < g.S; ++b) {
+            int lo = 1 << 30, hi = -(1 << 30);
+            for (int m = b * g.P; m < (b + 1) * g.P; ++m) {
+                lo = std::min(lo, sfl[(size_t)k * g.N + m]);
+                hi = std::max(hi, sfl[(size_t)k * g.N + m]);
+            }
+            // one extra row on each side absorbs floor(us*i + s) != us*i + floor(s)
+            tmin[(size_t)k * g.S + b] = lo - 1;
+            T = std::max(T, hi - lo + 4);
+        }
+    if (T > 16) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 shift spans %d slice rows within one slab (max 12)", T - 4);
+    t->T = T;
+    for (int fam = 0; fam < 2; ++fam) {
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int k = fam * g.K; k < (fam + 1) * g.K; ++k)
+            for (int m = 0; m < g.N; ++m) {
+                lo = std::min(lo, sfl[(size_t)k * g.N + m]);
+                hi = std::max(hi, sfl[(size_t)k * g.N + m]);
+            }
+        t->s2.smin[fam] = lo - 1;
+        t->s2.smax[fam] = hi + 1;
+    }
+    t->s2_coef = dalloc<float2>(h, (size_t)nt * g.S * g.nz * T, &st);
+    if (st != RCA_OK) return st;
+    cudaMemcpyAsync(t->s2_tmin, tmin.data(), tmin.size() * 4, cudaMemcpyHostToDevice, s);
+    k_tables_coef<<<(nt * g.S * g.nz + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_tmin, T, t->s2_coef,
+                                                                 h->d_status);
+    if ((st = cuda_check(h, cudaGetLastError(), "coef kernel")) != RCA_OK) return st;
+
+    // Stage-1 chunks: row tiles of zt slice rows, lateral distances in chunks
+    // of dc; each chunk's sample window is contiguous in the [ns][E] IQ block.
+    auto plan = [&](int zt, int dc, std::vector<int4>* out) {
+        int tiles = (g.nzs + zt - 1) / zt, nch = (g.N + dc - 1) / dc, win = 0;
+        if (out) out->assign((size_t)nt * tiles * nch, make_int4(0, 0, 0, 0));
+        for (int k = 0; k < nt; ++k)
+            for (int tt = 0; tt < tiles; ++tt)
+                for (int c = 0; c < nch; ++c) {
+                    int d0 = c * dc, d1 = std::min(g.N, d0 + dc);
+                    long lo = 1L << 40, hi = -(1L << 40);
+                    for (int r = tt * zt; r < std::min(g.nzs, (tt + 1) * zt); ++r) {
+                        if (dm[r] < d0) continue;
+                        long tq = txq[(size_t)k * g.nzs + r];
+                        lo = std::min(lo, (tq + rxq[(size_t)r * g.N + d0]) >> 16);
+                        hi = std::max(hi, (tq + rxq[(size_t)r * g.N + std::min(d1 - 1, dm[r])]) >> 16);
+                    }
+                    int nrows = hi >= lo ? (int)(hi - lo + 2) : 0;
+                    win = std::max(win, nrows);
+                    if (out) (*out)[((size_t)k * tiles + tt) * nch + c] = make_int4((int)lo, nrows, d0, d1);
+                }
+        return win;
+    };
+    const size_t budget = 72 * 1024;
+    int zt = 16, dc = 16;
+    while ((size_t)plan(zt, dc, nullptr) * g.N * sizeof(float2) > budget && (zt > 2 || dc > 2)) {
+        if (dc >= zt && dc > 2) dc /= 2;
+        else zt /= 2;
+    }
+    std::vector<int4> chunks;
+    t->s1.zt = zt;
+    t->s1.dc = dc;
+    t->s1.win = plan(zt, dc, &chunks);
+    t->s1.n_tiles = (g.nzs + zt - 1) / zt;
+    t->s1.nch = (g.N + dc - 1) / dc;
+    if ((size_t)t->s1.win * g.N * sizeof(float2) > 200 * 1024)
+        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 sample window of %d samples x %d elements exceeds shared memory",
+                         t->s1.win, g.N);
+    t->s1.d_chunks = dalloc<int4>(h, chunks.size(), &st);
+    if (st != RCA_OK) return st;
+    cudaMemcpyAsync(t->s1.d_chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+
+    // Stage-2 plane-row tile.
+    int span = std::max(t->s2.smax[0] - t->s2.smin[0], t->s2.smax[1] - t->s2.smin[1]) + 2;
+    int zp = 16;
+    auto s2_bytes = [&](int z) {
+        int rows = g.us * (z - 1) + span;
+        return (size_t)g.K * rows * g.N * sizeof(float2) + (size_t)g.K * g.S * rows * sizeof(float2);
+    };
+    while (zp > 1 && s2_bytes(zp) > budget) zp /= 2;
+    t->s2.zp = zp;
+    t->s2.rows = g.us * (zp - 1) + span;
+    t->s2.n_tiles = (g.nz + zp - 1) / zp;
+    if (s2_bytes(zp) > 200 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 tile exceeds shared memory");
+
+    // Direct mode windows (per transverse position; rows of plane depth).
+    {
+        int dzt = 16, win = 0;
+        for (;;) {
+            win = 0;
+            int tiles = (g.nz + dzt - 1) / dzt;
+            for (int k = 0; k < nt; ++k)
+                for (int m = 0; m < g.N; ++m)
+                    for (int tt = 0; tt < tiles; ++tt) {
+                        long lo = 1L << 40, hi = -(1L << 40);
+                        for (int i = tt * dzt; i < std::min(g.nz, (tt + 1) * dzt); ++i) {
+                            int r = i * g.us;
+                            long tq = dtx[((size_t)k * g.N + m) * g.nz + i];
+                            lo = std::min(lo, (tq + rxq[(size_t)r * g.N]) >> 16);
+                            hi = std::max(hi, (tq + rxq[(size_t)r * g.N + std::max(0, dm[r])]) >> 16);
+                        }
+                        win = std::max(win, (int)(hi - lo + 2));
+                    }
+            if ((size_t)win * g.N * sizeof(float2) <= budget || dzt == 1) break;
+            dzt /= 2;
+        }
+        t->direct_zt = dzt;
+        t->direct_win = win;
+    }
+    return cuda_check(h, cudaStreamSynchronize(s), "table build");
+}

@@ -1,0 +1,190 @@
+"""Python binding of librca with the C names (include/rca.h).
+
+Argument marshalling only: buffers are torch tensors (or raw integer device
+pointers), passed by address; every computation runs in librca's kernels.
+Non-zero statuses raise :class:`RcaError` carrying rca_last_error().
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import LOC2D, LOC3D, rca_bf_params, rca_geometry_desc, ulm_params  # noqa: F401
+
+
+class RcaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)} ({status}): {message}")
+        self.status = status
+
+
+def _status_name(s: int) -> str:
+    return L.load().rca_status_string(s).decode()
+
+
+def _check(st: int, h=None, what: str = ""):
+    if st != L.RCA_OK:
+        msg = L.load().rca_last_error(h).decode() if h is not None else what
+        raise RcaError(st, msg or what)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, C.c_void_p):
+        return x
+    return C.c_void_p(int(x))
+
+
+def rca_version() -> int:
+    return L.load().rca_version()
+
+
+def rca_status_string(s: int) -> str:
+    return _status_name(s)
+
+
+def rca_create(device: int = 0):
+    h = C.c_void_p()
+    _check(L.load().rca_create(C.byref(h), device), None, f"rca_create(device={device})")
+    return h
+
+
+def rca_destroy(h):
+    _check(L.load().rca_destroy(h), None, "rca_destroy")
+
+
+def rca_set_stream(h, stream=None):
+    """stream: torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default)."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(L.load().rca_set_stream(h, C.c_void_p(raw) if raw else None), h)
+
+
+def rca_last_error(h) -> str:
+    return L.load().rca_last_error(h).decode()
+
+
+def rca_sync_status(h) -> int:
+    dev = C.c_int(0)
+    _check(L.load().rca_sync_status(h, C.byref(dev)), h)
+    return dev.value
+
+
+def rca_reserve(h, g, n_frames: int):
+    _check(L.load().rca_reserve(h, g, n_frames), h)
+
+
+def geometry_desc(geom):
+    """rca_geometry_desc from any object with the geometry attributes
+    (n_el, nz, ns, P, K, us, pitch, fc, fs, c, z0, dz, fnum, ang_rc, ang_cr).
+    Returns (desc, keep-alive arrays)."""
+    rc = np.ascontiguousarray(geom.ang_rc, dtype=np.float64)
+    cr = np.ascontiguousarray(geom.ang_cr, dtype=np.float64)
+    d = rca_geometry_desc()
+    d.n_el, d.nz, d.ns, d.P, d.K, d.us = geom.n_el, geom.nz, geom.ns, geom.P, len(rc), geom.us
+    d.pitch_m, d.fc_hz, d.fs_hz, d.c_mps = geom.pitch, geom.fc, geom.fs, geom.c
+    d.z0_m, d.dz_m, d.fnum = geom.z0, geom.dz, geom.fnum
+    d.ang_rc_rad = rc.ctypes.data_as(C.POINTER(C.c_double))
+    d.ang_cr_rad = cr.ctypes.data_as(C.POINTER(C.c_double))
+    return d, (rc, cr)
+
+
+def rca_geometry_create(h, geom):
+    d, keep = geometry_desc(geom)
+    g = C.c_void_p()
+    _check(L.load().rca_geometry_create(h, C.byref(d), C.byref(g)), h)
+    del keep
+    return g
+
+
+def rca_geometry_destroy(g):
+    L.load().rca_geometry_destroy(g)
+
+
+def rca_delay_tables(h, g):
+    t = C.c_void_p()
+    _check(L.load().rca_delay_tables(h, g, C.byref(t)), h)
+    return t
+
+
+def rca_tables_destroy(t):
+    L.load().rca_tables_destroy(t)
+
+
+_TABLE_DTYPE = {
+    L.RCA_TAB_TX_F64: np.float64, L.RCA_TAB_RX_F64: np.float64, L.RCA_TAB_TX_Q16: np.int32,
+    L.RCA_TAB_RX_Q16: np.int32, L.RCA_TAB_W: np.complex64, L.RCA_TAB_DMAX: np.int32,
+    L.RCA_TAB_S2_SHIFT: np.float64, L.RCA_TAB_S2_PSI: np.complex64, L.RCA_TAB_S2_EC: np.complex64,
+    L.RCA_TAB_S2_COEF: np.complex64, L.RCA_TAB_S2_TMIN: np.int32,
+}
+
+
+def rca_tables_query(t, table_id: int):
+    nbytes = C.c_size_t(0)
+    dims = (C.c_int * 4)()
+    _check(L.load().rca_tables_query(t, table_id, C.byref(nbytes), dims), None, "rca_tables_query")
+    return nbytes.value, tuple(d for d in dims if d)
+
+
+def rca_tables_download(t, table_id: int) -> np.ndarray:
+    nbytes, dims = rca_tables_query(t, table_id)
+    out = np.zeros(dims, dtype=_TABLE_DTYPE[table_id])
+    assert out.nbytes == nbytes, (out.nbytes, nbytes)
+    _check(L.load().rca_tables_download(t, table_id, out.ctypes.data_as(C.c_void_p), nbytes), None,
+           "rca_tables_download")
+    return out
+
+
+def rca_ingest(h, t, rf, rf_dtype, scale, n_frames, clutter, iq, iq_dtype):
+    _check(L.load().rca_ingest(h, t, _ptr(rf), rf_dtype, _ptr(scale), n_frames, clutter, _ptr(iq), iq_dtype), h)
+
+
+def rca_stage1(h, t, iq, iq_dtype, n_frames, slices):
+    _check(L.load().rca_stage1(h, t, _ptr(iq), iq_dtype, n_frames, _ptr(slices)), h)
+
+
+def rca_stage2_project(h, t, slices, n_frames, planes, planes_dtype):
+    _check(L.load().rca_stage2_project(h, t, _ptr(slices), n_frames, _ptr(planes), planes_dtype), h)
+
+
+def rca_direct_project(h, t, iq, iq_dtype, n_frames, planes, planes_dtype):
+    _check(L.load().rca_direct_project(h, t, _ptr(iq), iq_dtype, n_frames, _ptr(planes), planes_dtype), h)
+
+
+def bf_params(mode=L.RCA_MODE_TWO_STAGE, clutter=L.RCA_CLUTTER_MEAN, iq_dtype=L.RCA_C32) -> rca_bf_params:
+    p = rca_bf_params()
+    p.mode, p.clutter, p.iq_dtype = mode, clutter, iq_dtype
+    return p
+
+
+def rca_beamform_projections(h, t, rf, rf_dtype, scale, n_frames, prm: rca_bf_params, planes, planes_dtype):
+    _check(L.load().rca_beamform_projections(h, t, _ptr(rf), rf_dtype, _ptr(scale), n_frames, C.byref(prm),
+                                             _ptr(planes), planes_dtype), h)
+
+
+def make_ulm_params(d=5, sig_z=1.0, sig_lat=1.0, alpha=0.1, ncc_min=0.5, enh=L.ULM_ENH_XDOPPLER) -> ulm_params:
+    p = ulm_params()
+    p.d, p.sig_z, p.sig_lat, p.alpha, p.ncc_min, p.enh = d, sig_z, sig_lat, alpha, ncc_min, enh
+    return p
+
+
+def ulm_enhance(h, t, planes, planes_dtype, n_frames, enh, A, M):
+    _check(L.load().ulm_enhance(h, t, _ptr(planes), planes_dtype, n_frames, enh, _ptr(A), _ptr(M)), h)
+
+
+def ulm_detect2d(h, t, A, M, n_frames, prm: ulm_params, out2d, cap2d, n2d, ncc_out=None, plane_offsets=None):
+    _check(L.load().ulm_detect2d(h, t, _ptr(A), _ptr(M), n_frames, C.byref(prm), _ptr(out2d), cap2d, _ptr(n2d),
+                                 _ptr(ncc_out), _ptr(plane_offsets)), h)
+
+
+def ulm_pair3d(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
+    _check(L.load().ulm_pair3d(h, t, _ptr(list2d), _ptr(n2d), cap2d, n_frames, _ptr(out3d), cap3d, _ptr(n3d)), h)
+
+
+def ulm_localize(h, t, planes, planes_dtype, n_frames, prm: ulm_params, out2d, cap2d, n2d, out3d, cap3d, n3d):
+    _check(L.load().ulm_localize(h, t, _ptr(planes), planes_dtype, n_frames, C.byref(prm), _ptr(out2d), cap2d,
+                                 _ptr(n2d), _ptr(out3d), cap3d, _ptr(n3d)), h)
