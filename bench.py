@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=4)
+    ap.add_argument("--frames", type=int, default=0, help="override the ensemble length (profiling runs)")
     return ap.parse_args()
 
 
@@ -164,6 +165,8 @@ def main():
     from synth import generate, quantize_int16, workload
 
     w = workload(args.workload, seed=workload(args.workload).seed + rank)
+    if args.frames:
+        w = workload(args.workload, seed=w.seed, n_frames=args.frames)
     g = w.geom
     F = w.n_frames
     t_gen = time.time()
