@@ -191,6 +191,7 @@ extern "C" rca_status rca_geometry_create(rca_handle* h, const rca_geometry_desc
     if (d->us > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "us = %d > 8", d->us);
     if (d->n_el % d->P != 0) return set_error(h, RCA_ERR_INVALID_ARG, "n_el %% P != 0");
     if (d->n_el > 256) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256");
+    if (d->n_el % 4 != 0) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el must be a multiple of 4 (16-byte sample rows)");
     if ((long)d->ns * 65536L >= (1L << 31)) return set_error(h, RCA_ERR_UNSUPPORTED, "ns too large for Q16 delays");
     if (!(d->pitch_m > 0) || !(d->fc_hz > 0) || !(d->fs_hz > 0) || !(d->c_mps > 0) || !(d->dz_m > 0) || !(d->fnum > 0) ||
         !(d->z0_m > 0))

@@ -25,29 +25,71 @@ __device__ __forceinline__ float rf_value(const void* rf, int rf_t, size_t i)
 // exp(-j 2 pi fc t_n) and the half-band low-pass (x2).
 // ---------------------------------------------------------------------------
 
-// One thread per (tx, element, sample) column; frames are strided by ncol.
-// float / half input: Neumaier-compensated float sum; int16: exact integer sum.
-__global__ void k_mean(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale, int F, int ns,
-                       int ncol, float* __restrict__ mean)
+// Four adjacent (tx, element, sample) columns per thread; frames strided by
+// ncol, loaded four frames at a time.  float / half input: Neumaier-
+// compensated float sums; int16: exact integer sums.
+__device__ __forceinline__ void rf_load4(const void* rf, int rf_t, size_t i, float v[4])
 {
-    int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncol) return;
+    if (rf_t == RCA_F32) {
+        float4 x = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(rf) + i));
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if (rf_t == RCA_F16) {
+        uint2 x = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __half*>(rf) + i));
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&x.x)), b = __half22float2(*reinterpret_cast<__half2*>(&x.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+        uint2 x = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const int16_t*>(rf) + i));
+        v[0] = (float)(short)(x.x & 0xffff); v[1] = (float)(short)(x.x >> 16);
+        v[2] = (float)(short)(x.y & 0xffff); v[3] = (float)(short)(x.y >> 16);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mean(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
+                                              int F, int ns, int ncol, float* __restrict__ mean)
+{
+    const int c4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c4 >= ncol) return;
     const size_t stride = (size_t)ncol;
-    if (rf_t == RCA_I16) {
-        const int16_t* q = reinterpret_cast<const int16_t*>(rf);
-        long long acc = 0;
-        for (int f = 0; f < F; ++f) acc += q[(size_t)f * stride + col];
-        mean[col] = (float)((double)acc / (double)F * (double)scale[col / ns]);
-        return;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+    long long qs[4] = {0, 0, 0, 0};
+    int f = 0;
+    for (; f + 4 <= F; f += 4) {
+        float v[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rf_load4(rf, rf_t, (size_t)(f + u) * stride + c4, v[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (rf_t == RCA_I16) {
+                    qs[j] += (long long)v[u][j];
+                } else {
+                    const float x = v[u][j], tt = s[j] + x;
+                    cmp[j] += (fabsf(s[j]) >= fabsf(x)) ? ((s[j] - tt) + x) : ((x - tt) + s[j]);
+                    s[j] = tt;
+                }
+            }
     }
-    float s = 0.f, c = 0.f;
-    for (int f = 0; f < F; ++f) {
-        float x = rf_value(rf, rf_t, (size_t)f * stride + col);
-        float t = s + x;
-        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
-        s = t;
+    for (; f < F; ++f) {
+        float v[4];
+        rf_load4(rf, rf_t, (size_t)f * stride + c4, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (rf_t == RCA_I16) {
+                qs[j] += (long long)v[j];
+            } else {
+                const float x = v[j], tt = s[j] + x;
+                cmp[j] += (fabsf(s[j]) >= fabsf(x)) ? ((s[j] - tt) + x) : ((x - tt) + s[j]);
+                s[j] = tt;
+            }
+        }
     }
-    mean[col] = (s + c) / (float)F;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = c4 + j;
+        mean[col] = (rf_t == RCA_I16) ? (float)((double)qs[j] / (double)F * (double)scale[col / ns])
+                                      : (s[j] + cmp[j]) / (float)F;
+    }
 }
 
 #define DM_NT 128           // samples per CTA
@@ -66,6 +108,7 @@ __global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int 
     const int fk = blockIdx.z;
     const int k = fk % nt;
     const size_t chan0 = (size_t)fk * E;
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < DM_NE * (DM_NT + 30); idx += blockDim.x) {
         int el = idx / (DM_NT + 30), s = idx - el * (DM_NT + 30);
         int n = n0 - 15 + s, e = e0 + el;
@@ -102,82 +145,217 @@ __global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int 
 //   xi = (tx_q16[k][r] + rx_q16[r][d]) / 2^16 samples.
 // For a fixed (r, d) the sample position is the same for every lateral pixel,
 // so each warp (32 consecutive pixels) reads 32 consecutive elements of one
-// sample row: the delay, its fraction and the weight are warp-uniform.
+// sample row of the [ns][E] IQ block: the delay, its fraction and the weight
+// are warp-uniform and are precomputed per (row, d) once per chunk.  The
+// chunk's sample window is one contiguous block of the IQ array, fetched by a
+// TMA bulk copy into a double buffer while the previous chunk is processed.
 // ---------------------------------------------------------------------------
-template <int MAXR>
-__global__ void __launch_bounds__(256) k_stage1(GeomDev g, const void* __restrict__ iq, int iq_t,
-                                                    const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
-                                                    const float2* __restrict__ W, const int* __restrict__ dmax,
-                                                    const int4* __restrict__ chunks, int zt, int n_tiles, int nch,
-                                                    float2* __restrict__ slices)
+// per-(row, d) record, 32 bytes: the interpolation fraction and the
+// apodised carrier weight (0 where the delay leaves the record) duplicated
+// into packed pairs, and the element offset of the sample row in the window
+struct __align__(16) RowD {
+    float fr0, fr1;  // fraction, fraction
+    float wx0, wx1;  // Re w, Re w
+    float wy0, wy1;  // Im w, Im w
+    int off;         // sample row * E
+    int pad;
+};
+
+// one complex IQ sample from shared memory (byte address) as a packed float pair
+template <typename TS>
+__device__ __forceinline__ uint64_t ld_sa(unsigned addr);
+template <>
+__device__ __forceinline__ uint64_t ld_sa<float2>(unsigned addr) { return lds_u64(addr); }
+template <>
+__device__ __forceinline__ uint64_t ld_sa<__half2>(unsigned addr)
 {
-    extern __shared__ float2 sw[];  // [nrows][E]
+    unsigned u = lds_u32(addr);
+    const float2 v = __half22float2(*reinterpret_cast<__half2*>(&u));
+    return f2_pack(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ uint64_t ld_sa<__nv_bfloat162>(unsigned addr)
+{
+    unsigned u = lds_u32(addr);
+    // bf16 -> f32 is a 16-bit shift of each half
+    return f2_pack(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+// one complex IQ sample (shared memory) as a packed float pair
+template <typename TS>
+__device__ __forceinline__ uint64_t ld_sp(const unsigned char* p);
+template <>
+__device__ __forceinline__ uint64_t ld_sp<float2>(const unsigned char* p) { return *reinterpret_cast<const uint64_t*>(p); }
+template <>
+__device__ __forceinline__ uint64_t ld_sp<__half2>(const unsigned char* p)
+{
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+    return f2_pack(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ uint64_t ld_sp<__nv_bfloat162>(const unsigned char* p)
+{
+    const unsigned u = *reinterpret_cast<const unsigned*>(p);
+    return f2_pack(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+// v = b0 + fr (b1 - b0);  A1 += wx * v;  A2 += wy * v   (all packed pairs).
+// The complex product w * v is recovered at the end as
+// (A1.x - A2.y, A1.y + A2.x).
+template <typename TS>
+__device__ __forceinline__ void lerp_acc2(uint64_t& A1, uint64_t& A2, unsigned a0, unsigned rowbytes, uint64_t frp,
+                                          uint64_t wxp, uint64_t wyp)
+{
+    const uint64_t b0 = ld_sa<TS>(a0), b1 = ld_sa<TS>(a0 + rowbytes);
+    const uint64_t v = f2_fma(frp, f2_sub(b1, b0), b0);
+    A1 = f2_fma(wxp, v, A1);
+    A2 = f2_fma(wyp, v, A2);
+}
+
+template <typename TS, int MAXR>
+__global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __restrict__ iq,
+                                                const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
+                                                const float2* __restrict__ W, const int* __restrict__ dmax,
+                                                const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch,
+                                                int win, float2* __restrict__ slices, unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint64_t bars[2];
     const int E = g.N, N = g.N;
+    TS* bufs = reinterpret_cast<TS*>(smraw);                  // [2][win][E]
+    RowD* recs = reinterpret_cast<RowD*>(bufs + 2 * (size_t)win * E);  // [2][zt][dc]
+    int* dcnt = reinterpret_cast<int*>(recs + 2 * zt * dc);  // [2][zt]
     const int tile = blockIdx.x, k = blockIdx.y, f = blockIdx.z;
     const int nt = 2 * g.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int LW = (N + 31) >> 5;
     const int RG = (blockDim.x >> 5) / LW;
     const int lw = warp % LW, rg = warp / LW;
-    const int l = lw * 32 + lane;
+    const int lb = lw * 32;
+    const int l = lb + lane;
     const int r0 = tile * zt;
     const int rend = min(r0 + zt, g.nzs);
-    float2 acc[MAXR];
-#pragma unroll
-    for (int j = 0; j < MAXR; ++j) acc[j] = make_float2(0.f, 0.f);
-    const size_t blk = ((size_t)f * nt + k) * g.ns;
     const int qmax = (g.ns - 1) << 16;
     const int4* ch = chunks + ((size_t)k * n_tiles + tile) * nch;
-    for (int c = 0; c < nch; ++c) {
-        const int4 cc = ch[c];  // {nlo, nrows, d0, d1}
-        if (cc.y == 0) continue;
-        __syncthreads();
-        const int total = cc.y * E;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int rr = idx / E, e = idx - rr * E;
-            int n = cc.x + rr;
-            float2 v = make_float2(0.f, 0.f);
-            if (n >= 0 && n < g.ns) v = load_c(iq, (blk + n) * E + e, iq_t);
-            sw[idx] = v;
+    const TS* blk = reinterpret_cast<const TS*>(iq) + ((size_t)f * nt + k) * g.ns * E;
+    const TS zero = TS();
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // zero the window rows outside the record, then (thread 0) bulk-copy the rest
+    auto issue = [&](int c, int b) {
+        const int4 cc = ch[c];
+        TS* dst = bufs + (size_t)b * win * E;
+        const int lo = max(cc.x, 0), hi = max(lo, min(cc.x + cc.y, g.ns));
+        const int z0 = min(lo - cc.x, cc.y), z1 = hi - cc.x;
+        for (int idx = threadIdx.x; idx < z0 * E; idx += blockDim.x) dst[idx] = zero;
+        for (int idx = threadIdx.x; idx < (cc.y - z1) * E; idx += blockDim.x) dst[(size_t)z1 * E + idx] = zero;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            const unsigned bytes = (unsigned)((hi - lo) * E * sizeof(TS));
+            mbar_arrive_expect_tx(&bars[b], bytes);
+            if (bytes) bulk_g2s(dst + (size_t)(lo - cc.x) * E, blk + (size_t)lo * E, bytes, &bars[b]);
         }
-        __syncthreads();
+    };
+
+    uint64_t acc1[MAXR], acc2[MAXR];
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) acc1[j] = acc2[j] = 0ull;
+    unsigned phase = 0;
+    issue(0, 0);
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        const int4 cc = ch[c];
+        RowD* rc = recs + b * zt * dc;
+        for (int idx = threadIdx.x; idx < zt * dc; idx += blockDim.x) {
+            const int rr = idx / dc, dd = idx - rr * dc;
+            const int r = r0 + rr, d = cc.z + dd;
+            RowD rec;
+            rec.off = 0;
+            rec.pad = 0;
+            rec.fr0 = rec.fr1 = rec.wx0 = rec.wx1 = rec.wy0 = rec.wy1 = 0.f;
+            if (r < rend && d < cc.w && d <= __ldg(dmax + r)) {
+                const int q = __ldg(tx_q16 + (size_t)k * g.nzs + r) + __ldg(rx_q16 + (size_t)r * N + d);
+                if (q >= 0 && q <= qmax) {
+                    const float2 w = __ldg(W + (size_t)r * N + d);
+                    rec.off = ((q >> 16) - cc.x) * E * (int)sizeof(TS);   // byte offset of the row
+                    rec.fr0 = rec.fr1 = (float)(q & 0xffff) * (1.0f / 65536.0f);
+                    rec.wx0 = rec.wx1 = w.x;
+                    rec.wy0 = rec.wy1 = w.y;
+                }
+            }
+            rc[idx] = rec;
+        }
+        for (int rr = threadIdx.x; rr < zt; rr += blockDim.x) {
+            const int r = r0 + rr;
+            dcnt[b * zt + rr] = r < rend ? max(0, min(cc.w, __ldg(dmax + r) + 1) - cc.z) : 0;
+        }
+        if (!cta_wait_copies(&bars[b], (phase >> b) & 1u, status)) return;
+        phase ^= 1u << b;
+        if (c + 1 < nch) issue(c + 1, b ^ 1);
+        if (cc.y == 0) continue;
+        const unsigned char* wbase = reinterpret_cast<const unsigned char*>(bufs + (size_t)b * win * E);
+        const int rowbytes = E * (int)sizeof(TS);
+        const int lim1 = lb + 31 - cc.z;     // warp-uniform: e = l - d reachable for dd <= lim1
+        const int lim2 = N - 1 - lb - cc.z;  // warp-uniform: e = l + d reachable for dd <= lim2
+        const int L1 = l - cc.z;             // this lane: e = l - d >= 0 for dd <= L1
+        const int L2 = N - 1 - l - cc.z;     // this lane: e = l + d < N for dd <= L2
+        // the thread's rows advance together: each d step updates MAXR
+        // independent accumulators (records past a row's aperture have w = 0);
+        // lanes outside the element range load zeros instead of branching
+        int ndw = 0;
 #pragma unroll
         for (int j = 0; j < MAXR; ++j) {
-            const int r = r0 + rg + j * RG;
-            if (r < rend) {
-                const int tq = __ldg(tx_q16 + (size_t)k * g.nzs + r);
-                const int dend = min(cc.w, __ldg(dmax + r) + 1);
-                const int* rxr = rx_q16 + (size_t)r * N;
-                const float2* wr = W + (size_t)r * N;
-                float2 a = acc[j];
-                for (int d = cc.z; d < dend; ++d) {
-                    const int q = tq + __ldg(rxr + d);
-                    if (q < 0 || q > qmax) continue;
-                    const int n = (q >> 16) - cc.x;
-                    const float fr = (float)(q & 0xffff) * (1.0f / 65536.0f);
-                    const float2 w = __ldg(wr + d);
-                    const float2* row0 = sw + n * E;
-                    const int e1 = l - d;
-                    if (e1 >= 0 && l < N) {
-                        float2 b0 = row0[e1], b1 = row0[E + e1];
-                        float2 v = make_float2(fmaf(fr, b1.x - b0.x, b0.x), fmaf(fr, b1.y - b0.y, b0.y));
-                        cfma(a, w, v);
+            const int rr = rg + j * RG;
+            if (rr < zt) ndw = max(ndw, dcnt[b * zt + rr]);
+        }
+        const int n1 = min(ndw, lim1 + 1);
+        const int s2 = cc.z == 0 ? 1 : 0;   // d = 0 is counted once
+        const int n2 = min(ndw, lim2 + 1);
+        const int nmax = max(n1, n2);
+        for (int dd = 0; dd < nmax; ++dd) {
+            const bool h1 = dd < n1 && dd <= L1 && l < N;
+            const bool h2 = dd >= s2 && dd < n2 && dd <= L2;
+            const int o1 = (L1 - dd) * (int)sizeof(TS);
+            const int o2 = (l + cc.z + dd) * (int)sizeof(TS);
+#pragma unroll
+            for (int j = 0; j < MAXR; ++j) {
+                const int rr = rg + j * RG;
+                if (rr < zt) {
+                    const ulonglong2* rp = reinterpret_cast<const ulonglong2*>(rc + rr * dc + dd);
+                    const ulonglong2 ra = rp[0], rb = rp[1];   // {fr, fr | wx, wx}, {wy, wy | off}
+                    const unsigned char* row = wbase + (int)(unsigned)rb.y;
+                    uint64_t x0 = 0ull, x1 = 0ull, y0 = 0ull, y1 = 0ull;
+                    if (h1) {
+                        x0 = ld_sp<TS>(row + o1);
+                        x1 = ld_sp<TS>(row + o1 + rowbytes);
                     }
-                    const int e2 = l + d;
-                    if (d > 0 && e2 < E) {
-                        float2 b0 = row0[e2], b1 = row0[E + e2];
-                        float2 v = make_float2(fmaf(fr, b1.x - b0.x, b0.x), fmaf(fr, b1.y - b0.y, b0.y));
-                        cfma(a, w, v);
+                    if (h2) {
+                        y0 = ld_sp<TS>(row + o2);
+                        y1 = ld_sp<TS>(row + o2 + rowbytes);
                     }
+                    const uint64_t v1 = f2_fma(ra.x, f2_sub(x1, x0), x0);
+                    const uint64_t v2 = f2_fma(ra.x, f2_sub(y1, y0), y0);
+                    acc1[j] = f2_fma(ra.y, v1, acc1[j]);
+                    acc2[j] = f2_fma(rb.x, v1, acc2[j]);
+                    acc1[j] = f2_fma(ra.y, v2, acc1[j]);
+                    acc2[j] = f2_fma(rb.x, v2, acc2[j]);
                 }
-                acc[j] = a;
             }
         }
     }
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) {
         const int r = r0 + rg + j * RG;
-        if (r < rend && l < N) slices[(((size_t)f * nt + k) * g.nzs + r) * N + l] = acc[j];
+        if (r < rend && (rg + j * RG) < zt && l < N) {
+            const float2 p1 = f2_unpack(acc1[j]), p2 = f2_unpack(acc2[j]);
+            slices[(((size_t)f * nt + k) * g.nzs + r) * N + l] = make_float2(p1.x - p2.y, p1.y + p2.x);
+        }
     }
 }
 
@@ -192,76 +370,165 @@ __global__ void __launch_bounds__(256) k_stage1(GeomDev g, const void* __restric
 // RC: transverse = y -> XZ planes (axis 0), lateral-slab -> YZ (axis 1).
 // CR: transverse = x -> YZ planes (axis 1), lateral-slab -> XZ (axis 0).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_stage2(GeomDev g, const float2* __restrict__ slices,
+template <int ZP>
+__global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restrict__ slices,
                                                 const int* __restrict__ sfl, const float* __restrict__ sfr,
                                                 const float2* __restrict__ psi, const float2* __restrict__ ec,
                                                 const float2* __restrict__ coef, const int* __restrict__ tmin, int T,
-                                                int zp, int rows, int smin0, int smin1, void* __restrict__ planes,
-                                                int pt)
+                                                int rows, int smin0, int smin1, void* __restrict__ planes, int pt,
+                                                unsigned* __restrict__ status)
 {
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
+    __shared__ uint64_t bar;
     const int N = g.N, K = g.K, S = g.S, P = g.P, us = g.us;
     const int tile = blockIdx.x, fam = blockIdx.y, f = blockIdx.z;
     const int nt = 2 * K;
-    const int i0 = tile * zp;
-    const int iend = min(i0 + zp, g.nz);
-    const int rlo = us * i0 + (fam ? smin1 : smin0);
-    float2* sS = sm;                            // [K][rows][N]
-    float2* sSum = sm + (size_t)K * rows * N;   // [K][S][rows]
-    for (int idx = threadIdx.x; idx < K * rows * N; idx += blockDim.x) {
-        int kk = idx / (rows * N), rr = (idx / N) % rows, l = idx % N;
-        int row = rlo + rr;
-        float2 v = make_float2(0.f, 0.f);
-        if (row >= 0 && row < g.nzs) v = slices[(((size_t)f * nt + fam * K + kk) * g.nzs + row) * N + l];
-        sS[idx] = v;
+    const int i0 = tile * ZP;
+    const int nrow = min(ZP, g.nz - i0);
+    const int smin = fam ? smin1 : smin0;
+    const int rlo = us * i0 + smin;
+    float2* sS = sm;                                 // [K][rows][N]
+    float2* sSum = sS + (size_t)K * rows * N;        // [K][S][rows]
+    float2* sCoef = sSum + (size_t)K * S * rows;     // [K][S][ZP][T]
+    float2* sPsi = sCoef + (size_t)K * S * ZP * T;   // [K][N]
+    float2* sEc = sPsi + (size_t)K * N;              // [K][ZP]
+    float* sSfr = reinterpret_cast<float*>(sEc + (size_t)K * ZP);  // [K][N]
+    int* sSfl = reinterpret_cast<int*>(sSfr + (size_t)K * N);       // [K][N]  (row offset - smin)
+    int* sTb = sSfl + (size_t)K * N;                                 // [K][S]  (tmin - smin)
+    const int lo = max(rlo, 0), hi = max(lo, min(rlo + rows, g.nzs));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < K * S * rows; idx += blockDim.x) {
-        int kk = idx / (S * rows), b = (idx / rows) % S, rr = idx % rows;
-        const float2* src = sS + ((size_t)kk * rows + rr) * N + b * P;
-        float2 a = make_float2(0.f, 0.f);
-        for (int q = 0; q < P; ++q) {
-            a.x += src[q].x;
-            a.y += src[q].y;
+    {
+        const int z0 = min(lo - rlo, rows), z1 = hi - rlo;
+        const int nzr = z0 + (rows - z1);
+        for (int idx = threadIdx.x; idx < K * nzr * N; idx += blockDim.x) {
+            const int kk = idx / (nzr * N), q = idx - kk * nzr * N, zr = q / N, l = q - zr * N;
+            const int rr = zr < z0 ? zr : z1 + (zr - z0);
+            sS[((size_t)kk * rows + rr) * N + l] = make_float2(0.f, 0.f);
         }
-        sSum[idx] = a;
+    }
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        const unsigned bytes = (unsigned)((hi - lo) * N * sizeof(float2));
+        mbar_arrive_expect_tx(&bar, bytes * K);
+        if (bytes)
+            for (int kk = 0; kk < K; ++kk)
+                bulk_g2s(sS + ((size_t)kk * rows + (lo - rlo)) * N,
+                         slices + (((size_t)f * nt + fam * K + kk) * g.nzs + lo) * N, bytes, &bar);
+    }
+    // per-CTA table slices while the copy is in flight
+    for (int idx = threadIdx.x; idx < K * S * ZP * T; idx += blockDim.x) {
+        const int t = idx % T, ii = (idx / T) % ZP, kb = idx / (T * ZP);
+        const int kk = kb / S, b = kb % S, i = min(i0 + ii, g.nz - 1);
+        sCoef[idx] = __ldg(coef + (((size_t)(fam * K + kk) * S + b) * g.nz + i) * T + t);
+    }
+    for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
+        const int k = fam * K + idx / N, u = idx % N;
+        sPsi[idx] = __ldg(psi + (size_t)k * N + u);
+        sSfr[idx] = __ldg(sfr + (size_t)k * N + u);
+        sSfl[idx] = __ldg(sfl + (size_t)k * N + u) - smin;
+    }
+    for (int idx = threadIdx.x; idx < K * ZP; idx += blockDim.x) {
+        const int kk = idx / ZP, ii = idx % ZP;
+        sEc[idx] = __ldg(ec + (size_t)(fam * K + kk) * g.nz + min(i0 + ii, g.nz - 1));
+    }
+    for (int idx = threadIdx.x; idx < K * S; idx += blockDim.x) sTb[idx] = __ldg(tmin + fam * K * S + idx) - smin;
+    if (!cta_wait_copies(&bar, 0, status)) return;
+    // slab sums over the lateral pixels: one warp per (k, row)
+    for (int o = warp; o < K * rows; o += nwarp) {
+        const int kk = o / rows, rr = o - kk * rows;
+        const float2* src = sS + ((size_t)kk * rows + rr) * N;
+        if ((32 % P) == 0) {
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                const int l = c0 + lane;
+                float2 v = l < N ? src[l] : make_float2(0.f, 0.f);
+                for (int m = 1; m < P; m <<= 1) {
+                    v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+                    v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+                }
+                if ((lane % P) == 0 && l < N) sSum[((size_t)kk * S + l / P) * rows + rr] = v;
+            }
+        } else {
+            for (int b = lane; b < S; b += 32) {
+                float2 a = make_float2(0.f, 0.f);
+                for (int q = 0; q < P; ++q) {
+                    a.x += src[b * P + q].x;
+                    a.y += src[b * P + q].y;
+                }
+                sSum[((size_t)kk * S + b) * rows + rr] = a;
+            }
+        }
     }
     __syncthreads();
     const int axT = fam == 0 ? 0 : 1;
     const int axL = 1 - axT;
     const size_t plane_sz = (size_t)g.nz * N;
-    const int nout = S * zp * N;
-    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
-        const int l = idx % N, ii = (idx / N) % zp, b = idx / (N * zp);
-        const int i = i0 + ii;
-        if (i >= iend) continue;
-        float2 acc = make_float2(0.f, 0.f);
+    const int LW = (N + 31) >> 5;
+    // transverse-slab planes: out[b][i][l] = sum_k sum_t coef[k][b][i][t] S_k(l, us i + tmin[k][b] + t)
+    for (int o = warp; o < S * LW; o += nwarp) {
+        const int lw = o % LW, b = o / LW;
+        const int l = lw * 32 + lane, lc = l < N ? l : 0;
+        uint64_t a1[ZP], a2[ZP];
+#pragma unroll
+        for (int ii = 0; ii < ZP; ++ii) a1[ii] = a2[ii] = 0ull;
         for (int kk = 0; kk < K; ++kk) {
-            const int k = fam * K + kk;
-            const int base = us * i + __ldg(tmin + k * S + b) - rlo;
-            const float2* cf = coef + (((size_t)k * S + b) * g.nz + i) * T;
-            const float2* src = sS + ((size_t)kk * rows + base) * N + l;
-            for (int t = 0; t < T; ++t) cfma(acc, __ldg(cf + t), src[(size_t)t * N]);
+            const int tb = sTb[kk * S + b];
+            const float2* cf = sCoef + (size_t)(kk * S + b) * ZP * T;
+            const uint64_t* col = reinterpret_cast<const uint64_t*>(sS + ((size_t)kk * rows + tb) * N + lc);
+            for (int t = 0; t < T; ++t) {
+#pragma unroll
+                for (int ii = 0; ii < ZP; ++ii) {
+                    const float2 c = cf[ii * T + t];
+                    const uint64_t v = col[(size_t)(us * ii + t) * N];
+                    a1[ii] = f2_fma(f2_pack(c.x, c.x), v, a1[ii]);
+                    a2[ii] = f2_fma(f2_pack(c.y, c.y), v, a2[ii]);
+                }
+            }
         }
-        store_c(planes, ((((size_t)f * 2 + axT) * 2 + fam) * S + b) * plane_sz + (size_t)i * N + l, pt, acc);
+        if (l < N) {
+            const size_t ob = ((((size_t)f * 2 + axT) * 2 + fam) * S + b) * plane_sz + (size_t)i0 * N + l;
+#pragma unroll
+            for (int ii = 0; ii < ZP; ++ii) {
+                if (ii < nrow) {
+                    const float2 p1 = f2_unpack(a1[ii]), p2 = f2_unpack(a2[ii]);
+                    store_c_cs(planes, ob + (size_t)ii * N, pt, make_float2(p1.x - p2.y, p1.y + p2.x));
+                }
+            }
+        }
     }
-    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
-        const int u = idx % N, ii = (idx / N) % zp, b = idx / (N * zp);
-        const int i = i0 + ii;
-        if (i >= iend) continue;
-        float2 acc = make_float2(0.f, 0.f);
+    // lateral-slab planes: out[b][i][u] = sum_k ec[k][i] psi[k][u] lerp(sum_{l in b} S_k(l, .), us i + s_k(u))
+    for (int o = warp; o < S * LW; o += nwarp) {
+        const int lw = o % LW, b = o / LW;
+        const int u = lw * 32 + lane;
+        if (u >= N) continue;
+        float2 acc[ZP];
+#pragma unroll
+        for (int ii = 0; ii < ZP; ++ii) acc[ii] = make_float2(0.f, 0.f);
         for (int kk = 0; kk < K; ++kk) {
-            const int k = fam * K + kk;
-            const int n0 = us * i + __ldg(sfl + k * N + u);
-            const float fr = __ldg(sfr + k * N + u);
-            const bool valid = n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f));
-            if (!valid) continue;
-            const float2* src = sSum + ((size_t)kk * S + b) * rows + (n0 - rlo);
-            const float2 s0 = src[0], s1 = src[1];
-            const float2 v = make_float2(fmaf(fr, s1.x - s0.x, s0.x), fmaf(fr, s1.y - s0.y, s0.y));
-            cfma(acc, cmul(__ldg(ec + (size_t)k * g.nz + i), __ldg(psi + (size_t)k * N + u)), v);
+            const int n0r = sSfl[kk * N + u];     // row offset relative to rlo at ii = 0
+            const float fr = sSfr[kk * N + u];
+            const float2 ps = sPsi[kk * N + u];
+            const float2* src = sSum + ((size_t)kk * S + b) * rows;
+#pragma unroll
+            for (int ii = 0; ii < ZP; ++ii) {
+                const int nr = us * ii + n0r;
+                const int n0 = rlo + nr;          // slice row
+                const bool valid = n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f));
+                if (valid) {
+                    const float2 s0 = src[nr], s1 = src[nr + 1];
+                    const float2 v = make_float2(fmaf(fr, s1.x - s0.x, s0.x), fmaf(fr, s1.y - s0.y, s0.y));
+                    cfma(acc[ii], cmul(sEc[kk * ZP + ii], ps), v);
+                }
+            }
         }
-        store_c(planes, ((((size_t)f * 2 + axL) * 2 + fam) * S + b) * plane_sz + (size_t)i * N + u, pt, acc);
+        const size_t ob = ((((size_t)f * 2 + axL) * 2 + fam) * S + b) * plane_sz + (size_t)i0 * N + u;
+#pragma unroll
+        for (int ii = 0; ii < ZP; ++ii)
+            if (ii < nrow) store_c_cs(planes, ob + (size_t)ii * N, pt, acc[ii]);
     }
 }
 
@@ -394,7 +661,7 @@ rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca
         const int ncol = nt * g.N * g.ns;
         mean = (float*)ws_get(h, WS_MEAN, (size_t)ncol * sizeof(float), &st);
         if (!mean) return st;
-        k_mean<<<(ncol + 255) / 256, 256, 0, h->stream>>>(rf, rf_t, scale, F, g.ns, ncol, mean);
+        k_mean<<<(ncol / 4 + 255) / 256, 256, 0, h->stream>>>(rf, rf_t, scale, F, g.ns, ncol, mean);
     }
     Fir fir;
     for (int q = 0; q < 31; ++q) fir.h[q] = t->fir[q];
@@ -412,48 +679,74 @@ static void warp_layout(int N, int zt, int* LW, int* RG, int* per)
     *per = (zt + *RG - 1) / *RG;
 }
 
-template <int MAXR>
-static rca_status stage1_launch(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
-                                float2* slices, int threads)
+template <typename TS, int MAXR>
+static rca_status stage1_launch(rca_handle* h, const rca_tables* t, const void* iq, int F, float2* slices,
+                                int threads)
 {
     const GeomDev& g = t->gd;
-    size_t smem = (size_t)t->s1.win * g.N * sizeof(float2);
-    auto kern = k_stage1<MAXR>;
+    const Stage1Plan& p = t->s1;
+    size_t smem = 2 * (size_t)p.win * g.N * sizeof(TS) + 2 * (size_t)p.zt * p.dc * sizeof(RowD) +
+                  2 * (size_t)p.zt * sizeof(int);
+    auto kern = k_stage1<TS, MAXR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage1 smem attribute");
-    dim3 grid(t->s1.n_tiles, 2 * g.K, F);
-    kern<<<grid, threads, smem, h->stream>>>(g, iq, iq_t, t->tx_q16, t->rx_q16, t->W, t->dmax, t->s1.d_chunks,
-                                             t->s1.zt, t->s1.n_tiles, t->s1.nch, slices);
+    dim3 grid(p.n_tiles, 2 * g.K, F);
+    kern<<<grid, threads, smem, h->stream>>>(g, iq, t->tx_q16, t->rx_q16, t->W, t->dmax, p.d_chunks, p.zt, p.dc,
+                                             p.n_tiles, p.nch, p.win, slices, h->d_status);
     return cuda_check(h, cudaGetLastError(), "stage1 kernel");
 }
 
-rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F, float2* slices)
+template <typename TS>
+static rca_status stage1_dispatch(rca_handle* h, const rca_tables* t, const void* iq, int F, float2* slices)
 {
     const GeomDev& g = t->gd;
     int LW, RG, per;
     warp_layout(g.N, t->s1.zt, &LW, &RG, &per);
     if (LW > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256 is not supported");
     const int threads = 32 * LW * RG;
-    if (per <= 2) return stage1_launch<2>(h, t, iq, iq_t, F, slices, threads);
-    if (per <= 4) return stage1_launch<4>(h, t, iq, iq_t, F, slices, threads);
-    if (per <= 8) return stage1_launch<8>(h, t, iq, iq_t, F, slices, threads);
-    if (per <= 16) return stage1_launch<16>(h, t, iq, iq_t, F, slices, threads);
+    if (per <= 2) return stage1_launch<TS, 2>(h, t, iq, F, slices, threads);
+    if (per <= 4) return stage1_launch<TS, 4>(h, t, iq, F, slices, threads);
+    if (per <= 8) return stage1_launch<TS, 8>(h, t, iq, F, slices, threads);
+    if (per <= 16) return stage1_launch<TS, 16>(h, t, iq, F, slices, threads);
     return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 row tile too tall");
+}
+
+rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F, float2* slices)
+{
+    if (iq_t == RCA_C32) return stage1_dispatch<float2>(h, t, iq, F, slices);
+    if (iq_t == RCA_C16F) return stage1_dispatch<__half2>(h, t, iq, F, slices);
+    if (iq_t == RCA_C16BF) return stage1_dispatch<__nv_bfloat162>(h, t, iq, F, slices);
+    return set_error(h, RCA_ERR_UNSUPPORTED, "iq dtype must be C32, C16F or C16BF");
+}
+
+template <int ZP>
+static rca_status stage2_launch(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes,
+                                rca_dtype pt)
+{
+    const GeomDev& g = t->gd;
+    const int rows = t->s2.rows, K = g.K, S = g.S, T = t->T;
+    size_t smem = ((size_t)K * rows * g.N + (size_t)K * S * rows + (size_t)K * S * ZP * T + (size_t)K * g.N +
+                   (size_t)K * ZP) * sizeof(float2) +
+                  ((size_t)2 * K * g.N + (size_t)K * S) * sizeof(int);
+    auto kern = k_stage2<ZP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "stage2 smem attribute");
+    dim3 grid(t->s2.n_tiles, 2, F);
+    kern<<<grid, 512, smem, h->stream>>>(g, slices, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin,
+                                         T, rows, t->s2.smin[0], t->s2.smin[1], planes, (int)pt, h->d_status);
+    return cuda_check(h, cudaGetLastError(), "stage2 kernel");
 }
 
 rca_status launch_stage2(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes, rca_dtype pt)
 {
-    const GeomDev& g = t->gd;
     if (!complex_dtype(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
-    const int rows = t->s2.rows;
-    size_t smem = ((size_t)g.K * rows * g.N + (size_t)g.K * g.S * rows) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_check(h, e, "stage2 smem attribute");
-    dim3 grid(t->s2.n_tiles, 2, F);
-    k_stage2<<<grid, 256, smem, h->stream>>>(g, slices, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef,
-                                             t->s2_tmin, t->T, t->s2.zp, rows, t->s2.smin[0], t->s2.smin[1], planes,
-                                             (int)pt);
-    return cuda_check(h, cudaGetLastError(), "stage2 kernel");
+    switch (t->s2.zp) {
+    case 1: return stage2_launch<1>(h, t, slices, F, planes, pt);
+    case 2: return stage2_launch<2>(h, t, slices, F, planes, pt);
+    case 4: return stage2_launch<4>(h, t, slices, F, planes, pt);
+    case 8: return stage2_launch<8>(h, t, slices, F, planes, pt);
+    default: return stage2_launch<16>(h, t, slices, F, planes, pt);
+    }
 }
 
 template <int MAXR>

@@ -26,44 +26,51 @@ __device__ __forceinline__ float block_max_256(float v, float* red)
 // XDoppler: each thread owns one pixel (axis, slab, row, lateral) and walks
 // the frames with a sliding 3-frame window, so every plane is read once:
 //   Q_t = P_RC,t conj(P_CR,t),  A_t = sqrt(|Q_{t-1} + Q_t + Q_{t+1}|).
-// M_t = max A_t through a block max and one atomicMax per block and frame
-// (non-negative floats order like their bit patterns).
+// The planes of frame t+2 are loaded while frame t is finished.  M_t = max
+// A_t: warp max, shared-memory atomicMax per frame, one global atomicMax per
+// block and frame at the end (non-negative floats order like their bits).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes, int pt, int F, int S,
                                                  size_t plane_sz, int enh, float* __restrict__ A,
                                                  unsigned* __restrict__ M)
 {
-    __shared__ float red[8];
+    extern __shared__ unsigned mx[];  // [F]
+    for (int t = threadIdx.x; t < F; t += blockDim.x) mx[t] = 0u;
+    __syncthreads();
     const size_t per_axis = (size_t)S * plane_sz;
     const size_t npx = 2 * per_axis;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = p < npx;
     const size_t axis = act ? p / per_axis : 0, rest = act ? p % per_axis : 0;
+    const int lane = threadIdx.x & 31;
     auto at = [&](int t, int fam) { return (((size_t)t * 2 + axis) * 2 + fam) * per_axis + rest; };
-    auto q_of = [&](int t) {
-        float2 a = load_c(planes, at(t, 0), pt), b = load_c(planes, at(t, 1), pt);
-        return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);  // a * conj(b)
+    auto ld = [&](int t, int fam) {
+        return (act && t < F) ? load_c(planes, at(t, fam), pt) : make_float2(0.f, 0.f);
     };
-    float2 qm = make_float2(0.f, 0.f), q0 = act ? q_of(0) : make_float2(0.f, 0.f);
+    auto xq = [](float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); };
+    float2 r0 = ld(0, 0), c0 = ld(0, 1), r1 = ld(1, 0), c1 = ld(1, 1);
+    float2 r2 = ld(2, 0), c2 = ld(2, 1);
+    float2 qm = make_float2(0.f, 0.f);
     for (int t = 0; t < F; ++t) {
-        float a = 0.f;
-        if (act) {
-            if (enh == ULM_ENH_XDOPPLER) {
-                float2 qp = (t + 1 < F) ? q_of(t + 1) : make_float2(0.f, 0.f);
-                float re = qm.x + q0.x + qp.x, im = qm.y + q0.y + qp.y;
-                a = sqrtf(sqrtf(re * re + im * im));
-                qm = q0;
-                q0 = qp;
-            } else {
-                float2 x = load_c(planes, at(t, 0), pt), y = load_c(planes, at(t, 1), pt);
-                float re = x.x + y.x, im = x.y + y.y;
-                a = sqrtf(re * re + im * im);
-            }
-            A[(size_t)t * npx + p] = a;
+        const float2 r3 = ld(t + 3, 0), c3 = ld(t + 3, 1);  // prefetch
+        float a;
+        if (enh == ULM_ENH_XDOPPLER) {
+            const float2 q0 = xq(r0, c0), qp = xq(r1, c1);
+            const float re = qm.x + q0.x + qp.x, im = qm.y + q0.y + qp.y;
+            a = sqrtf(sqrtf(re * re + im * im));
+            qm = q0;
+        } else {
+            const float re = r0.x + c0.x, im = r0.y + c0.y;
+            a = sqrtf(re * re + im * im);
         }
-        float m = block_max_256(a, red);
-        if (threadIdx.x == 0) atomicMax(M + t, __float_as_uint(m));
+        if (act) __stcs(A + (size_t)t * npx + p, a);
+        float m = act ? a : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) atomicMax(mx + t, __float_as_uint(m));
+        r0 = r1; c0 = c1; r1 = r2; c1 = c2; r2 = r3; c2 = c3;
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < F; t += blockDim.x) atomicMax(M + t, mx[t]);
 }
 
 // ---------------------------------------------------------------------------
@@ -75,174 +82,284 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
 // Candidates are compacted in raster order into a fixed-capacity slot of
 // the strip; the true count is kept.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_detect(const float* __restrict__ A, const float* __restrict__ Mf, int S,
+#define DET_SEG 8   // outputs per thread along a row / column in the separable passes
+
+template <int H>
+__global__ void __launch_bounds__(256, 2) k_detect(const float* __restrict__ A, const float* __restrict__ Mf, int S,
                                                 int nz, int N, NccConst nc, ulm_loc2d* __restrict__ cand,
                                                 int* __restrict__ cnt, float* __restrict__ ncc_out,
                                                 unsigned* __restrict__ status)
 {
-    extern __shared__ float sm[];
-    const int h = nc.h, d = nc.d;
+    constexpr int D = 2 * H + 1;
+    extern __shared__ __align__(128) float sm[];
     const int strip = blockIdx.x, plane = blockIdx.y;
     const int nstrip = gridDim.x;
     const int t = plane / (2 * S), axis = (plane / S) % 2, b = plane % S;
     const int i0 = strip * DET_RS;
-    const int rin = DET_RS + 2 + 2 * h, rn = DET_RS + 2;
+    const int rin = DET_RS + 2 + 2 * H, rn = DET_RS + 2;
     float* sA = sm;
     float* H1 = sA + rin * N;
     float* H2 = H1 + rin * N;
     float* HG = H2 + rin * N;
     float* sN = HG + rin * N;
-    __shared__ int wsum[8];
+    __shared__ int wsum[32];
     __shared__ int base_count;
+    __shared__ uint64_t bar;
     const float* Ap = A + (size_t)plane * nz * N;
     const float Mt = Mf[t];
-    for (int idx = threadIdx.x; idx < rin * N; idx += blockDim.x) {
-        int rr = idx / N, l = idx - rr * N;
-        int row = i0 - 1 - h + rr;
-        sA[idx] = (row >= 0 && row < nz) ? Ap[(size_t)row * N + l] : 0.f;
+    {
+        // rows [i0-1-H, i0+DET_RS+1+H) of the plane: zero outside, one bulk copy inside
+        const int rlo = i0 - 1 - H;
+        const int lo = max(rlo, 0), hi = max(lo, min(rlo + rin, nz));
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        const int z0 = min(lo - rlo, rin), z1 = hi - rlo;
+        for (int idx = threadIdx.x; idx < z0 * N; idx += blockDim.x) sA[idx] = 0.f;
+        for (int idx = threadIdx.x; idx < (rin - z1) * N; idx += blockDim.x) sA[(size_t)z1 * N + idx] = 0.f;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            const unsigned bytes = (unsigned)((hi - lo) * N * sizeof(float));
+            mbar_arrive_expect_tx(&bar, bytes);
+            if (bytes) bulk_g2s(sA + (size_t)(lo - rlo) * N, Ap + (size_t)lo * N, bytes, &bar);
+        }
+        if (!cta_wait_copies(&bar, 0, status)) return;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < rin * N; idx += blockDim.x) {
-        int rr = idx / N, l = idx - rr * N;
+    // horizontal pass: lanes over consecutive columns (conflict-free), each
+    // output sums its own D-wide window
+    for (int w = threadIdx.x; w < rin * N; w += blockDim.x) {
+        const int rr = w / N, c = w - rr * N;
+        const float* row = sA + rr * N;
         float s1 = 0.f, s2 = 0.f, sg = 0.f;
-        if (l >= h && l < N - h) {
-            const float* x = sA + rr * N + l - h;
-            for (int q = 0; q < d; ++q) {
-                float v = x[q];
-                s1 += v;
-                s2 = fmaf(v, v, s2);
-                sg = fmaf(nc.gl[q], v, sg);
+        if (c >= H && c < N - H) {
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                const float x = row[c - H + q];
+                s1 += x;
+                s2 = fmaf(x, x, s2);
+                sg = fmaf(nc.gl[q], x, sg);
             }
         }
-        H1[idx] = s1;
-        H2[idx] = s2;
-        HG[idx] = sg;
+        H1[w] = s1;
+        H2[w] = s2;
+        HG[w] = sg;
     }
     __syncthreads();
+    // vertical pass + NCC: each thread owns DET_SEG consecutive output rows of one column
     const float flat = nc.flat_coef * Mt * Mt;
-    const float inv_d2 = 1.0f / (float)(d * d);
-    for (int idx = threadIdx.x; idx < rn * N; idx += blockDim.x) {
-        int ro = idx / N, l = idx - ro * N;
-        int i = i0 - 1 + ro;
-        float v = 0.f;
-        if (i >= h && i < nz - h && l >= h && l < N - h && Mt > 0.f) {
-            float s1 = 0.f, s2 = 0.f, sg = 0.f;
-            for (int a = 0; a <= 2 * h; ++a) {
-                int o = (ro + a) * N + l;
-                s1 += H1[o];
-                s2 += H2[o];
-                sg = fmaf(nc.gz[a], HG[o], sg);
-            }
-            float ssA = s2 - s1 * s1 * inv_d2;
-            if (ssA > flat) v = (sg - nc.muG * s1) * nc.inv_ssG_sqrt * rsqrtf(ssA);
+    const float inv_d2 = 1.0f / (float)(D * D);
+    const int nrs = (rn + DET_SEG - 1) / DET_SEG;
+    for (int w = threadIdx.x; w < nrs * N; w += blockDim.x) {
+        const int rs = w / N, l = w - rs * N;
+        const int ro0 = rs * DET_SEG;
+        float h1[DET_SEG + 2 * H], h2[DET_SEG + 2 * H], hg[DET_SEG + 2 * H];
+#pragma unroll
+        for (int q = 0; q < DET_SEG + 2 * H; ++q) {
+            const int rr = min(ro0 + q, rin - 1);
+            h1[q] = H1[rr * N + l];
+            h2[q] = H2[rr * N + l];
+            hg[q] = HG[rr * N + l];
         }
-        sN[idx] = v;
-        if (ncc_out && ro >= 1 && ro <= DET_RS && i < nz) ncc_out[((size_t)plane * nz + i) * N + l] = v;
+#pragma unroll
+        for (int o = 0; o < DET_SEG; ++o) {
+            const int ro = ro0 + o, i = i0 - 1 + ro;
+            if (ro < rn) {
+                float v = 0.f;
+                if (i >= H && i < nz - H && l >= H && l < N - H && Mt > 0.f) {
+                    float s1 = 0.f, s2 = 0.f, sg = 0.f;
+#pragma unroll
+                    for (int q = 0; q < D; ++q) {
+                        s1 += h1[o + q];
+                        s2 += h2[o + q];
+                        sg = fmaf(nc.gz[q], hg[o + q], sg);
+                    }
+                    const float ssA = s2 - s1 * s1 * inv_d2;
+                    if (ssA > flat) v = (sg - nc.muG * s1) * nc.inv_ssG_sqrt * rsqrtf(ssA);
+                }
+                sN[ro * N + l] = v;
+                if (ncc_out && ro >= 1 && ro <= DET_RS && i < nz) ncc_out[((size_t)plane * nz + i) * N + l] = v;
+            }
+        }
     }
-    if (threadIdx.x == 0) base_count = 0;
     __syncthreads();
+    // peaks: each thread tests a contiguous run of pixels (raster order), one
+    // block-wide exclusive scan of the per-thread counts places them
     const float athr = nc.alpha * Mt;
     ulm_loc2d* slot = cand + ((size_t)plane * nstrip + strip) * CAND_CAP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < DET_RS * N; base += blockDim.x) {
-        const int p = base + threadIdx.x;
+    const int npx = DET_RS * N;
+    const int per = (npx + blockDim.x - 1) / blockDim.x;
+    const int p0 = threadIdx.x * per, p1 = min(npx, p0 + per);
+    auto is_peak = [&](int p, float& c) {
         const int ro = 1 + p / N, l = p % N;
         const int i = i0 - 1 + ro;
-        bool pk = false;
-        float c = 0.f;
-        if (p < DET_RS * N && i >= 1 && i < nz - 1 && l >= 1 && l < N - 1) {
-            c = sN[ro * N + l];
-            float amp = sA[(ro + h) * N + l];
-            if (c >= nc.ncc_min && amp >= athr) {
-                pk = true;
-                for (int a = -1; a <= 1; ++a)
-                    for (int bb = -1; bb <= 1; ++bb) {
-                        if (a == 0 && bb == 0) continue;
-                        float q = sN[(ro + a) * N + l + bb];
-                        bool earlier = (a < 0) || (a == 0 && bb < 0);
-                        if (earlier ? !(c > q) : !(c >= q)) pk = false;
-                    }
+        if (i < 1 || i >= nz - 1 || l < 1 || l >= N - 1) return false;
+        c = sN[ro * N + l];
+        if (!(c >= nc.ncc_min) || !(sA[(ro + H) * N + l] >= athr)) return false;
+#pragma unroll
+        for (int a = -1; a <= 1; ++a)
+#pragma unroll
+            for (int bb = -1; bb <= 1; ++bb) {
+                if (a == 0 && bb == 0) continue;
+                const float q = sN[(ro + a) * N + l + bb];
+                const bool earlier = (a < 0) || (a == 0 && bb < 0);
+                if (earlier ? !(c > q) : !(c >= q)) return false;
             }
-        }
-        unsigned bal = __ballot_sync(0xffffffffu, pk);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        int before = base_count;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        before += __popc(bal & ((1u << lane) - 1u));
-        if (pk && before < CAND_CAP) {
-            auto para = [](float fm, float f0, float fp) {
-                float den = fm - 2.f * f0 + fp;
-                if (den >= 0.f) return 0.f;
-                float dl = (fm - fp) / (2.f * den);
-                return fminf(0.5f, fmaxf(-0.5f, dl));
-            };
-            ulm_loc2d e;
-            e.frame = t;
-            e.axis = axis;
-            e.slab = b;
-            e.iz = i;
-            e.ilat = l;
-            e.z = (float)i + para(sN[(ro - 1) * N + l], c, sN[(ro + 1) * N + l]);
-            e.lat = (float)l + para(sN[ro * N + l - 1], c, sN[ro * N + l + 1]);
-            e.ncc = c;
-            e.amp = sA[(ro + h) * N + l];
-            e.reserved = 0;
-            slot[before] = e;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
-            base_count += tot;
-        }
-        __syncthreads();
+        return true;
+    };
+    int mine = 0;
+    for (int p = p0; p < p1; ++p) {
+        float c;
+        mine += is_peak(p, c) ? 1 : 0;
     }
+    int x = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = x - mine;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    if (mine) {
+        for (int p = p0; p < p1; ++p) {
+            float c;
+            if (!is_peak(p, c)) continue;
+            if (before < CAND_CAP) {
+                const int ro = 1 + p / N, l = p % N, i = i0 - 1 + ro;
+                auto para = [](float fm, float f0, float fp) {
+                    const float den = fm - 2.f * f0 + fp;
+                    if (den >= 0.f) return 0.f;
+                    const float dl = (fm - fp) / (2.f * den);
+                    return fminf(0.5f, fmaxf(-0.5f, dl));
+                };
+                ulm_loc2d e;
+                e.frame = t;
+                e.axis = axis;
+                e.slab = b;
+                e.iz = i;
+                e.ilat = l;
+                e.z = (float)i + para(sN[(ro - 1) * N + l], c, sN[(ro + 1) * N + l]);
+                e.lat = (float)l + para(sN[ro * N + l - 1], c, sN[ro * N + l + 1]);
+                e.ncc = c;
+                e.amp = sA[(ro + H) * N + l];
+                e.reserved = 0;
+                slot[before] = e;
+            }
+            ++before;
+        }
+    }
+    if (threadIdx.x == blockDim.x - 1) base_count = before;
+    __syncthreads();
     if (threadIdx.x == 0) {
         cnt[(size_t)plane * nstrip + strip] = base_count;
         if (base_count > CAND_CAP) atomicOr(status, ST_CAPACITY);
     }
 }
 
-// Single-CTA exclusive scan of min(cnt[i], cap_each) (cap_each <= 0: no cap).
-// off[n] = total kept; *total_true = sum of cnt (may exceed the kept total).
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt, int n, int cap_each,
-                                               int* __restrict__ off, int* __restrict__ total_true,
-                                               const int* __restrict__ n_dev)
+// Multi-block exclusive scan of min(cnt[i], cap_each) (cap_each <= 0: no cap)
+// over n entries (n = min(n, *n_dev) when n_dev is given).  off[n] = kept
+// total; *total_true = sum of the uncapped counts.
+#define SCAN_CHUNK 4096
+#define SCAN_THREADS 512
+
+__device__ __forceinline__ int scan_n(int n, const int* n_dev) { return n_dev ? min(n, *n_dev) : n; }
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_part(const int* __restrict__ cnt, int n, const int* __restrict__ n_dev,
+                                                            int cap_each, long long* __restrict__ part)
 {
-    __shared__ int part[1024];
-    __shared__ long long tpart[1024];
-    if (n_dev) n = min(n, *n_dev);
-    const int T = blockDim.x;
-    const int per = (n + T - 1) / T;
-    const int lo = threadIdx.x * per, hi = min(n, lo + per);
-    int s = 0;
-    long long st = 0;
-    for (int i = lo; i < hi; ++i) {
-        int c = cnt[i];
+    __shared__ long long red[2][SCAN_THREADS / 32];
+    n = scan_n(n, n_dev);
+    const int lo = blockIdx.x * SCAN_CHUNK, hi = min(n, lo + SCAN_CHUNK);
+    long long s = 0, st = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int c = cnt[i];
         st += c;
         s += (cap_each > 0) ? min(c, cap_each) : c;
     }
-    part[threadIdx.x] = s;
-    tpart[threadIdx.x] = st;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        st += __shfl_xor_sync(0xffffffffu, st, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s;
+        red[1][threadIdx.x >> 5] = st;
+    }
     __syncthreads();
-    for (int o = 1; o < T; o <<= 1) {
-        int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        long long tv = threadIdx.x >= o ? tpart[threadIdx.x - o] : 0;
+    if (threadIdx.x == 0) {
+        long long a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// one block: exclusive scan of the per-chunk totals (nb <= 1024 chunks)
+__global__ void __launch_bounds__(1024) k_scan_top(long long* __restrict__ part, int nb, int n,
+                                                   const int* __restrict__ n_dev, int* __restrict__ off,
+                                                   int* __restrict__ total_true)
+{
+    __shared__ long long a[1024], b[1024];
+    n = scan_n(n, n_dev);
+    const int used = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    const int i = threadIdx.x;
+    a[i] = (i < nb && i < used) ? part[2 * i] : 0;
+    b[i] = (i < nb && i < used) ? part[2 * i + 1] : 0;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        long long va = i >= o ? a[i - o] : 0, vb = i >= o ? b[i - o] : 0;
         __syncthreads();
-        part[threadIdx.x] += v;
-        tpart[threadIdx.x] += tv;
+        a[i] += va;
+        b[i] += vb;
         __syncthreads();
     }
-    int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (int i = lo; i < hi; ++i) {
-        off[i] = run;
-        int c = cnt[i];
-        run += (cap_each > 0) ? min(c, cap_each) : c;
+    if (i < nb) part[2 * i] = i ? a[i - 1] : 0;  // exclusive chunk offset
+    if (i == 1023) {
+        off[n] = (int)min(a[1023], (long long)0x7fffffff);
+        if (total_true) *total_true = (int)min(b[1023], (long long)0x7fffffff);
     }
-    if (threadIdx.x == T - 1) {
-        off[n] = part[T - 1];
-        if (total_true) *total_true = (int)(tpart[T - 1] < 0x7fffffffLL ? tpart[T - 1] : 0x7fffffffLL);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int* __restrict__ cnt, int n,
+                                                             const int* __restrict__ n_dev, int cap_each,
+                                                             const long long* __restrict__ part, int* __restrict__ off)
+{
+    constexpr int PER = SCAN_CHUNK / SCAN_THREADS;
+    __shared__ int wsum[SCAN_THREADS / 32];
+    n = scan_n(n, n_dev);
+    const int lo = blockIdx.x * SCAN_CHUNK;
+    if (lo >= n) return;
+    const int base = lo + threadIdx.x * PER;
+    int v[PER], s = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = base + q;
+        const int c = i < n ? cnt[i] : 0;
+        v[q] = (cap_each > 0) ? min(c, cap_each) : c;
+        s += v[q];
+    }
+    // block exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    int run = (int)part[2 * blockIdx.x] + wpre + x - s;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = base + q;
+        if (i < n) off[i] = run;
+        run += v[q];
     }
 }
 
@@ -378,6 +495,18 @@ __global__ void k_pair_write(const ulm_loc2d* __restrict__ L, const int* __restr
 
 }  // namespace
 
+// exclusive scan on the device; part: workspace of 2 * ceil(n_max / SCAN_CHUNK) long longs
+static rca_status device_scan(rca_handle* h, const int* cnt, int n_max, const int* n_dev, int cap_each, int* off,
+                              int* total_true, long long* part)
+{
+    const int nb = std::max(1, (n_max + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    if (nb > 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "scan over more than %d entries", 1024 * SCAN_CHUNK);
+    k_scan_part<<<nb, SCAN_THREADS, 0, h->stream>>>(cnt, n_max, n_dev, cap_each, part);
+    k_scan_top<<<1, 1024, 0, h->stream>>>(part, nb, n_max, n_dev, off, total_true);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, h->stream>>>(cnt, n_max, n_dev, cap_each, part, off);
+    return cuda_check(h, cudaGetLastError(), "scan kernels");
+}
+
 rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F, int enh,
                           float* A, float* M)
 {
@@ -385,9 +514,13 @@ rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes
     if (enh != ULM_ENH_XDOPPLER && enh != ULM_ENH_COHERENT) return set_error(h, RCA_ERR_INVALID_ARG, "bad enhancement mode");
     const size_t plane_sz = (size_t)g.nz * g.N;
     const size_t npx = 2 * (size_t)g.S * plane_sz;
+    if (F > 48 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 49152 frames in one call");
     cudaMemsetAsync(M, 0, sizeof(float) * F, h->stream);
-    k_enhance<<<(unsigned)((npx + 255) / 256), 256, 0, h->stream>>>(planes, (int)pt, F, g.S, plane_sz, enh, A,
-                                                                   reinterpret_cast<unsigned*>(M));
+    const size_t smem = (size_t)F * sizeof(unsigned);
+    cudaError_t e = cudaFuncSetAttribute(k_enhance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "enhance smem attribute");
+    k_enhance<<<(unsigned)((npx + 255) / 256), 256, smem, h->stream>>>(planes, (int)pt, F, g.S, plane_sz, enh, A,
+                                                                      reinterpret_cast<unsigned*>(M));
     return cuda_check(h, cudaGetLastError(), "enhance kernel");
 }
 
@@ -431,11 +564,28 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     if (!off) return st;
     const int rin = DET_RS + 2 + 2 * hh;
     size_t smem = ((size_t)4 * rin * g.N + (size_t)(DET_RS + 2) * g.N) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_check(h, e, "detect smem attribute");
     dim3 grid(nstrip, nplanes);
-    k_detect<<<grid, 256, smem, h->stream>>>(A, M, g.S, g.nz, g.N, nc, cand, cnt, ncc_out, h->d_status);
-    k_scan<<<1, 1024, 0, h->stream>>>(cnt, nslots, CAND_CAP, off, n2d, nullptr);
+    cudaError_t e = cudaSuccess;
+    switch (hh) {
+#define RCA_DETECT_CASE(HV)                                                                                \
+    case HV:                                                                                               \
+        e = cudaFuncSetAttribute(k_detect<HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        if (e != cudaSuccess) return cuda_check(h, e, "detect smem attribute");                          \
+        k_detect<HV><<<grid, 256, smem, h->stream>>>(A, M, g.S, g.nz, g.N, nc, cand, cnt, ncc_out, h->d_status); \
+        break;
+        RCA_DETECT_CASE(1)
+        RCA_DETECT_CASE(2)
+        RCA_DETECT_CASE(3)
+        RCA_DETECT_CASE(4)
+        RCA_DETECT_CASE(5)
+        RCA_DETECT_CASE(6)
+        RCA_DETECT_CASE(7)
+#undef RCA_DETECT_CASE
+    default: return set_error(h, RCA_ERR_INVALID_ARG, "NCC kernel length out of range");
+    }
+    long long* part = (long long*)ws_get(h, WS_N2D, (size_t)2 * 1024 * sizeof(long long), &st);
+    if (!part) return st;
+    if ((st = device_scan(h, cnt, nslots, nullptr, CAND_CAP, off, n2d, part)) != RCA_OK) return st;
     k_gather<<<(nslots + 7) / 8, 256, 0, h->stream>>>(cand, cnt, off, nslots, out, cap, h->d_status);
     if (plane_off) k_strip_to_plane<<<(nplanes + 1 + 255) / 256, 256, 0, h->stream>>>(off, nstrip, nplanes, plane_off);
     return cuda_check(h, cudaGetLastError(), "detect kernels");
@@ -458,7 +608,9 @@ rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L,
     k_list_plane_offsets<<<(nplanes + 1 + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, g.S, nplanes, poff);
     k_pair_match<<<(nn + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, g.S, g.P, poff, match);
     k_match_flags<<<(nn + 255) / 256, 256, 0, h->stream>>>(match, n2d, cap2d, flags);
-    k_scan<<<1, 1024, 0, h->stream>>>(flags, nn, 0, off, n3d, n2d);
+    long long* part = (long long*)ws_get(h, WS_N2D, (size_t)2 * 1024 * sizeof(long long), &st);
+    if (!part) return st;
+    if ((st = device_scan(h, flags, nn, n2d, 0, off, n3d, part)) != RCA_OK) return st;
     k_pair_write<<<(nn + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, match, off, out, cap3d, h->d_status);
     return cuda_check(h, cudaGetLastError(), "pair kernels");
 }

@@ -128,7 +128,7 @@ struct rca_tables {
 // ---------------------------------------------------------------------------
 #define RCA_MAX_NCC_D 15
 #define CAND_CAP 64       // 2D candidates per (plane, row strip)
-#define DET_RS 16         // rows per detect strip
+#define DET_RS 32         // rows per detect strip
 
 struct NccConst {
     int d, h;
@@ -195,4 +195,149 @@ __device__ __forceinline__ void cfma(float2& acc, float2 w, float2 v)
     acc.x = fmaf(-w.y, v.y, acc.x);
     acc.y = fmaf(w.x, v.y, acc.y);
     acc.y = fmaf(w.y, v.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk, global -> shared) completed on an mbarrier.
+// Every wait is bounded by a clock budget; a wait that runs out reports
+// ST_TIMEOUT through the status word and the caller returns.
+// ---------------------------------------------------------------------------
+#define RCA_WAIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make mbarrier initialisation visible to the async (TMA) proxy
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// order this thread's earlier generic shared-memory accesses before later
+// async-proxy (TMA) accesses to the same memory
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bytes and both addresses must be multiples of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the given phase parity; false if the budget ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase)
+{
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, phase)) {
+        if (clock64() - t0 > RCA_WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// All threads wait for `phase` of `bar`, then synchronise.  Returns false
+// (after recording ST_TIMEOUT and waiting once more, bounded, for the copy
+// still in flight) if any thread's wait ran out; the CTA must then return.
+__device__ __forceinline__ bool cta_wait_copies(uint64_t* bar, unsigned phase, unsigned* status)
+{
+    bool ok = mbar_wait_bounded(bar, phase);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        mbar_wait_bounded(bar, phase);
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// Streaming store (evict-first): outputs that are not re-read soon.
+__device__ __forceinline__ void store_c_cs(void* p, size_t i, int dt, float2 v)
+{
+    if (dt == RCA_C32) {
+        __stcs(reinterpret_cast<float2*>(p) + i, v);
+    } else if (dt == RCA_C16F) {
+        __half2 h = __float22half2_rn(v);
+        __stcs(reinterpret_cast<unsigned*>(p) + i, *reinterpret_cast<unsigned*>(&h));
+    } else {
+        __nv_bfloat162 b = __float22bfloat162_rn(v);
+        __stcs(reinterpret_cast<unsigned*>(p) + i, *reinterpret_cast<unsigned*>(&b));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// packed FP32 pairs (Blackwell f32x2 FMA): two lanes of float math per instruction
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t f2_pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2_unpack(uint64_t v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// 32-bit shared-memory loads by byte address
+__device__ __forceinline__ uint64_t lds_u64(unsigned addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ unsigned lds_u32(unsigned addr)
+{
+    unsigned v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void lds_u64x2(unsigned addr, uint64_t& a, uint64_t& b)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }

@@ -130,8 +130,11 @@ __global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, i
         double s = shift[(size_t)k * g.N + m];
         double zeta = (double)(g.us * i) + s;
         if (!(zeta >= 0.0) || zeta > (double)(g.nzs - 1)) continue;
-        int n0 = (int)floor(zeta);
-        double fr = zeta - (double)n0;
+        // slice row and fraction from us*i + floor(s) (equal to floor(zeta)
+        // except within rounding of an integer, where the interpolant is continuous)
+        double fl = floor(s);
+        int n0 = g.us * i + (int)fl;
+        double fr = s - fl;
         double sh = elem_pos(g, m) * g.sin_th[k] / (1.0 + g.cos_th[k]);
         double ph = TWO_PI_D * g.fc * tau_c(g, k, plane_z(g, i) + sh);
         double sn, cs;
@@ -260,11 +263,10 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
                 lo = std::min(lo, sfl[(size_t)k * g.N + m]);
                 hi = std::max(hi, sfl[(size_t)k * g.N + m]);
             }
-            // one extra row on each side absorbs floor(us*i + s) != us*i + floor(s)
-            tmin[(size_t)k * g.S + b] = lo - 1;
-            T = std::max(T, hi - lo + 4);
+            tmin[(size_t)k * g.S + b] = lo;
+            T = std::max(T, hi - lo + 2);
         }
-    if (T > 16) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 shift spans %d slice rows within one slab (max 12)", T - 4);
+    if (T > 16) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 shift spans %d slice rows within one slab (max 14)", T - 2);
     t->T = T;
     for (int fam = 0; fam < 2; ++fam) {
         int lo = 1 << 30, hi = -(1 << 30);
@@ -273,7 +275,7 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
                 lo = std::min(lo, sfl[(size_t)k * g.N + m]);
                 hi = std::max(hi, sfl[(size_t)k * g.N + m]);
             }
-        t->s2.smin[fam] = lo - 1;
+        t->s2.smin[fam] = lo;
         t->s2.smax[fam] = hi + 1;
     }
     t->s2_coef = dalloc<float2>(h, (size_t)nt * g.S * g.nz * T, &st);
@@ -305,11 +307,16 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
                 }
         return win;
     };
-    const size_t budget = 72 * 1024;
-    int zt = 16, dc = 16;
-    while ((size_t)plan(zt, dc, nullptr) * g.N * sizeof(float2) > budget && (zt > 2 || dc > 2)) {
-        if (dc >= zt && dc > 2) dc /= 2;
-        else zt /= 2;
+    // two sample windows (double buffer) plus the per-(row, d) records must
+    // leave room for two CTAs per SM
+    const size_t budget = 104 * 1024;
+    const int shapes[][2] = {{16, 16}, {16, 8}, {8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {1, 1}};
+    int zt = 1, dc = 1;
+    for (auto& sh : shapes) {
+        zt = sh[0];
+        dc = sh[1];
+        size_t need = 2 * (size_t)plan(zt, dc, nullptr) * g.N * sizeof(float2) + 2 * (size_t)zt * dc * 32 + 2 * zt * 4;
+        if (need <= budget) break;
     }
     std::vector<int4> chunks;
     t->s1.zt = zt;
@@ -317,7 +324,7 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     t->s1.win = plan(zt, dc, &chunks);
     t->s1.n_tiles = (g.nzs + zt - 1) / zt;
     t->s1.nch = (g.N + dc - 1) / dc;
-    if ((size_t)t->s1.win * g.N * sizeof(float2) > 200 * 1024)
+    if (2 * (size_t)t->s1.win * g.N * sizeof(float2) > 200 * 1024)
         return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 sample window of %d samples x %d elements exceeds shared memory",
                          t->s1.win, g.N);
     t->s1.d_chunks = dalloc<int4>(h, chunks.size(), &st);
@@ -329,9 +336,11 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     int zp = 16;
     auto s2_bytes = [&](int z) {
         int rows = g.us * (z - 1) + span;
-        return (size_t)g.K * rows * g.N * sizeof(float2) + (size_t)g.K * g.S * rows * sizeof(float2);
+        return (size_t)g.K * rows * g.N * sizeof(float2) + (size_t)g.K * g.S * rows * sizeof(float2) +
+               (size_t)g.K * g.S * z * T * sizeof(float2) + (size_t)g.K * g.N * 16 + (size_t)g.K * z * 8 +
+               (size_t)g.K * g.S * 4;
     };
-    while (zp > 1 && s2_bytes(zp) > budget) zp /= 2;
+    while (zp > 1 && s2_bytes(zp) > 110 * 1024) zp /= 2;
     t->s2.zp = zp;
     t->s2.rows = g.us * (zp - 1) + span;
     t->s2.n_tiles = (g.nz + zp - 1) / zp;
