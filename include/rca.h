@@ -40,7 +40,9 @@
  * Array layouts (row-major; complex = interleaved re, im):
  *   rf      [F][2K][E][ns]           F frames, 2K transmissions (RC first),
  *                                    E = n_el receive elements, ns samples
- *   iq      [F][2K][E][ns] complex   baseband IQ after clutter removal
+ *   iq      [F][2K][ns][E] complex   baseband IQ after clutter removal
+ *                                    (element innermost: one sample row of
+ *                                    all elements is contiguous)
  *   slices  [F][2K][nzs][N] complex  Stage-1 reference slices, N = n_el
  *                                    lateral pixels, nzs = (nz-1)*us + 1
  *   planes  [F][2][2][S][nz][N] complex   [axis][family][slab]:
@@ -125,7 +127,8 @@ rca_status rca_reserve(rca_handle* h, const rca_geometry* g, int n_frames);
 /* ---------------------------------------------------------------------- */
 
 typedef struct {
-    int n_el;          /* elements per array (rows = columns); N lateral pixels */
+    int n_el;          /* elements per array (rows = columns); N lateral pixels;
+                          a multiple of 4 (16-byte sample rows), at most 256 */
     int nz;            /* axial pixels of the projection planes */
     int ns;            /* RF samples per channel */
     int P;             /* sub-block / slab size in pixels (paper: 8); n_el % P == 0 */
@@ -200,7 +203,7 @@ typedef struct {
  * demodulation b[n] = 2 sum_m h[m] r~[n-m] exp(-j 2 pi fc t_{n-m}) with a
  * 31-tap half-band Hamming low-pass h (cut-off fs/4).
  *   rf: [F][2K][E][ns] RCA_F32, RCA_F16 or RCA_I16 (then scale[2K][E] float,
- *       value = q * scale); iq: [F][2K][E][ns] RCA_C32 / C16F / C16BF. */
+ *       value = q * scale); iq: [F][2K][ns][E] RCA_C32 / C16F / C16BF. */
 rca_status rca_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca_dtype rf_dtype,
                       const float* scale, int n_frames, int clutter, void* iq, rca_dtype iq_dtype);
 
@@ -299,6 +302,60 @@ rca_status ulm_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* list2
 rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype planes_dtype,
                         int n_frames, const ulm_params* prm, ulm_loc2d* out2d, int cap2d, int* n2d_dev,
                         ulm_loc3d* out3d, int cap3d, int* n3d_dev);
+
+/* ---------------------------------------------------------------------- */
+/* Batched form and launch-shape autotuning                                */
+/* ---------------------------------------------------------------------- */
+
+typedef struct rca_batch rca_batch;
+
+/* One ensemble of a batch.  Buffers are caller-owned device memory and must
+ * stay valid (and at the same address) for the life of the batch plan. */
+typedef struct {
+    const rca_tables* tables;  /* the ensemble's geometry (ensembles may differ in K) */
+    const void* rf;            /* [F][2K][E][ns] channel data, dtype of the batch */
+    const float* scale;        /* [2K][E] per-channel scale when the batch rf dtype is RCA_I16 */
+    int n_frames;              /* F */
+    void* planes;              /* [F][2][2][S][nz][N] output planes, dtype of the batch */
+    ulm_loc2d* out2d;          /* localisation outputs (used when the batch has ulm_params) */
+    int cap2d;
+    int* n2d_dev;
+    ulm_loc3d* out3d;
+    int cap3d;
+    int* n3d_dev;
+} rca_batch_item;
+
+/* Plan a batch of n ensembles of uneven frame counts and transmission sets.
+ * Beamforming of the whole batch (mean clutter removal, demodulation,
+ * Stage 1, Stage 2 + projection) runs as ONE persistent launch: a device
+ * work queue of units, ordered so that every unit only waits for earlier
+ * ones through per-ensemble completion counters (bounded waits: a wait that
+ * runs out sets RCA_ERR_TIMEOUT in the status word and stops the launch).
+ * With prm non-NULL each ensemble is then localised (ulm_localize).
+ * Allocates the per-ensemble IQ and slice workspace (owned by the plan).
+ * Errors: INVALID_ARG / SHAPE / UNSUPPORTED on the host. */
+rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_item* items, rca_dtype rf_dtype,
+                            rca_dtype iq_dtype, rca_dtype planes_dtype, const ulm_params* prm, rca_batch** out);
+
+/* Enqueue one run of the batch on the handle's stream.  use_graph != 0:
+ * the first call runs the batch once, then captures it into a CUDA graph
+ * (on a private stream); every call launches that graph. */
+rca_status rca_batch_run(rca_batch* b, int use_graph);
+
+/* Bound of every dependency wait in the persistent launch, in SM clock
+ * cycles (default ~4e9).  block_ensemble >= 0 makes that ensemble's Stage-1
+ * units wait for one demodulation unit that never exists -- a host-built
+ * impossible queue used to test that the launch ends with RCA_ERR_TIMEOUT. */
+rca_status rca_batch_set_wait_limit(rca_batch* b, long long cycles, int block_ensemble);
+
+rca_status rca_batch_destroy(rca_batch* b);
+
+/* Time the Stage-1 (row tile x distance chunk) and Stage-2 (plane-row tile)
+ * launch shapes that fit shared memory on the given IQ (n_frames frames of
+ * t's geometry, RCA_C32 / C16F / C16BF) and keep the fastest in t.
+ * Synchronises.  zt, dc, zp (optional) receive the chosen shapes. */
+rca_status rca_autotune(rca_handle* h, rca_tables* t, const void* iq, rca_dtype iq_dtype, int n_frames,
+                        int* zt, int* dc, int* zp);
 
 #ifdef __cplusplus
 }

@@ -51,6 +51,12 @@ class ulm_params(C.Structure):
                 ("ncc_min", C.c_float), ("enh", C.c_int), ("reserved", C.c_int * 4)]
 
 
+class rca_batch_item(C.Structure):
+    _fields_ = [("tables", C.c_void_p), ("rf", C.c_void_p), ("scale", C.c_void_p), ("n_frames", C.c_int),
+                ("planes", C.c_void_p), ("out2d", C.c_void_p), ("cap2d", C.c_int), ("n2d_dev", C.c_void_p),
+                ("out3d", C.c_void_p), ("cap3d", C.c_int), ("n3d_dev", C.c_void_p)]
+
+
 LOC2D = np.dtype([("frame", "<i4"), ("axis", "<i4"), ("slab", "<i4"), ("iz", "<i4"), ("ilat", "<i4"),
                   ("z", "<f4"), ("lat", "<f4"), ("ncc", "<f4"), ("amp", "<f4"), ("reserved", "<i4")])
 LOC3D = np.dtype([("frame", "<i4"), ("i_xz", "<i4"), ("i_yz", "<i4"), ("reserved", "<i4"),
@@ -88,6 +94,11 @@ SIGNATURES = {
     "ulm_detect2d": (_S, [_P, _P, _P, _P, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _P]),
     "ulm_pair3d": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
     "ulm_localize": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _I, _P]),
+    "rca_batch_create": (_S, [_P, _I, C.POINTER(rca_batch_item), _I, _I, _I, C.POINTER(ulm_params), C.POINTER(_P)]),
+    "rca_batch_run": (_S, [_P, _I]),
+    "rca_batch_set_wait_limit": (_S, [_P, C.c_longlong, _I]),
+    "rca_batch_destroy": (_S, [_P]),
+    "rca_autotune": (_S, [_P, _P, _P, _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
 }
 
 _lock = threading.Lock()

@@ -521,3 +521,341 @@ extern "C" rca_status ulm_localize(rca_handle* h, const rca_tables* t, const voi
     if ((st = launch_detect2d(h, t, A, M, F, prm, out2d, cap2d, n2d, nullptr, nullptr)) != RCA_OK) return st;
     return launch_pair3d(h, t, out2d, n2d, cap2d, F, out3d, cap3d, n3d);
 }
+
+// ---------------------------------------------------------------------------
+// batched form
+// ---------------------------------------------------------------------------
+static void batch_free(rca_batch* b)
+{
+    if (b->lh) {
+        for (auto& w : b->lh->ws)
+            if (w.p) cudaFree(w.p);
+        delete b->lh;  // its status word belongs to the caller's handle
+        b->lh = nullptr;
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (void* p : b->owned)
+        if (p) cudaFree(p);
+    if (b->d_ens) cudaFree(b->d_ens);
+    if (b->d_segs) cudaFree(b->d_segs);
+    if (b->d_cnt) cudaFree(b->d_cnt);
+}
+
+extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_item* items, rca_dtype rf_t,
+                                       rca_dtype iq_t, rca_dtype pl_t, const ulm_params* prm, rca_batch** out)
+{
+    CHECK_HANDLE(h);
+    if (!items || !out || n <= 0) return set_error(h, RCA_ERR_INVALID_ARG, "null items/output or n <= 0");
+    *out = nullptr;
+    if (!is_real_rf(rf_t) || !is_complex(iq_t) || !is_complex(pl_t))
+        return set_error(h, RCA_ERR_UNSUPPORTED, "rf must be F32/F16/I16, iq and planes complex");
+    if (prm && check_ulm(h, prm) != RCA_OK) return RCA_ERR_INVALID_ARG;
+    for (int e = 0; e < n; ++e) {
+        const rca_batch_item& it = items[e];
+        if (!it.tables || !it.rf || !it.planes || it.n_frames <= 0)
+            return set_error(h, RCA_ERR_INVALID_ARG, "item %d: null tables/rf/planes or n_frames <= 0", e);
+        if (it.tables->h->device != h->device) return set_error(h, RCA_ERR_INVALID_ARG, "item %d on another device", e);
+        if (rf_t == RCA_I16 && !it.scale) return set_error(h, RCA_ERR_INVALID_ARG, "item %d: int16 rf needs a scale", e);
+        if (prm && (!it.n2d_dev || !it.n3d_dev || it.cap2d < 0 || it.cap3d < 0 || (it.cap2d && !it.out2d) ||
+                    (it.cap3d && !it.out3d)))
+            return set_error(h, RCA_ERR_INVALID_ARG, "item %d: localisation outputs missing", e);
+        if (prm && (it.tables->gd.N < prm->d || it.tables->gd.nz < prm->d))
+            return set_error(h, RCA_ERR_SHAPE, "item %d: plane smaller than the NCC kernel", e);
+    }
+    DeviceGuard dg(h->device);
+    rca_batch* b = new (std::nothrow) rca_batch();
+    if (!b) return set_error(h, RCA_ERR_CUDA, "out of host memory");
+    b->h = h;
+    b->n = n;
+    b->rf_t = rf_t;
+    b->iq_t = iq_t;
+    b->pl_t = pl_t;
+    for (int q = 0; q < 31; ++q) b->fir[q] = items[0].tables->fir[q];
+    const size_t esz = dtype_size(iq_t);
+    rca_status st = RCA_OK;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes + 256) != cudaSuccess) {
+            st = set_error(h, RCA_ERR_CUDA, "batch workspace cudaMalloc(%zu) failed", bytes);
+            return nullptr;
+        }
+        b->owned.push_back(p);
+        return p;
+    };
+    int counters = 0;
+    size_t smem = (size_t)32 * 159 * 8;  // demodulation tile (DM_NE x DM_PITCH float2)
+    int maxr = 1, zpmax = 1;
+    std::vector<int4> segA, segRest;
+    int unit = 0;
+    b->ens.resize(n);
+    for (int e = 0; e < n && st == RCA_OK; ++e) {
+        const rca_batch_item& it = items[e];
+        const rca_tables* t = it.tables;
+        const GeomDev& g = t->gd;
+        const int nt = 2 * g.K, F = it.n_frames;
+        BatchEns& E = b->ens[e];
+        E.g = g;
+        E.rf = it.rf;
+        E.scale = it.scale;
+        E.F = F;
+        E.planes = it.planes;
+        E.mean = (float*)alloc((size_t)nt * g.N * g.ns * 4);
+        E.iq = alloc((size_t)F * nt * g.ns * g.N * esz);
+        E.slices = (float2*)alloc((size_t)F * nt * g.nzs * g.N * 8);
+        E.tx_q16 = t->tx_q16;
+        E.rx_q16 = t->rx_q16;
+        E.W = t->W;
+        E.dmax = t->dmax;
+        E.chunks = t->s1.d_chunks;
+        E.zt = t->s1.zt;
+        E.dc = t->s1.dc;
+        E.n_tiles = t->s1.n_tiles;
+        E.nch = t->s1.nch;
+        E.win = t->s1.win;
+        E.mix = t->mix;
+        E.sfl = t->s2_sfl;
+        E.sfr = t->s2_sfr;
+        E.psi = t->s2_psi;
+        E.ec = t->s2_ec;
+        E.coef = t->s2_coef;
+        E.tmin = t->s2_tmin;
+        E.T = t->T;
+        E.zp = t->s2.zp;
+        E.rows = t->s2.rows;
+        E.smin0 = t->s2.smin[0];
+        E.smin1 = t->s2.smin[1];
+        E.n_tiles2 = t->s2.n_tiles;
+        const int ncol = nt * g.N * g.ns;
+        const int nbx = (g.ns + 127) / 128, nby = (g.N + 31) / 32;
+        E.nA = (ncol / 4 + 255) / 256;
+        E.nB_fk = nbx * nby;
+        E.nB = E.nB_fk * F * nt;
+        E.nC = E.n_tiles * nt * F;
+        E.nD = E.n_tiles2 * 2 * F;
+        E.cA = counters;
+        E.cB0 = counters + 1;
+        E.cC0 = counters + 1 + F * nt;
+        counters += 1 + F * nt + F;
+        segA.push_back(make_int4(BS_MEAN, e, 0, E.nA));
+        segRest.push_back(make_int4(BS_DEMOD, e, 0, E.nB));
+        segRest.push_back(make_int4(BS_STAGE1, e, 0, E.nC));
+        segRest.push_back(make_int4(BS_STAGE2, e, 0, E.nD));
+        int LW = (g.N + 31) / 32, RG = std::max(1, 8 / LW);
+        maxr = std::max(maxr, (E.zt + RG - 1) / RG);
+        while (zpmax < E.zp) zpmax <<= 1;
+        smem = std::max(smem, stage1_smem_bytes(t, E.zt, E.dc, E.win, esz));
+        smem = std::max(smem, stage2_smem_bytes(t, E.zp));
+        if (prm) {
+            b->A.push_back((float*)alloc((size_t)F * 2 * g.S * g.nz * g.N * 4));
+            b->M.push_back((float*)alloc((size_t)F * 4));
+        }
+    }
+    if (st != RCA_OK) {
+        batch_free(b);
+        delete b;
+        return st;
+    }
+    if (maxr > 16 || smem > 200 * 1024) {
+        batch_free(b);
+        delete b;
+        return set_error(h, RCA_ERR_UNSUPPORTED, "batch tile shapes exceed the persistent kernel limits");
+    }
+    for (auto& sg : segA) {
+        b->segs.push_back(make_int4(sg.x, sg.y, unit, sg.w));
+        unit += sg.w;
+    }
+    for (auto& sg : segRest) {
+        b->segs.push_back(make_int4(sg.x, sg.y, unit, sg.w));
+        unit += sg.w;
+    }
+    b->total = unit;
+    b->n_counters = counters;
+    b->maxr = maxr;
+    b->zpmax = zpmax;
+    b->smem = smem;
+    if (cudaMalloc(&b->d_ens, sizeof(BatchEns) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_segs, sizeof(int4) * b->segs.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_cnt, sizeof(int) * (counters + 2)) != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return set_error(h, RCA_ERR_CUDA, "batch descriptor cudaMalloc failed");
+    }
+    cudaMemcpy(b->d_ens, b->ens.data(), sizeof(BatchEns) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_segs, b->segs.data(), sizeof(int4) * b->segs.size(), cudaMemcpyHostToDevice);
+    if (prm) {
+        b->localise = true;
+        b->prm = *prm;
+        b->lh = new (std::nothrow) rca_handle();
+        if (!b->lh) {
+            batch_free(b);
+            delete b;
+            return set_error(h, RCA_ERR_CUDA, "out of host memory");
+        }
+        b->lh->device = h->device;
+        b->lh->d_status = h->d_status;
+        for (int e = 0; e < n; ++e) {
+            b->tabs.push_back(items[e].tables);
+            b->out2d.push_back(items[e].out2d);
+            b->out3d.push_back(items[e].out3d);
+            b->cap2d.push_back(items[e].cap2d);
+            b->cap3d.push_back(items[e].cap3d);
+            b->n2d.push_back(items[e].n2d_dev);
+            b->n3d.push_back(items[e].n3d_dev);
+        }
+    }
+    *out = b;
+    return RCA_OK;
+}
+
+static rca_status batch_enqueue(rca_batch* b)
+{
+    rca_status st = launch_batch(b->h, b);
+    if (st != RCA_OK || !b->localise) return st;
+    rca_handle* h = b->lh;
+    h->stream = b->h->stream;
+    for (int e = 0; e < b->n; ++e) {
+        const rca_tables* t = b->tabs[e];
+        const int F = b->ens[e].F;
+        if ((st = launch_enhance(h, t, b->ens[e].planes, b->pl_t, F, b->prm.enh, b->A[e], b->M[e])) != RCA_OK) return st;
+        if ((st = launch_detect2d(h, t, b->A[e], b->M[e], F, &b->prm, b->out2d[e], b->cap2d[e], b->n2d[e], nullptr,
+                                  nullptr)) != RCA_OK)
+            return st;
+        if ((st = launch_pair3d(h, t, b->out2d[e], b->n2d[e], b->cap2d[e], F, b->out3d[e], b->cap3d[e], b->n3d[e])) != RCA_OK)
+            return st;
+    }
+    if (!h->last_error.empty()) b->h->last_error = h->last_error;
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_batch_run(rca_batch* b, int use_graph)
+{
+    if (!b) return RCA_ERR_INVALID_ARG;
+    rca_handle* h = b->h;
+    DeviceGuard dg(h->device);
+    if (!use_graph) return batch_enqueue(b);
+    if (!b->exec) {
+        // one plain run sizes every workspace, then the same work is captured
+        rca_status st = batch_enqueue(b);
+        if (st != RCA_OK) return st;
+        if ((st = cuda_check(h, cudaStreamSynchronize(h->stream), "batch warm-up")) != RCA_OK) return st;
+        if (!b->cap_stream &&
+            (st = cuda_check(h, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "capture stream")) != RCA_OK)
+            return st;
+        cudaStream_t user = h->stream;
+        h->stream = b->cap_stream;
+        cudaGraph_t graph = nullptr;
+        st = cuda_check(h, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        if (st == RCA_OK) {
+            rca_status st2 = batch_enqueue(b);
+            st = cuda_check(h, cudaStreamEndCapture(b->cap_stream, &graph), "end capture");
+            if (st2 != RCA_OK) st = st2;
+        }
+        h->stream = user;
+        if (st == RCA_OK) st = cuda_check(h, cudaGraphInstantiate(&b->exec, graph, 0), "graph instantiate");
+        if (graph) cudaGraphDestroy(graph);
+        if (st != RCA_OK) return st;
+        return RCA_OK;  // the warm-up run already produced this run's results
+    }
+    return cuda_check(h, cudaGraphLaunch(b->exec, h->stream), "graph launch");
+}
+
+extern "C" rca_status rca_batch_set_wait_limit(rca_batch* b, long long cycles, int block_ensemble)
+{
+    if (!b || cycles <= 0 || block_ensemble >= b->n) return RCA_ERR_INVALID_ARG;
+    DeviceGuard dg(b->h->device);
+    b->wait_limit = cycles;
+    if (block_ensemble >= 0) {
+        BatchEns E = b->ens[block_ensemble];
+        E.nB_fk += 1;  // Stage-1 units now wait for a demodulation unit that does not exist
+        cudaMemcpy(b->d_ens + block_ensemble, &E, sizeof(BatchEns), cudaMemcpyHostToDevice);
+    }
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return RCA_OK;
+}
+
+extern "C" rca_status rca_batch_destroy(rca_batch* b)
+{
+    if (!b) return RCA_ERR_INVALID_ARG;
+    DeviceGuard dg(b->h->device);
+    cudaStreamSynchronize(b->h->stream);
+    batch_free(b);
+    delete b;
+    return RCA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+extern "C" rca_status rca_autotune(rca_handle* h, rca_tables* t, const void* iq, rca_dtype iq_t, int F, int* zt_out,
+                                   int* dc_out, int* zp_out)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!iq || !is_complex(iq_t)) return set_error(h, RCA_ERR_INVALID_ARG, "null or non-complex IQ");
+    if (capturing(h)) return set_error(h, RCA_ERR_INVALID_ARG, "rca_autotune cannot run during stream capture");
+    DeviceGuard dg(h->device);
+    const GeomDev& g = t->gd;
+    float2* slices = (float2*)ws_get(h, WS_SLICES, (size_t)F * 2 * g.K * g.nzs * g.N * sizeof(float2), &st);
+    if (!slices) return st;
+    void* planes = ws_get(h, WS_A, (size_t)F * 4 * g.S * g.nz * g.N * sizeof(float2), &st);
+    if (!planes) return st;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_it = [&](auto fn) -> float {
+        fn();  // warm-up
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 3; ++r) fn();
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const size_t esz = dtype_size(iq_t);
+    const int shapes[][2] = {{32, 8}, {16, 16}, {16, 8}, {16, 4}, {8, 16}, {8, 8}, {8, 4}, {4, 8}, {4, 4}};
+    float best = 1e30f;
+    int bz = t->s1.zt, bd = t->s1.dc;
+    for (auto& sh : shapes) {
+        const int zt = sh[0], dc = sh[1];
+        const int win = stage1_window(t, zt, dc, nullptr);
+        if (stage1_smem_bytes(t, zt, dc, win, esz) > 200 * 1024) continue;
+        const int LW = (g.N + 31) / 32, RG = std::max(1, 8 / LW);
+        if ((zt + RG - 1) / RG > 16) continue;
+        if ((st = plan_stage1(h, t, zt, dc)) != RCA_OK) break;
+        const float ms = time_it([&] { launch_stage1(h, t, iq, iq_t, F, slices); });
+        if (ms < best) {
+            best = ms;
+            bz = zt;
+            bd = dc;
+        }
+    }
+    if (st == RCA_OK) st = plan_stage1(h, t, bz, bd);
+    // Stage 2 on the slices of the chosen shape
+    if (st == RCA_OK) st = launch_stage1(h, t, iq, iq_t, F, slices);
+    float best2 = 1e30f;
+    int bzp = t->s2.zp;
+    for (int zp = 1; zp <= 16 && st == RCA_OK; zp <<= 1) {
+        if (stage2_smem_bytes(t, zp) > 200 * 1024) break;
+        plan_stage2(t, zp);
+        const float ms = time_it([&] { launch_stage2(h, t, slices, F, planes, RCA_C32); });
+        if (ms < best2) {
+            best2 = ms;
+            bzp = zp;
+        }
+    }
+    plan_stage2(t, bzp);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RCA_OK) return st;
+    st = cuda_check(h, cudaStreamSynchronize(h->stream), "autotune");
+    if (zt_out) *zt_out = bz;
+    if (dc_out) *dc_out = bd;
+    if (zp_out) *zp_out = bzp;
+    return st;
+}

@@ -44,10 +44,11 @@ __device__ __forceinline__ void rf_load4(const void* rf, int rf_t, size_t i, flo
     }
 }
 
-__global__ void __launch_bounds__(256) k_mean(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
-                                              int F, int ns, int ncol, float* __restrict__ mean)
+__device__ __forceinline__ void mean_body(int bx, const void* __restrict__ rf, int rf_t,
+                                          const float* __restrict__ scale, int F, int ns, int ncol,
+                                          float* __restrict__ mean)
 {
-    const int c4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int c4 = (bx * blockDim.x + threadIdx.x) * 4;
     if (c4 >= ncol) return;
     const size_t stride = (size_t)ncol;
     float s[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
@@ -92,20 +93,26 @@ __global__ void __launch_bounds__(256) k_mean(const void* __restrict__ rf, int r
     }
 }
 
+__global__ void __launch_bounds__(256) k_mean(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
+                                              int F, int ns, int ncol, float* __restrict__ mean)
+{
+    mean_body(blockIdx.x, rf, rf_t, scale, F, ns, ncol, mean);
+}
+
 #define DM_NT 128           // samples per CTA
 #define DM_NE 32            // elements per CTA
 #define DM_PITCH (DM_NT + 31)  // odd float2 pitch: conflict-free column reads
 
 // CTA = (128 samples, 32 elements, one frame-transmission).  Reads RF rows
 // [e][n] coalesced along n, writes IQ [n][e] coalesced along e.
-__global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
-                                               const float* __restrict__ mean, const float2* __restrict__ mix, Fir fir,
-                                               int nt, int E, int ns, void* __restrict__ iq, int iq_t)
+__device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __restrict__ xs,
+                                           const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
+                                           const float* __restrict__ mean, const float2* __restrict__ mix,
+                                           const Fir& fir, int nt, int E, int ns, void* __restrict__ iq, int iq_t)
 {
-    __shared__ float2 xs[DM_NE * DM_PITCH];
-    const int n0 = blockIdx.x * DM_NT;
-    const int e0 = blockIdx.y * DM_NE;
-    const int fk = blockIdx.z;
+    const int n0 = bx * DM_NT;
+    const int e0 = by * DM_NE;
+    const int fk = bz;
     const int k = fk % nt;
     const size_t chan0 = (size_t)fk * E;
 #pragma unroll 4
@@ -137,6 +144,14 @@ __global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int 
         }
         store_c(iq, ((size_t)fk * ns + n) * E + e, iq_t, make_float2(2.f * re, 2.f * im));
     }
+}
+
+__global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
+                                               const float* __restrict__ mean, const float2* __restrict__ mix, Fir fir,
+                                               int nt, int E, int ns, void* __restrict__ iq, int iq_t)
+{
+    __shared__ float2 xs[DM_NE * DM_PITCH];
+    demod_body(blockIdx.x, blockIdx.y, blockIdx.z, xs, rf, rf_t, scale, mean, mix, fir, nt, E, ns, iq, iq_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,20 +227,19 @@ __device__ __forceinline__ void lerp_acc2(uint64_t& A1, uint64_t& A2, unsigned a
     A2 = f2_fma(wyp, v, A2);
 }
 
+// returns false if a bounded wait ran out (the CTA must stop)
 template <typename TS, int MAXR>
-__global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __restrict__ iq,
-                                                const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
-                                                const float2* __restrict__ W, const int* __restrict__ dmax,
-                                                const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch,
-                                                int win, float2* __restrict__ slices, unsigned* __restrict__ status)
+__device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned char* __restrict__ smraw,
+                                            uint64_t* bars, const GeomDev& g, const void* __restrict__ iq,
+                                            const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
+                                            const float2* __restrict__ W, const int* __restrict__ dmax,
+                                            const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch,
+                                            int win, float2* __restrict__ slices, unsigned* __restrict__ status)
 {
-    extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ uint64_t bars[2];
     const int E = g.N, N = g.N;
     TS* bufs = reinterpret_cast<TS*>(smraw);                  // [2][win][E]
     RowD* recs = reinterpret_cast<RowD*>(bufs + 2 * (size_t)win * E);  // [2][zt][dc]
     int* dcnt = reinterpret_cast<int*>(recs + 2 * zt * dc);  // [2][zt]
-    const int tile = blockIdx.x, k = blockIdx.y, f = blockIdx.z;
     const int nt = 2 * g.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int LW = (N + 31) >> 5;
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
             const int r = r0 + rr;
             dcnt[b * zt + rr] = r < rend ? max(0, min(cc.w, __ldg(dmax + r) + 1) - cc.z) : 0;
         }
-        if (!cta_wait_copies(&bars[b], (phase >> b) & 1u, status)) return;
+        if (!cta_wait_copies(&bars[b], (phase >> b) & 1u, status)) return false;
         phase ^= 1u << b;
         if (c + 1 < nch) issue(c + 1, b ^ 1);
         if (cc.y == 0) continue;
@@ -357,6 +371,20 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
             slices[(((size_t)f * nt + k) * g.nzs + r) * N + l] = make_float2(p1.x - p2.y, p1.y + p2.x);
         }
     }
+    return true;
+}
+
+template <typename TS, int MAXR>
+__global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __restrict__ iq,
+                                                const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
+                                                const float2* __restrict__ W, const int* __restrict__ dmax,
+                                                const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch,
+                                                int win, float2* __restrict__ slices, unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint64_t bars[2];
+    stage1_body<TS, MAXR>(blockIdx.x, blockIdx.y, blockIdx.z, smraw, bars, g, iq, tx_q16, rx_q16, W, dmax, chunks,
+                          zt, dc, n_tiles, nch, win, slices, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,20 +399,19 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
 // CR: transverse = x -> YZ planes (axis 1), lateral-slab -> XZ (axis 0).
 // ---------------------------------------------------------------------------
 template <int ZP>
-__global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restrict__ slices,
-                                                const int* __restrict__ sfl, const float* __restrict__ sfr,
-                                                const float2* __restrict__ psi, const float2* __restrict__ ec,
-                                                const float2* __restrict__ coef, const int* __restrict__ tmin, int T,
-                                                int rows, int smin0, int smin1, void* __restrict__ planes, int pt,
-                                                unsigned* __restrict__ status)
+__device__ __forceinline__ bool stage2_body(int tile, int fam, int f, int zp, float2* __restrict__ sm, uint64_t* barp,
+                                            const GeomDev& g, const float2* __restrict__ slices,
+                                            const int* __restrict__ sfl, const float* __restrict__ sfr,
+                                            const float2* __restrict__ psi, const float2* __restrict__ ec,
+                                            const float2* __restrict__ coef, const int* __restrict__ tmin, int T,
+                                            int rows, int smin0, int smin1, void* __restrict__ planes, int pt,
+                                            unsigned* __restrict__ status)
 {
-    extern __shared__ __align__(128) float2 sm[];
-    __shared__ uint64_t bar;
+    uint64_t& bar = *barp;
     const int N = g.N, K = g.K, S = g.S, P = g.P, us = g.us;
-    const int tile = blockIdx.x, fam = blockIdx.y, f = blockIdx.z;
     const int nt = 2 * K;
-    const int i0 = tile * ZP;
-    const int nrow = min(ZP, g.nz - i0);
+    const int i0 = tile * zp;          // zp <= ZP plane rows per tile
+    const int nrow = min(zp, g.nz - i0);
     const int smin = fam ? smin1 : smin0;
     const int rlo = us * i0 + smin;
     float2* sS = sm;                                 // [K][rows][N]
@@ -437,7 +464,7 @@ __global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restr
         sEc[idx] = __ldg(ec + (size_t)(fam * K + kk) * g.nz + min(i0 + ii, g.nz - 1));
     }
     for (int idx = threadIdx.x; idx < K * S; idx += blockDim.x) sTb[idx] = __ldg(tmin + fam * K * S + idx) - smin;
-    if (!cta_wait_copies(&bar, 0, status)) return;
+    if (!cta_wait_copies(&bar, 0, status)) return false;
     // slab sums over the lateral pixels: one warp per (k, row)
     for (int o = warp; o < K * rows; o += nwarp) {
         const int kk = o / rows, rr = o - kk * rows;
@@ -482,10 +509,12 @@ __global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restr
             for (int t = 0; t < T; ++t) {
 #pragma unroll
                 for (int ii = 0; ii < ZP; ++ii) {
-                    const float2 c = cf[ii * T + t];
-                    const uint64_t v = col[(size_t)(us * ii + t) * N];
-                    a1[ii] = f2_fma(f2_pack(c.x, c.x), v, a1[ii]);
-                    a2[ii] = f2_fma(f2_pack(c.y, c.y), v, a2[ii]);
+                    if (ii < nrow) {
+                        const float2 c = cf[ii * T + t];
+                        const uint64_t v = col[(size_t)(us * ii + t) * N];
+                        a1[ii] = f2_fma(f2_pack(c.x, c.x), v, a1[ii]);
+                        a2[ii] = f2_fma(f2_pack(c.y, c.y), v, a2[ii]);
+                    }
                 }
             }
         }
@@ -517,7 +546,7 @@ __global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restr
             for (int ii = 0; ii < ZP; ++ii) {
                 const int nr = us * ii + n0r;
                 const int n0 = rlo + nr;          // slice row
-                const bool valid = n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f));
+                const bool valid = ii < nrow && n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f));
                 if (valid) {
                     const float2 s0 = src[nr], s1 = src[nr + 1];
                     const float2 v = make_float2(fmaf(fr, s1.x - s0.x, s0.x), fmaf(fr, s1.y - s0.y, s0.y));
@@ -530,6 +559,21 @@ __global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restr
         for (int ii = 0; ii < ZP; ++ii)
             if (ii < nrow) store_c_cs(planes, ob + (size_t)ii * N, pt, acc[ii]);
     }
+    return true;
+}
+
+template <int ZP>
+__global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restrict__ slices,
+                                                const int* __restrict__ sfl, const float* __restrict__ sfr,
+                                                const float2* __restrict__ psi, const float2* __restrict__ ec,
+                                                const float2* __restrict__ coef, const int* __restrict__ tmin, int T,
+                                                int rows, int smin0, int smin1, void* __restrict__ planes, int pt,
+                                                unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) float2 sm[];
+    __shared__ uint64_t bar;
+    stage2_body<ZP>(blockIdx.x, blockIdx.y, blockIdx.z, ZP, sm, &bar, g, slices, sfl, sfr, psi, ec, coef, tmin, T,
+                    rows, smin0, smin1, planes, pt, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -647,6 +691,138 @@ __global__ void __launch_bounds__(256) k_direct(GeomDev g, const void* __restric
 }
 
 inline bool complex_dtype(rca_dtype t) { return t == RCA_C32 || t == RCA_C16F || t == RCA_C16BF; }
+
+
+// ---------------------------------------------------------------------------
+// Persistent batched beamforming.  Every CTA repeatedly takes the next work
+// unit from a device queue (mean units of all ensembles first, then per
+// ensemble demodulation, Stage 1 and Stage 2 units), waits -- bounded -- until
+// the unit's inputs are complete (per-ensemble counters), runs the same body
+// as the standalone kernel, and publishes its completion.  Units only wait
+// on units earlier in the queue, which were taken by CTAs already running,
+// so the queue always drains.  A wait that runs out sets ST_TIMEOUT and an
+// abort flag that stops every CTA at its next unit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename TS, int MAXR, int ZP>
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
+                                                 int nseg, int total, int* __restrict__ cnt, int n_counters,
+                                                 long long wait_limit, Fir fir, int rf_t, int iq_t, int pt,
+                                                 unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint64_t bars[2];
+    __shared__ int s_unit, s_ok;
+    int* next = cnt + n_counters;
+    int* abort_flag = cnt + n_counters + 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(next, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= total) break;
+        int sg = 0;
+        while (sg + 1 < nseg && segs[sg + 1].z <= u) ++sg;
+        const int4 SG = segs[sg];
+        const int stage = SG.x, e = SG.y, loc = u - SG.z;
+        const BatchEns& E = ens[e];
+        const GeomDev& g = E.g;
+        const int nt = 2 * g.K;
+        // decode the unit, its dependency and the counter it completes
+        int dep = -1, dep_target = 0, done = -1;
+        int a0 = 0, a1 = 0, a2 = 0;
+        if (stage == BS_MEAN) {
+            a0 = loc;
+            done = E.cA;
+        } else if (stage == BS_DEMOD) {
+            const int nbx = (g.ns + DM_NT - 1) / DM_NT, nby = (g.N + DM_NE - 1) / DM_NE;
+            a0 = loc % nbx;
+            a1 = (loc / nbx) % nby;
+            a2 = loc / (nbx * nby);  // f * nt + k
+            dep = E.cA;
+            dep_target = E.nA;
+            done = E.cB0 + a2;
+        } else if (stage == BS_STAGE1) {
+            a0 = loc % E.n_tiles;                // tile
+            a1 = (loc / E.n_tiles) % nt;         // k
+            a2 = loc / (E.n_tiles * nt);         // f
+            dep = E.cB0 + a2 * nt + a1;
+            dep_target = E.nB_fk;
+            done = E.cC0 + a2;
+        } else {
+            a0 = loc % E.n_tiles2;               // tile
+            a1 = (loc / E.n_tiles2) % 2;         // family
+            a2 = loc / (E.n_tiles2 * 2);         // f
+            dep = E.cC0 + a2;
+            dep_target = E.n_tiles * nt;
+        }
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (dep >= 0) {
+                const long long t0 = clock64();
+                while (ld_acquire(cnt + dep) < dep_target) {
+                    if (*(volatile int*)abort_flag) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > wait_limit) {
+                        atomicOr(status, ST_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                // order the producers' global writes before this CTA's TMA reads
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            if (*(volatile int*)abort_flag) ok = 0;
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        bool ok = true;
+        if (stage == BS_MEAN) {
+            mean_body(a0, E.rf, rf_t, E.scale, E.F, g.ns, nt * g.N * g.ns, E.mean);
+        } else if (stage == BS_DEMOD) {
+            demod_body(a0, a1, a2, reinterpret_cast<float2*>(smraw), E.rf, rf_t, E.scale, E.mean, E.mix, fir, nt, g.N,
+                       g.ns, E.iq, iq_t);
+        } else if (stage == BS_STAGE1) {
+            ok = stage1_body<TS, MAXR>(a0, a1, a2, smraw, bars, g, E.iq, E.tx_q16, E.rx_q16, E.W, E.dmax, E.chunks,
+                                       E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);
+        } else {
+            ok = stage2_body<ZP>(a0, a1, a2, E.zp, reinterpret_cast<float2*>(smraw), &bars[0], g, E.slices, E.sfl,
+                                 E.sfr, E.psi, E.ec, E.coef, E.tmin, E.T, E.rows, E.smin0, E.smin1, E.planes, pt,
+                                 status);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (stage == BS_STAGE1) {
+                mbar_inval(&bars[0]);
+                mbar_inval(&bars[1]);
+            } else if (stage == BS_STAGE2) {
+                mbar_inval(&bars[0]);
+            }
+            if (!ok) {
+                atomicExch(abort_flag, 1);
+            } else if (done >= 0) {
+                __threadfence();
+                atomicAdd(cnt + done, 1);
+            }
+        }
+        if (!ok) break;
+    }
+}
 
 }  // namespace
 
@@ -780,4 +956,57 @@ rca_status launch_direct(rca_handle* h, const rca_tables* t, const void* iq, rca
     if (per <= 8) return direct_launch<8>(h, t, iq, iq_t, F, planes, pt, threads);
     if (per <= 16) return direct_launch<16>(h, t, iq, iq_t, F, planes, pt, threads);
     return set_error(h, RCA_ERR_UNSUPPORTED, "direct row tile too tall");
+}
+
+// ---------------------------------------------------------------------------
+// batched launch
+// ---------------------------------------------------------------------------
+template <typename TS, int MAXR, int ZP>
+static rca_status batch_launch(rca_handle* h, rca_batch* b)
+{
+    auto kern = k_batch<TS, MAXR, ZP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "batch smem attribute");
+    if (b->grid == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, b->smem);
+        b->grid = std::max(1, per_sm) * sms;
+    }
+    Fir fir;
+    for (int q = 0; q < 31; ++q) fir.h[q] = b->fir[q];
+    cudaMemsetAsync(b->d_cnt, 0, sizeof(int) * (b->n_counters + 2), h->stream);
+    kern<<<b->grid, 256, b->smem, h->stream>>>(b->d_ens, b->d_segs, (int)b->segs.size(), b->total, b->d_cnt,
+                                               b->n_counters, b->wait_limit, fir, (int)b->rf_t, (int)b->iq_t,
+                                               (int)b->pl_t, h->d_status);
+    return cuda_check(h, cudaGetLastError(), "batch kernel");
+}
+
+template <typename TS, int MAXR>
+static rca_status batch_zp(rca_handle* h, rca_batch* b)
+{
+    switch (b->zpmax) {
+    case 1: return batch_launch<TS, MAXR, 1>(h, b);
+    case 2: return batch_launch<TS, MAXR, 2>(h, b);
+    case 4: return batch_launch<TS, MAXR, 4>(h, b);
+    case 8: return batch_launch<TS, MAXR, 8>(h, b);
+    default: return batch_launch<TS, MAXR, 16>(h, b);
+    }
+}
+
+template <typename TS>
+static rca_status batch_maxr(rca_handle* h, rca_batch* b)
+{
+    if (b->maxr <= 2) return batch_zp<TS, 2>(h, b);
+    if (b->maxr <= 4) return batch_zp<TS, 4>(h, b);
+    if (b->maxr <= 8) return batch_zp<TS, 8>(h, b);
+    return batch_zp<TS, 16>(h, b);
+}
+
+rca_status launch_batch(rca_handle* h, rca_batch* b)
+{
+    if (b->iq_t == RCA_C32) return batch_maxr<float2>(h, b);
+    if (b->iq_t == RCA_C16F) return batch_maxr<__half2>(h, b);
+    return batch_maxr<__nv_bfloat162>(h, b);
 }

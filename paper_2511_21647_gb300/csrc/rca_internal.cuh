@@ -121,7 +121,16 @@ struct rca_tables {
     Stage2Plan s2;
     int direct_win = 0;         // window for direct mode (rows of samples)
     int direct_zt = 0;
+    // host copies used to (re)plan launch shapes
+    std::vector<int> h_txq, h_rxq, h_dm, h_sfl;
 };
+
+// launch-shape planning (tables.cu)
+int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* chunks);
+size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t esz);
+rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc);
+size_t stage2_smem_bytes(const rca_tables* t, int zp);
+void plan_stage2(rca_tables* t, int zp);
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -341,3 +350,77 @@ __device__ __forceinline__ void lds_u64x2(unsigned addr, uint64_t& a, uint64_t& 
 {
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
+
+// ---------------------------------------------------------------------------
+// batched form: one persistent launch over the beamforming work of many
+// ensembles (ingest mean, demodulation, Stage 1, Stage 2), ordered by a
+// device work queue with per-ensemble dependency counters
+// ---------------------------------------------------------------------------
+enum BatchStage { BS_MEAN = 0, BS_DEMOD = 1, BS_STAGE1 = 2, BS_STAGE2 = 3 };
+
+struct BatchEns {
+    GeomDev g;
+    const void* rf;
+    const float* scale;
+    int F;
+    float* mean;
+    void* iq;
+    float2* slices;
+    void* planes;
+    // tables
+    const int* tx_q16;
+    const int* rx_q16;
+    const float2* W;
+    const int* dmax;
+    const int4* chunks;
+    int zt, dc, n_tiles, nch, win;
+    const float2* mix;
+    const int* sfl;
+    const float* sfr;
+    const float2* psi;
+    const float2* ec;
+    const float2* coef;
+    const int* tmin;
+    int T, zp, rows, smin0, smin1, n_tiles2;
+    // work units and counters
+    int nA, nB, nC, nD;      // units per stage
+    int nB_fk;               // demodulation units per (frame, transmission)
+    int cA, cB0, cC0;        // counter indices: mean done, demod done per (f, k), Stage 1 done per f
+};
+
+struct rca_batch {
+    rca_handle* h = nullptr;
+    int n = 0;
+    rca_dtype rf_t = RCA_F32, iq_t = RCA_C32, pl_t = RCA_C32;
+    std::vector<BatchEns> ens;
+    std::vector<int4> segs;       // {stage, ensemble, first unit, count}
+    int total = 0;                // work units
+    int n_counters = 0;
+    BatchEns* d_ens = nullptr;
+    int4* d_segs = nullptr;
+    int* d_cnt = nullptr;         // [n_counters + 2]: counters, next-unit, abort
+    std::vector<void*> owned;     // per-ensemble workspace
+    float fir[31];
+    long long wait_limit = RCA_WAIT_CYCLES;
+    int maxr = 2, zpmax = 1;
+    size_t smem = 0;
+    int grid = 0;
+    // optional localisation
+    bool localise = false;
+    ulm_params prm{};
+    std::vector<const rca_tables*> tabs;
+    std::vector<ulm_loc2d*> out2d;
+    std::vector<ulm_loc3d*> out3d;
+    std::vector<int> cap2d, cap3d;
+    std::vector<int*> n2d, n3d;
+    std::vector<float*> A, M;
+    // private handle for the localisation workspace (shares the caller's
+    // status word), so a captured graph never points at buffers that other
+    // calls on the caller's handle could reallocate
+    rca_handle* lh = nullptr;
+    // CUDA graph of one batch run
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+};
+
+rca_status launch_batch(rca_handle* h, rca_batch* b);

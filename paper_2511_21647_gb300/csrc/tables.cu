@@ -285,66 +285,26 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
                                                                  h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "coef kernel")) != RCA_OK) return st;
 
-    // Stage-1 chunks: row tiles of zt slice rows, lateral distances in chunks
-    // of dc; each chunk's sample window is contiguous in the [ns][E] IQ block.
-    auto plan = [&](int zt, int dc, std::vector<int4>* out) {
-        int tiles = (g.nzs + zt - 1) / zt, nch = (g.N + dc - 1) / dc, win = 0;
-        if (out) out->assign((size_t)nt * tiles * nch, make_int4(0, 0, 0, 0));
-        for (int k = 0; k < nt; ++k)
-            for (int tt = 0; tt < tiles; ++tt)
-                for (int c = 0; c < nch; ++c) {
-                    int d0 = c * dc, d1 = std::min(g.N, d0 + dc);
-                    long lo = 1L << 40, hi = -(1L << 40);
-                    for (int r = tt * zt; r < std::min(g.nzs, (tt + 1) * zt); ++r) {
-                        if (dm[r] < d0) continue;
-                        long tq = txq[(size_t)k * g.nzs + r];
-                        lo = std::min(lo, (tq + rxq[(size_t)r * g.N + d0]) >> 16);
-                        hi = std::max(hi, (tq + rxq[(size_t)r * g.N + std::min(d1 - 1, dm[r])]) >> 16);
-                    }
-                    int nrows = hi >= lo ? (int)(hi - lo + 2) : 0;
-                    win = std::max(win, nrows);
-                    if (out) (*out)[((size_t)k * tiles + tt) * nch + c] = make_int4((int)lo, nrows, d0, d1);
-                }
-        return win;
-    };
-    // two sample windows (double buffer) plus the per-(row, d) records must
-    // leave room for two CTAs per SM
+    t->h_txq = txq;
+    t->h_rxq = rxq;
+    t->h_dm = dm;
+    t->h_sfl = sfl;
+    // Stage 1: the tallest row tile / widest distance chunk whose double
+    // buffer leaves room for two CTAs per SM (the autotuner may replace it)
     const size_t budget = 104 * 1024;
     const int shapes[][2] = {{16, 16}, {16, 8}, {8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {1, 1}};
     int zt = 1, dc = 1;
     for (auto& sh : shapes) {
         zt = sh[0];
         dc = sh[1];
-        size_t need = 2 * (size_t)plan(zt, dc, nullptr) * g.N * sizeof(float2) + 2 * (size_t)zt * dc * 32 + 2 * zt * 4;
-        if (need <= budget) break;
+        if (stage1_smem_bytes(t, zt, dc, stage1_window(t, zt, dc, nullptr), sizeof(float2)) <= budget) break;
     }
-    std::vector<int4> chunks;
-    t->s1.zt = zt;
-    t->s1.dc = dc;
-    t->s1.win = plan(zt, dc, &chunks);
-    t->s1.n_tiles = (g.nzs + zt - 1) / zt;
-    t->s1.nch = (g.N + dc - 1) / dc;
-    if (2 * (size_t)t->s1.win * g.N * sizeof(float2) > 200 * 1024)
-        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 sample window of %d samples x %d elements exceeds shared memory",
-                         t->s1.win, g.N);
-    t->s1.d_chunks = dalloc<int4>(h, chunks.size(), &st);
-    if (st != RCA_OK) return st;
-    cudaMemcpyAsync(t->s1.d_chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
-
-    // Stage-2 plane-row tile.
-    int span = std::max(t->s2.smax[0] - t->s2.smin[0], t->s2.smax[1] - t->s2.smin[1]) + 2;
+    if ((st = plan_stage1(h, t, zt, dc)) != RCA_OK) return st;
+    // Stage 2: the tallest plane-row tile that fits the same budget
     int zp = 16;
-    auto s2_bytes = [&](int z) {
-        int rows = g.us * (z - 1) + span;
-        return (size_t)g.K * rows * g.N * sizeof(float2) + (size_t)g.K * g.S * rows * sizeof(float2) +
-               (size_t)g.K * g.S * z * T * sizeof(float2) + (size_t)g.K * g.N * 16 + (size_t)g.K * z * 8 +
-               (size_t)g.K * g.S * 4;
-    };
-    while (zp > 1 && s2_bytes(zp) > 110 * 1024) zp /= 2;
-    t->s2.zp = zp;
-    t->s2.rows = g.us * (zp - 1) + span;
-    t->s2.n_tiles = (g.nz + zp - 1) / zp;
-    if (s2_bytes(zp) > 200 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 tile exceeds shared memory");
+    while (zp > 1 && stage2_smem_bytes(t, zp) > 110 * 1024) zp /= 2;
+    if (stage2_smem_bytes(t, zp) > 200 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 tile exceeds shared memory");
+    plan_stage2(t, zp);
 
     // Direct mode windows (per transverse position; rows of plane depth).
     {
@@ -371,4 +331,86 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
         t->direct_win = win;
     }
     return cuda_check(h, cudaStreamSynchronize(s), "table build");
+}
+
+// ---------------------------------------------------------------------------
+// launch-shape planning from the host copies of the tables
+// ---------------------------------------------------------------------------
+// Stage-1 chunks: row tiles of zt slice rows, lateral distances in chunks of
+// dc; each chunk's sample window is contiguous in the [ns][E] IQ block.
+// Returns the largest window (rows); fills chunks {nlo, nrows, d0, d1}.
+int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* out)
+{
+    const GeomDev& g = t->gd;
+    const int nt = 2 * g.K;
+    const int tiles = (g.nzs + zt - 1) / zt, nch = (g.N + dc - 1) / dc;
+    int win = 0;
+    if (out) out->assign((size_t)nt * tiles * nch, make_int4(0, 0, 0, 0));
+    for (int k = 0; k < nt; ++k)
+        for (int tt = 0; tt < tiles; ++tt)
+            for (int c = 0; c < nch; ++c) {
+                const int d0 = c * dc, d1 = std::min(g.N, d0 + dc);
+                long lo = 1L << 40, hi = -(1L << 40);
+                for (int r = tt * zt; r < std::min(g.nzs, (tt + 1) * zt); ++r) {
+                    if (t->h_dm[r] < d0) continue;
+                    const long tq = t->h_txq[(size_t)k * g.nzs + r];
+                    lo = std::min(lo, (tq + t->h_rxq[(size_t)r * g.N + d0]) >> 16);
+                    hi = std::max(hi, (tq + t->h_rxq[(size_t)r * g.N + std::min(d1 - 1, t->h_dm[r])]) >> 16);
+                }
+                const int nrows = hi >= lo ? (int)(hi - lo + 2) : 0;
+                win = std::max(win, nrows);
+                if (out) (*out)[((size_t)k * tiles + tt) * nch + c] = make_int4((int)lo, nrows, d0, d1);
+            }
+    return win;
+}
+
+// double-buffered windows + per-(row, d) records (32 B) + per-row counts
+size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t esz)
+{
+    return 2 * (size_t)win * t->gd.N * esz + 2 * (size_t)zt * dc * 32 + 2 * (size_t)zt * 4;
+}
+
+rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
+{
+    std::vector<int4> chunks;
+    const int win = stage1_window(t, zt, dc, &chunks);
+    if (stage1_smem_bytes(t, zt, dc, win, sizeof(float2)) > 200 * 1024)
+        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 sample window of %d samples x %d elements exceeds shared memory",
+                         win, t->gd.N);
+    int4* d = nullptr;
+    rca_status st = RCA_OK;
+    d = dalloc<int4>(h, chunks.size(), &st);
+    if (st != RCA_OK) return st;
+    st = cuda_check(h, cudaMemcpyAsync(d, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream),
+                    "chunk upload");
+    if (st == RCA_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "chunk upload sync");
+    if (st != RCA_OK) {
+        cudaFree(d);
+        return st;
+    }
+    if (t->s1.d_chunks) cudaFree(t->s1.d_chunks);
+    t->s1.d_chunks = d;
+    t->s1.zt = zt;
+    t->s1.dc = dc;
+    t->s1.win = win;
+    t->s1.n_tiles = (t->gd.nzs + zt - 1) / zt;
+    t->s1.nch = (t->gd.N + dc - 1) / dc;
+    return RCA_OK;
+}
+
+size_t stage2_smem_bytes(const rca_tables* t, int zp)
+{
+    const GeomDev& g = t->gd;
+    const int span = std::max(t->s2.smax[0] - t->s2.smin[0], t->s2.smax[1] - t->s2.smin[1]) + 2;
+    const int rows = g.us * (zp - 1) + span;
+    return (size_t)g.K * rows * g.N * 8 + (size_t)g.K * g.S * rows * 8 + (size_t)g.K * g.S * zp * t->T * 8 +
+           (size_t)g.K * g.N * 8 + (size_t)g.K * zp * 8 + ((size_t)2 * g.K * g.N + (size_t)g.K * g.S) * 4;
+}
+
+void plan_stage2(rca_tables* t, int zp)
+{
+    const int span = std::max(t->s2.smax[0] - t->s2.smin[0], t->s2.smax[1] - t->s2.smin[1]) + 2;
+    t->s2.zp = zp;
+    t->s2.rows = t->gd.us * (zp - 1) + span;
+    t->s2.n_tiles = (t->gd.nz + zp - 1) / zp;
 }

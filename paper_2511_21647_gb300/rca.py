@@ -11,7 +11,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib as L
-from ._lib import LOC2D, LOC3D, rca_bf_params, rca_geometry_desc, ulm_params  # noqa: F401
+from ._lib import LOC2D, LOC3D, rca_batch_item, rca_bf_params, rca_geometry_desc, ulm_params  # noqa: F401
 
 
 class RcaError(RuntimeError):
@@ -188,3 +188,46 @@ def ulm_pair3d(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
 def ulm_localize(h, t, planes, planes_dtype, n_frames, prm: ulm_params, out2d, cap2d, n2d, out3d, cap3d, n3d):
     _check(L.load().ulm_localize(h, t, _ptr(planes), planes_dtype, n_frames, C.byref(prm), _ptr(out2d), cap2d,
                                  _ptr(n2d), _ptr(out3d), cap3d, _ptr(n3d)), h)
+
+
+def rca_batch_create(h, items, rf_dtype, iq_dtype, planes_dtype, prm=None):
+    """items: sequence of dicts with keys tables, rf, scale, n_frames, planes and
+    (with prm) out2d, cap2d, n2d, out3d, cap3d, n3d (tensors or pointers)."""
+    arr = (rca_batch_item * len(items))()
+    keep = []
+    for q, it in enumerate(items):
+        a = arr[q]
+        a.tables = it["tables"]
+        a.rf = _ptr(it["rf"])
+        a.scale = _ptr(it.get("scale"))
+        a.n_frames = it["n_frames"]
+        a.planes = _ptr(it["planes"])
+        a.out2d = _ptr(it.get("out2d"))
+        a.cap2d = it.get("cap2d", 0)
+        a.n2d_dev = _ptr(it.get("n2d"))
+        a.out3d = _ptr(it.get("out3d"))
+        a.cap3d = it.get("cap3d", 0)
+        a.n3d_dev = _ptr(it.get("n3d"))
+        keep.append(it)
+    b = C.c_void_p()
+    _check(L.load().rca_batch_create(h, len(items), arr, rf_dtype, iq_dtype, planes_dtype,
+                                     C.byref(prm) if prm is not None else None, C.byref(b)), h)
+    return b
+
+
+def rca_batch_run(b, use_graph=False, h=None):
+    _check(L.load().rca_batch_run(b, int(bool(use_graph))), h, "rca_batch_run")
+
+
+def rca_batch_set_wait_limit(b, cycles, block_ensemble=-1):
+    _check(L.load().rca_batch_set_wait_limit(b, int(cycles), int(block_ensemble)), None, "rca_batch_set_wait_limit")
+
+
+def rca_batch_destroy(b):
+    _check(L.load().rca_batch_destroy(b), None, "rca_batch_destroy")
+
+
+def rca_autotune(h, t, iq, iq_dtype, n_frames):
+    zt, dc, zp = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(L.load().rca_autotune(h, t, _ptr(iq), iq_dtype, n_frames, C.byref(zt), C.byref(dc), C.byref(zp)), h)
+    return zt.value, dc.value, zp.value
