@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=4)
     ap.add_argument("--frames", type=int, default=0, help="override the ensemble length (profiling runs)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision / batched / learned forms")
     return ap.parse_args()
 
 
@@ -332,6 +333,11 @@ def main():
                "d2h_bytes_per_step": int(d2h // K)}
 
     status_after = R.rca_sync_status(h)
+    forms = None
+    if rank == 0 and not args.no_forms and not reduced and not args.frames:
+        forms = {}
+        forms["reduced"] = reduced_form(R, L, sess, rf, F, prm, max(3, args.warmup), K, stream)
+        forms["batched"] = batched_form(R, L, dev, stream, K)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
@@ -362,6 +368,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "forms": forms,
             "gpu_launches": K * sum(launches.values()),
             "clocks": clk.summary(),
             "localisations": {"n2d": n2d_v, "n3d": n3d_v},
@@ -373,6 +380,114 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def reduced_form(R, L, sess, rf, F, prm, W, K, stream):
+    """Same ensemble, int16 channel data + per-channel scale, FP16 IQ, BF16
+    planes, FP32 accumulation: ms per ensemble through the public calls."""
+    import torch
+    from paper_2511_21647_gb300.pipeline import complex_buffer
+    from synth import quantize_int16
+    q, scale = quantize_int16(rf)
+    q, scale = q.contiguous(), scale.contiguous()
+    planes = complex_buffer(sess.planes_shape(F), L.RCA_C16BF, rf.device)
+    cap2d, cap3d = 1 << 21, 1 << 19
+    bufs = sess.loc_buffers(cap2d, cap3d)
+    bp = R.bf_params(iq_dtype=L.RCA_C16F)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step(timed=False):
+        if timed:
+            ev[0].record(stream)
+        R.rca_beamform_projections(sess.h, sess.t, q, L.RCA_I16, scale, F, bp, planes, L.RCA_C16BF)
+        if timed:
+            ev[1].record(stream)
+        R.ulm_localize(sess.h, sess.t, planes, L.RCA_C16BF, F, prm, bufs[0], cap2d, bufs[1], bufs[2], cap3d, bufs[3])
+        if timed:
+            ev[2].record(stream)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    bf, lo = [], []
+    for _ in range(K):
+        step(True)
+        torch.cuda.synchronize()
+        bf.append(ev[0].elapsed_time(ev[1]))
+        lo.append(ev[1].elapsed_time(ev[2]))
+    ms = (sum(bf) + sum(lo)) / K
+    return {"ms_per_ensemble": round(ms, 3), "value": round(F / (ms / 1e3), 1), "unit": "frames/s",
+            "beamform_ms": round(sum(bf) / K, 3), "localise_ms": round(sum(lo) / K, 3),
+            "dtype": "int16 RF + per-channel scale, FP16 IQ, BF16 planes, FP32 accumulation",
+            "n3d": int(bufs[3].item()), "status": R.rca_sync_status(sess.h)}
+
+
+def batched_form(R, L, dev, stream, K):
+    """16 uneven ensembles of the tiny geometry (100..600 frames, 2K in
+    {2, 4, 8}) beamformed by one persistent launch and localised, replayed as
+    a CUDA graph; compared with the same work issued ensemble by ensemble."""
+    import torch
+    from paper_2511_21647_gb300.pipeline import complex_buffer
+    from synth import batch_workloads, generate
+    ws = batch_workloads(16)
+    h = R.rca_create(dev.index or 0)
+    R.rca_set_stream(h, stream)
+    prm = R.make_ulm_params(d=5, sig_z=0.807, sig_lat=1.4495, alpha=0.1, ncc_min=0.5)
+    items, keep = [], []
+    t_gen = time.time()
+    for w in ws:
+        g = w.geom
+        geo = R.rca_geometry_create(h, g)
+        t = R.rca_delay_tables(h, geo)
+        rf = generate(w, device=str(dev), dtype=torch.float32, frame_batch=32).rf.contiguous()
+        items.append(dict(tables=t, rf=rf, n_frames=w.n_frames,
+                          planes=complex_buffer((w.n_frames, 2, 2, g.n_slab, g.nz, g.n_el), L.RCA_C32, dev),
+                          out2d=torch.zeros((1 << 17, 10), dtype=torch.int32, device=dev), cap2d=1 << 17,
+                          n2d=torch.zeros(1, dtype=torch.int32, device=dev),
+                          out3d=torch.zeros((1 << 16, 10), dtype=torch.int32, device=dev), cap3d=1 << 16,
+                          n3d=torch.zeros(1, dtype=torch.int32, device=dev)))
+        keep.append((geo, t))
+    gen_s = time.time() - t_gen
+    frames = sum(w.n_frames for w in ws)
+    b = R.rca_batch_create(h, items, L.RCA_F32, L.RCA_C32, L.RCA_C32, prm)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R.rca_batch_run(b, use_graph=True, h=h)
+    for _ in range(2):
+        R.rca_batch_run(b, use_graph=True, h=h)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        R.rca_batch_run(b, use_graph=True, h=h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / K
+    st_batch = R.rca_sync_status(h)
+
+    def sequential():
+        for it in items:
+            R.rca_beamform_projections(h, it["tables"], it["rf"], L.RCA_F32, None, it["n_frames"], R.bf_params(),
+                                       it["planes"], L.RCA_C32)
+            R.ulm_localize(h, it["tables"], it["planes"], L.RCA_C32, it["n_frames"], prm, it["out2d"], it["cap2d"],
+                           it["n2d"], it["out3d"], it["cap3d"], it["n3d"])
+    for _ in range(2):
+        sequential()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        sequential()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / K
+    R.rca_batch_destroy(b)
+    for geo, t in keep:
+        R.rca_tables_destroy(t)
+        R.rca_geometry_destroy(geo)
+    R.rca_destroy(h)
+    return {"ensembles": len(ws), "frames": frames, "n_tx": sorted({w.geom.n_tx for w in ws}),
+            "ms_per_batch": round(ms_batch, 3), "value": round(frames / (ms_batch / 1e3), 1), "unit": "frames/s",
+            "ms_per_300_frames": round(ms_batch * 300 / frames, 3),
+            "sequential_ms_per_batch": round(ms_seq, 3), "speedup_vs_sequential": round(ms_seq / ms_batch, 3),
+            "graph": True, "status": st_batch, "generate_s": round(gen_s, 1)}
 
 
 def cpu_baseline(w, rf_tensor, n_frames):

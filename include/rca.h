@@ -304,6 +304,64 @@ rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, 
                         ulm_loc3d* out3d, int cap3d, int* n3d_dev);
 
 /* ---------------------------------------------------------------------- */
+/* Learned localiser (the paper's future-work form, Sec. IV)               */
+/* ---------------------------------------------------------------------- */
+
+/* conv3x3(1->C)+ReLU, conv3x3(C->C)+ReLU x2, conv3x3(C->16), pixel shuffle
+ * to a 4x heatmap; BF16 tensor-core kernels with FP32 accumulation and FP32
+ * master weights, MSE loss against Gaussian targets, Adam. */
+typedef struct ulm_cnn ulm_cnn;
+
+typedef struct {
+    int channels;        /* C (only 32 is built) */
+    int max_pixels;      /* largest batch * H * W the network will see */
+    float lr, beta1, beta2, eps;  /* Adam (1e-3, 0.9, 0.999, 1e-8) */
+    unsigned long long seed;      /* He-normal initial weights */
+} ulm_cnn_desc;
+
+/* Parameter vector (FP32, host order): w1 [C][9][1], b1 [C], w2 [C][9][C],
+ * b2, w3 [C][9][C], b3, w4 [16][9][C], b4 [16]; tap = 3 (dy+1) + (dx+1). */
+rca_status ulm_cnn_create(rca_handle* h, const ulm_cnn_desc* desc, ulm_cnn** out);
+rca_status ulm_cnn_destroy(ulm_cnn* c);
+rca_status ulm_cnn_param_count(const ulm_cnn* c, size_t* n);
+/* copy parameters from host memory (resets the Adam state; synchronises) */
+rca_status ulm_cnn_set_params(ulm_cnn* c, const float* host, size_t n);
+/* copy parameters / the last step's gradients to host memory (synchronises) */
+rca_status ulm_cnn_get_params(const ulm_cnn* c, float* host, size_t n);
+rca_status ulm_cnn_get_grads(const ulm_cnn* c, float* host, size_t n);
+
+/* Forward pass.  Input plane b is A[b][H][W] / M[b / planes_per_frame]
+ * (M NULL: A as is); heat: [B][4H][4W] float (device). */
+rca_status ulm_cnn_forward(ulm_cnn* c, const float* A, const float* M, int planes_per_frame, int B, int H, int W,
+                           float* heat);
+
+/* One training step on a batch: forward, MSE against target [B][4H][4W],
+ * backward (gradients kept for ulm_cnn_get_grads) and, if apply_update, an
+ * Adam update.  loss_dev: device float receiving the mean squared error. */
+rca_status ulm_cnn_train_step(ulm_cnn* c, const float* A, const float* M, int planes_per_frame, int B, int H, int W,
+                              const float* target, float* loss_dev, int apply_update);
+
+/* Gaussian training targets: target[b][y][x] = sum over the points of plane
+ * b of exp(-((y - z4)^2 + (x - x4)^2) / (2 sigma^2)).  pts: [n][3] device
+ * floats (plane, z4, x4) sorted by plane; target: [B][H4][W4]. */
+rca_status ulm_cnn_target(rca_handle* h, const float* pts, int n, int B, int H4, int W4, float sigma, float* target);
+
+/* Checkpoint (weights and Adam state) to / from a file (synchronises). */
+rca_status ulm_cnn_save(const ulm_cnn* c, const char* path);
+rca_status ulm_cnn_load(ulm_cnn* c, const char* path);
+
+/* 2D localisations from score maps on an up-times finer grid (the CNN
+ * heatmap): a fine pixel is a localisation iff its score >= score_min,
+ * A >= alpha M_t at the plane pixel that contains it, and it is a 3x3
+ * regional maximum (ties to the earlier raster pixel); parabolic sub-pixel
+ * refinement.  Positions are returned in plane pixels, (fine - (up-1)/2)/up;
+ * iz / ilat are the plane pixel; amp = A there; ncc = the score.
+ *   map: [F][2][S][up nz][up N]; A, M as from ulm_enhance.  Output as for
+ *   ulm_detect2d (same order and capacity rules), ready for ulm_pair3d. */
+rca_status ulm_detect_map(rca_handle* h, const rca_tables* t, const float* map, int up, const float* A, const float* M,
+                          int n_frames, float score_min, float alpha, ulm_loc2d* out2d, int cap2d, int* n2d_dev);
+
+/* ---------------------------------------------------------------------- */
 /* Batched form and launch-shape autotuning                                */
 /* ---------------------------------------------------------------------- */
 

@@ -19,6 +19,8 @@ import threading
 
 import numpy as np
 
+from . import cnn  # noqa: F401  (FP64 CNN reference, same status as this module)
+
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")

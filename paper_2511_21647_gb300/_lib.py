@@ -57,6 +57,11 @@ class rca_batch_item(C.Structure):
                 ("out3d", C.c_void_p), ("cap3d", C.c_int), ("n3d_dev", C.c_void_p)]
 
 
+class ulm_cnn_desc(C.Structure):
+    _fields_ = [("channels", C.c_int), ("max_pixels", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_ulonglong)]
+
+
 LOC2D = np.dtype([("frame", "<i4"), ("axis", "<i4"), ("slab", "<i4"), ("iz", "<i4"), ("ilat", "<i4"),
                   ("z", "<f4"), ("lat", "<f4"), ("ncc", "<f4"), ("amp", "<f4"), ("reserved", "<i4")])
 LOC3D = np.dtype([("frame", "<i4"), ("i_xz", "<i4"), ("i_yz", "<i4"), ("reserved", "<i4"),
@@ -94,6 +99,18 @@ SIGNATURES = {
     "ulm_detect2d": (_S, [_P, _P, _P, _P, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _P]),
     "ulm_pair3d": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
     "ulm_localize": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _I, _P]),
+    "ulm_cnn_create": (_S, [_P, C.POINTER(ulm_cnn_desc), C.POINTER(_P)]),
+    "ulm_cnn_destroy": (_S, [_P]),
+    "ulm_cnn_param_count": (_S, [_P, C.POINTER(_SZ)]),
+    "ulm_cnn_set_params": (_S, [_P, _P, _SZ]),
+    "ulm_cnn_get_params": (_S, [_P, _P, _SZ]),
+    "ulm_cnn_get_grads": (_S, [_P, _P, _SZ]),
+    "ulm_cnn_forward": (_S, [_P, _P, _P, _I, _I, _I, _I, _P]),
+    "ulm_cnn_train_step": (_S, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _I]),
+    "ulm_cnn_target": (_S, [_P, _P, _I, _I, _I, _I, C.c_float, _P]),
+    "ulm_cnn_save": (_S, [_P, C.c_char_p]),
+    "ulm_cnn_load": (_S, [_P, C.c_char_p]),
+    "ulm_detect_map": (_S, [_P, _P, _P, _I, _P, _P, _I, C.c_float, C.c_float, _P, _I, _P]),
     "rca_batch_create": (_S, [_P, _I, C.POINTER(rca_batch_item), _I, _I, _I, C.POINTER(ulm_params), C.POINTER(_P)]),
     "rca_batch_run": (_S, [_P, _I]),
     "rca_batch_set_wait_limit": (_S, [_P, C.c_longlong, _I]),

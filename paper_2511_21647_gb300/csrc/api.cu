@@ -522,6 +522,21 @@ extern "C" rca_status ulm_localize(rca_handle* h, const rca_tables* t, const voi
     return launch_pair3d(h, t, out2d, n2d, cap2d, F, out3d, cap3d, n3d);
 }
 
+extern "C" rca_status ulm_detect_map(rca_handle* h, const rca_tables* t, const float* map, int up, const float* A,
+                                     const float* M, int F, float score_min, float alpha, ulm_loc2d* out2d, int cap2d,
+                                     int* n2d)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!map || !A || !M || !n2d || cap2d < 0 || (cap2d > 0 && !out2d))
+        return set_error(h, RCA_ERR_INVALID_ARG, "null map, A, M, list or count");
+    if (up < 1 || up > 8) return set_error(h, RCA_ERR_INVALID_ARG, "up must be in [1, 8]");
+    if (!(alpha >= 0)) return set_error(h, RCA_ERR_INVALID_ARG, "bad alpha");
+    DeviceGuard dg(h->device);
+    return launch_detect_map(h, t, map, up, A, M, F, score_min, alpha, out2d, cap2d, n2d);
+}
+
 // ---------------------------------------------------------------------------
 // batched form
 // ---------------------------------------------------------------------------

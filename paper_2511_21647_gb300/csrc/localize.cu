@@ -259,6 +259,120 @@ __global__ void __launch_bounds__(256, 2) k_detect(const float* __restrict__ A, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Peaks of score maps on a finer grid (the learned localiser's heatmaps).
+// CTA = (strip of DET_RS fine rows, plane); same raster-order compaction as
+// k_detect.  Positions are converted to plane pixels for pairing.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ map, int up, const float* __restrict__ A,
+                                                    const float* __restrict__ Mf, int S, int nz, int N, float score_min,
+                                                    float alpha, ulm_loc2d* __restrict__ cand, int* __restrict__ cnt,
+                                                    unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) float smf[];
+    __shared__ int wsum[32];
+    __shared__ int base_count;
+    __shared__ uint64_t bar;
+    const int H4 = nz * up, W4 = N * up;
+    const int strip = blockIdx.x, plane = blockIdx.y, nstrip = gridDim.x;
+    const int t = plane / (2 * S), axis = (plane / S) % 2, b = plane % S;
+    const int i0 = strip * DET_RS, rin = DET_RS + 2;
+    const float* mp = map + (size_t)plane * H4 * W4;
+    const float* Ap = A + (size_t)plane * nz * N;
+    const float Mt = Mf[t];
+    {
+        const int rlo = i0 - 1;
+        const int lo = max(rlo, 0), hi = max(lo, min(rlo + rin, H4));
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        const int z0 = min(lo - rlo, rin), z1 = hi - rlo;
+        for (int idx = threadIdx.x; idx < z0 * W4; idx += blockDim.x) smf[idx] = 0.f;
+        for (int idx = threadIdx.x; idx < (rin - z1) * W4; idx += blockDim.x) smf[(size_t)z1 * W4 + idx] = 0.f;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            const unsigned bytes = (unsigned)((hi - lo) * W4 * sizeof(float));
+            mbar_arrive_expect_tx(&bar, bytes);
+            if (bytes) bulk_g2s(smf + (size_t)(lo - rlo) * W4, mp + (size_t)lo * W4, bytes, &bar);
+        }
+        if (!cta_wait_copies(&bar, 0, status)) return;
+    }
+    const float athr = alpha * Mt;
+    ulm_loc2d* slot = cand + ((size_t)plane * nstrip + strip) * CAND_CAP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int npx = DET_RS * W4;
+    const int per = (npx + blockDim.x - 1) / blockDim.x;
+    const int p0 = threadIdx.x * per, p1 = min(npx, p0 + per);
+    auto is_peak = [&](int p, float& c) {
+        const int ro = 1 + p / W4, j = p % W4;
+        const int i = i0 - 1 + ro;
+        if (i < 1 || i >= H4 - 1 || j < 1 || j >= W4 - 1) return false;
+        c = smf[ro * W4 + j];
+        if (!(c >= score_min) || !(Ap[(size_t)(i / up) * N + j / up] >= athr)) return false;
+#pragma unroll
+        for (int a = -1; a <= 1; ++a)
+#pragma unroll
+            for (int bb = -1; bb <= 1; ++bb) {
+                if (a == 0 && bb == 0) continue;
+                const float q = smf[(ro + a) * W4 + j + bb];
+                const bool earlier = (a < 0) || (a == 0 && bb < 0);
+                if (earlier ? !(c > q) : !(c >= q)) return false;
+            }
+        return true;
+    };
+    int mine = 0;
+    for (int p = p0; p < p1; ++p) {
+        float c;
+        mine += is_peak(p, c) ? 1 : 0;
+    }
+    int x = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = x - mine;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    if (mine) {
+        const float half = 0.5f * (float)(up - 1), inv = 1.f / (float)up;
+        for (int p = p0; p < p1; ++p) {
+            float c;
+            if (!is_peak(p, c)) continue;
+            if (before < CAND_CAP) {
+                const int ro = 1 + p / W4, j = p % W4, i = i0 - 1 + ro;
+                auto para = [](float fm, float f0, float fp) {
+                    const float den = fm - 2.f * f0 + fp;
+                    if (den >= 0.f) return 0.f;
+                    const float dl = (fm - fp) / (2.f * den);
+                    return fminf(0.5f, fmaxf(-0.5f, dl));
+                };
+                ulm_loc2d e;
+                e.frame = t;
+                e.axis = axis;
+                e.slab = b;
+                e.iz = i / up;
+                e.ilat = j / up;
+                e.z = ((float)i + para(smf[(ro - 1) * W4 + j], c, smf[(ro + 1) * W4 + j]) - half) * inv;
+                e.lat = ((float)j + para(smf[ro * W4 + j - 1], c, smf[ro * W4 + j + 1]) - half) * inv;
+                e.ncc = c;
+                e.amp = Ap[(size_t)e.iz * N + e.ilat];
+                e.reserved = 0;
+                slot[before] = e;
+            }
+            ++before;
+        }
+    }
+    if (threadIdx.x == blockDim.x - 1) base_count = before;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cnt[(size_t)plane * nstrip + strip] = base_count;
+        if (base_count > CAND_CAP) atomicOr(status, ST_CAPACITY);
+    }
+}
+
 // Multi-block exclusive scan of min(cnt[i], cap_each) (cap_each <= 0: no cap)
 // over n entries (n = min(n, *n_dev) when n_dev is given).  off[n] = kept
 // total; *total_true = sum of the uncapped counts.
@@ -613,4 +727,32 @@ rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L,
     if ((st = device_scan(h, flags, nn, n2d, 0, off, n3d, part)) != RCA_OK) return st;
     k_pair_write<<<(nn + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, match, off, out, cap3d, h->d_status);
     return cuda_check(h, cudaGetLastError(), "pair kernels");
+}
+
+rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* map, int up, const float* A, const float* M,
+                             int F, float score_min, float alpha, ulm_loc2d* out, int cap, int* n2d)
+{
+    const GeomDev& g = t->gd;
+    const int H4 = g.nz * up, W4 = g.N * up;
+    const int nstrip = (H4 + DET_RS - 1) / DET_RS;
+    const int nplanes = F * 2 * g.S;
+    const int nslots = nplanes * nstrip;
+    rca_status st = RCA_OK;
+    ulm_loc2d* cand = (ulm_loc2d*)ws_get(h, WS_CAND, (size_t)nslots * CAND_CAP * sizeof(ulm_loc2d), &st);
+    if (!cand) return st;
+    int* cnt = (int*)ws_get(h, WS_CANDCNT, (size_t)nslots * sizeof(int), &st);
+    if (!cnt) return st;
+    int* off = (int*)ws_get(h, WS_SCAN, (size_t)(nslots + 1) * sizeof(int), &st);
+    if (!off) return st;
+    long long* part = (long long*)ws_get(h, WS_N2D, (size_t)2 * 1024 * sizeof(long long), &st);
+    if (!part) return st;
+    const size_t smem = (size_t)(DET_RS + 2) * W4 * sizeof(float);
+    if (smem > 200 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "map rows of %d fine pixels exceed shared memory", W4);
+    cudaError_t e = cudaFuncSetAttribute(k_detect_map, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "detect_map smem attribute");
+    dim3 grid(nstrip, nplanes);
+    k_detect_map<<<grid, 256, smem, h->stream>>>(map, up, A, M, g.S, g.nz, g.N, score_min, alpha, cand, cnt, h->d_status);
+    if ((st = device_scan(h, cnt, nslots, nullptr, CAND_CAP, off, n2d, part)) != RCA_OK) return st;
+    k_gather<<<(nslots + 7) / 8, 256, 0, h->stream>>>(cand, cnt, off, nslots, out, cap, h->d_status);
+    return cuda_check(h, cudaGetLastError(), "detect_map kernels");
 }

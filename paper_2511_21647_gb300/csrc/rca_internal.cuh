@@ -169,6 +169,8 @@ rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes
 rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, const float* M, int F,
                            const ulm_params* prm, ulm_loc2d* out, int cap, int* n2d, float* ncc_out,
                            int* plane_off);
+rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* map, int up, const float* A, const float* M,
+                             int F, float score_min, float alpha, ulm_loc2d* out, int cap, int* n2d);
 rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d, int cap2d,
                          int F, ulm_loc3d* out, int cap3d, int* n3d);
 

@@ -11,7 +11,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib as L
-from ._lib import LOC2D, LOC3D, rca_batch_item, rca_bf_params, rca_geometry_desc, ulm_params  # noqa: F401
+from ._lib import (LOC2D, LOC3D, rca_batch_item, rca_bf_params, rca_geometry_desc, ulm_cnn_desc,  # noqa: F401
+                   ulm_params)
 
 
 class RcaError(RuntimeError):
@@ -231,3 +232,64 @@ def rca_autotune(h, t, iq, iq_dtype, n_frames):
     zt, dc, zp = C.c_int(0), C.c_int(0), C.c_int(0)
     _check(L.load().rca_autotune(h, t, _ptr(iq), iq_dtype, n_frames, C.byref(zt), C.byref(dc), C.byref(zp)), h)
     return zt.value, dc.value, zp.value
+
+
+def ulm_cnn_create(h, channels=32, max_pixels=1 << 22, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
+    d = ulm_cnn_desc()
+    d.channels, d.max_pixels, d.lr, d.beta1, d.beta2, d.eps, d.seed = channels, max_pixels, lr, beta1, beta2, eps, seed
+    c = C.c_void_p()
+    _check(L.load().ulm_cnn_create(h, C.byref(d), C.byref(c)), h)
+    return c
+
+
+def ulm_cnn_destroy(c):
+    _check(L.load().ulm_cnn_destroy(c), None, "ulm_cnn_destroy")
+
+
+def ulm_cnn_param_count(c) -> int:
+    n = C.c_size_t(0)
+    _check(L.load().ulm_cnn_param_count(c, C.byref(n)), None, "ulm_cnn_param_count")
+    return n.value
+
+
+def ulm_cnn_set_params(c, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(L.load().ulm_cnn_set_params(c, p.ctypes.data_as(C.c_void_p), p.size), None, "ulm_cnn_set_params")
+
+
+def ulm_cnn_get_params(c) -> np.ndarray:
+    out = np.zeros(ulm_cnn_param_count(c), dtype=np.float32)
+    _check(L.load().ulm_cnn_get_params(c, out.ctypes.data_as(C.c_void_p), out.size), None, "ulm_cnn_get_params")
+    return out
+
+
+def ulm_cnn_get_grads(c) -> np.ndarray:
+    out = np.zeros(ulm_cnn_param_count(c), dtype=np.float32)
+    _check(L.load().ulm_cnn_get_grads(c, out.ctypes.data_as(C.c_void_p), out.size), None, "ulm_cnn_get_grads")
+    return out
+
+
+def ulm_cnn_forward(c, A, M, planes_per_frame, B, H, W, heat):
+    _check(L.load().ulm_cnn_forward(c, _ptr(A), _ptr(M), planes_per_frame, B, H, W, _ptr(heat)), None, "ulm_cnn_forward")
+
+
+def ulm_cnn_train_step(c, A, M, planes_per_frame, B, H, W, target, loss_dev, apply_update=True):
+    _check(L.load().ulm_cnn_train_step(c, _ptr(A), _ptr(M), planes_per_frame, B, H, W, _ptr(target), _ptr(loss_dev),
+                                       int(bool(apply_update))), None, "ulm_cnn_train_step")
+
+
+def ulm_cnn_target(h, pts, n, B, H4, W4, sigma, target):
+    _check(L.load().ulm_cnn_target(h, _ptr(pts), n, B, H4, W4, sigma, _ptr(target)), h)
+
+
+def ulm_cnn_save(c, path: str):
+    _check(L.load().ulm_cnn_save(c, path.encode()), None, "ulm_cnn_save")
+
+
+def ulm_cnn_load(c, path: str):
+    _check(L.load().ulm_cnn_load(c, path.encode()), None, "ulm_cnn_load")
+
+
+def ulm_detect_map(h, t, heat, up, A, M, n_frames, score_min, alpha, out2d, cap2d, n2d):
+    _check(L.load().ulm_detect_map(h, t, _ptr(heat), up, _ptr(A), _ptr(M), n_frames, score_min, alpha, _ptr(out2d),
+                                   cap2d, _ptr(n2d)), h)
