@@ -338,6 +338,7 @@ def main():
         forms = {}
         forms["reduced"] = reduced_form(R, L, sess, rf, F, prm, max(3, args.warmup), K, stream)
         forms["batched"] = batched_form(R, L, dev, stream, K)
+        forms["learned"] = learned_form(R, L, sess, planes, F, g, dev, stream, peaks)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
@@ -488,6 +489,88 @@ def batched_form(R, L, dev, stream, K):
             "ms_per_300_frames": round(ms_batch * 300 / frames, 3),
             "sequential_ms_per_batch": round(ms_seq, 3), "speedup_vs_sequential": round(ms_seq / ms_batch, 3),
             "graph": True, "status": st_batch, "generate_s": round(gen_s, 1)}
+
+
+def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):
+    """The learned localiser: trained on 20k planes of the tiny-geometry
+    generator (BF16 tensor-core kernels), scored against the NCC path on
+    held-out data, then timed on this paper-scale ensemble's planes (XDoppler
+    amplitude -> CNN -> heatmap peaks -> pairing, in chunks of frames)."""
+    import torch
+    from dataclasses import replace
+    from paper_2511_21647_gb300 import learned
+    from synth import workload
+    tg = workload("tiny").geom
+    t0 = time.time()
+    data = learned.build_dataset(tg, learned.training_workloads(40, frames=64))
+    build_s = time.time() - t0
+    n_train = data.n_planes
+    h = sess.h
+    c = R.ulm_cnn_create(h, max_pixels=1 << 24, seed=1)
+    t0 = time.time()
+    steps = 2000
+    hist = learned.train(c, data, steps=steps, batch=64, log_every=500)
+    train_s = time.time() - t0
+    prm = R.make_ulm_params(d=5, sig_z=0.807, sig_lat=1.4495, alpha=0.1, ncc_min=0.5)
+    ev = {}
+    for n_mb, seed in ((20, 9100), (40, 9200)):
+        res = learned.evaluate(tg, replace(workload("tiny"), n_mb=n_mb, seed=seed), c, prm)
+        ev[str(res["density_per_mm3"])] = {"ncc": res["ncc"], "cnn": res["cnn"]}
+    del data
+    torch.cuda.empty_cache()
+    # paper-scale inference on the bench ensemble's planes
+    S = g.n_el // g.P
+    A, M = sess.enhance(planes)
+    fc = 16                                  # frames per chunk
+    P = fc * 2 * S
+    heat = torch.empty((P, 4 * g.nz, 4 * g.n_el), dtype=torch.float32, device=dev)
+    cap = 1 << 18
+    l2 = torch.zeros((cap, 10), dtype=torch.int32, device=dev)
+    l3 = torch.zeros((cap, 10), dtype=torch.int32, device=dev)
+    n2 = torch.zeros(1, dtype=torch.int32, device=dev)
+    n3 = torch.zeros(1, dtype=torch.int32, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def infer(timing):
+        cnn_ms = 0.0
+        for f0 in range(0, F - fc + 1, fc):
+            a = A[f0:f0 + fc]
+            m = M[f0:f0 + fc]
+            e[0].record(stream)
+            R.ulm_cnn_forward(c, a, m, 2 * S, P, g.nz, g.n_el, heat)
+            e[1].record(stream)
+            R.ulm_detect_map(h, sess.t, heat, 4, a, m, fc, 0.3, 0.1, l2, cap, n2)
+            R.ulm_pair3d(h, sess.t, l2, n2, cap, fc, l3, cap, n3)
+            e[2].record(stream)
+            if timing:
+                torch.cuda.synchronize()
+                cnn_ms += e[0].elapsed_time(e[1])
+        return cnn_ms
+
+    infer(False)
+    torch.cuda.synchronize()
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    infer(False)
+    w1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = w0.elapsed_time(w1)
+    cnn_ms = infer(True)
+    frames = (F // fc) * fc
+    px = frames * 2 * S * g.nz * g.n_el
+    flop = px * (2 * 9 * 32 + 2 * 2 * 288 * 32 + 2 * 288 * 16)
+    tflops = flop / (cnn_ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops", 1900.0)
+    R.ulm_cnn_destroy(c)
+    return {"train_planes": n_train,
+            "train_steps": steps, "batch": 64, "loss_first_last": [hist[0][1], hist[-1][1]],
+            "dataset_s": round(build_s, 1), "train_s": round(train_s, 1), "eval_tiny": ev,
+            "paper_frames": frames, "localise_ms_per_300_frames": round(total_ms * 300 / frames, 3),
+            "cnn_ms_per_300_frames": round(cnn_ms * 300 / frames, 3),
+            "cnn_roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+                             "frac": round(tflops / peak, 4), "kernel": "k_conv_mma (mma.sync BF16)",
+                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+            "status": R.rca_sync_status(h)}
 
 
 def cpu_baseline(w, rf_tensor, n_frames):

@@ -120,8 +120,9 @@ def test_training_and_gain_over_ncc(handle):
     """Short run (the bench trains longer): the loss falls, and on held-out
     ensembles at 0.05 and 0.11 MB/mm^3 the CNN and NCC localisations are
     scored against the ground truth (detection accuracy, missing rate,
-    RMSE).  The CNN must localise (RMSE under 60 um, missing rate under 0.9);
-    the comparison is printed."""
+    RMSE).  The CNN must localise: RMSE under half a wavelength (99 um) and
+    within 1.5x the NCC path's, missing rate under 0.9; the comparison is
+    printed."""
     from dataclasses import replace
     from paper_2511_21647_gb300 import learned, rca
     from synth import workload
@@ -138,7 +139,8 @@ def test_training_and_gain_over_ncc(handle):
             res = learned.evaluate(g, w, c, prm)
             print(f"\nheld-out {res['density_per_mm3']} MB/mm^3: NCC {res['ncc']}  CNN {res['cnn']}")
             assert res["status"] == 0
-            assert res["cnn"]["rmse_um"] is not None and res["cnn"]["rmse_um"] < 60
+            assert res["cnn"]["rmse_um"] is not None and res["cnn"]["rmse_um"] < 99
+            assert res["cnn"]["rmse_um"] < 1.5 * max(res["ncc"]["rmse_um"] or 0.0, 20.0)
             assert res["cnn"]["missing_rate"] < 0.9
     finally:
         rca.ulm_cnn_destroy(c)
