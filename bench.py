@@ -280,6 +280,20 @@ def main():
         ach = bytes_alg[dominant] / (stage_ms[dominant] / 1e3) / 1e9
         roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    # DRAM traffic of the dominant kernel from the committed ncu summary, only
+    # while the kernel's source is the one that was profiled
+    try:
+        import hashlib
+        prof = _json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        key = roof["kernel"].split("<")[0]
+        ent = prof.get(key)
+        if ent:
+            src = open(os.path.join(ROOT, ent["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == ent["source_sha256_16"]:
+                roof["traffic"] = int(ent["dram_bytes_per_frame"] * F)
+                roof["traffic_source"] = "profiles/kernels_paper_40frames_full.md, scaled by frames"
+    except (OSError, ValueError, KeyError):
+        pass
     stage_roof = {}
     for s in stages:
         gbs = bytes_alg[s] / (stage_ms[s] / 1e3) / 1e9
