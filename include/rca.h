@@ -297,6 +297,34 @@ rca_status ulm_detect2d(rca_handle* h, const rca_tables* t, const float* A, cons
 rca_status ulm_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* list2d, const int* n2d_dev,
                       int cap2d, int n_frames, ulm_loc3d* out3d, int cap3d, int* n3d_dev);
 
+/* ulm_pair3d without allocation.  The paper has no counterpart: this entry
+ * point serves callers that must not allocate device memory once they are
+ * running.  An acquisition loop that sized its memory before the first
+ * ensemble cannot take the device-wide stall of an allocation, or its
+ * failure, in the middle of a scan; a program whose own memory pool already
+ * holds the free device memory would see an allocation fail.  ulm_pair3d
+ * takes its scratch from the handle's workspace, which grows with cudaMalloc
+ * when a longer list arrives; this call uses a fixed scratch array compiled
+ * into the library instead (ULM_PAIR3D_NOALLOC_SCRATCH_BYTES, 6.3 MiB, one
+ * per device) and allocates nothing.
+ *   Arguments, results and status rules: as ulm_pair3d (same kernels, same
+ *   lists bit for bit), with two limits: cap2d <= ULM_PAIR3D_NOALLOC_MAX_2D
+ *   and n_frames * 2 * S <= ULM_PAIR3D_NOALLOC_MAX_PLANES.  Beyond them it
+ *   returns RCA_ERR_UNSUPPORTED (message in rca_last_error) before anything
+ *   is enqueued.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   with that device current, which can make the CUDA runtime load the
+ *   library's device code; make that first call before any stream capture.
+ *   Sharing: every handle and every call on a device uses the one array.
+ *   Calls in order on one stream are fine (each call writes every scratch
+ *   entry it reads, so nothing is cleared or carried over); calls whose work
+ *   overlaps on the GPU (two streams, two threads) race and give wrong lists. */
+#define ULM_PAIR3D_NOALLOC_MAX_2D (1 << 19)
+#define ULM_PAIR3D_NOALLOC_MAX_PLANES (1 << 16)
+#define ULM_PAIR3D_NOALLOC_SCRATCH_BYTES 6556160
+rca_status ulm_pair3d_noalloc(rca_handle* h, const rca_tables* t, const ulm_loc2d* list2d, const int* n2d_dev,
+                              int cap2d, int n_frames, ulm_loc3d* out3d, int cap3d, int* n3d_dev);
+
 /* The whole localisation path: ulm_enhance -> ulm_detect2d -> ulm_pair3d with
  * library workspace for A and M. */
 rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype planes_dtype,

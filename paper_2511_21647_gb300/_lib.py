@@ -12,6 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librca.so")
 
 RCA_MAX_K = 8
+ULM_PAIR3D_NOALLOC_MAX_2D = 1 << 19
+ULM_PAIR3D_NOALLOC_MAX_PLANES = 1 << 16
 
 # rca_status
 RCA_OK = 0
@@ -98,6 +100,7 @@ SIGNATURES = {
     "ulm_enhance": (_S, [_P, _P, _P, _I, _I, _I, _P, _P]),
     "ulm_detect2d": (_S, [_P, _P, _P, _P, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _P]),
     "ulm_pair3d": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
+    "ulm_pair3d_noalloc": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
     "ulm_localize": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _I, _P]),
     "ulm_cnn_create": (_S, [_P, C.POINTER(ulm_cnn_desc), C.POINTER(_P)]),
     "ulm_cnn_destroy": (_S, [_P]),

@@ -499,6 +499,18 @@ extern "C" rca_status ulm_pair3d(rca_handle* h, const rca_tables* t, const ulm_l
     return launch_pair3d(h, t, L, n2d, cap2d, F, out, cap3d, n3d);
 }
 
+extern "C" rca_status ulm_pair3d_noalloc(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d,
+                                         int cap2d, int F, ulm_loc3d* out, int cap3d, int* n3d)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!n2d || !n3d || cap2d < 0 || cap3d < 0 || (cap2d > 0 && !L) || (cap3d > 0 && !out))
+        return set_error(h, RCA_ERR_INVALID_ARG, "null list or count");
+    DeviceGuard dg(h->device);
+    return launch_pair3d_noalloc(h, t, L, n2d, cap2d, F, out, cap3d, n3d);
+}
+
 extern "C" rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
                                    const ulm_params* prm, ulm_loc2d* out2d, int cap2d, int* n2d, ulm_loc3d* out3d,
                                    int cap3d, int* n3d)

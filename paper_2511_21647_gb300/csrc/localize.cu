@@ -2,6 +2,7 @@
 // XZ / YZ pairing (Sec. II-A4, Fig. 1e, Fig. 1g).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "rca_internal.cuh"
 
@@ -727,6 +728,94 @@ rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L,
     if ((st = device_scan(h, flags, nn, n2d, 0, off, n3d, part)) != RCA_OK) return st;
     k_pair_write<<<(nn + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, match, off, out, cap3d, h->d_status);
     return cuda_check(h, cudaGetLastError(), "pair kernels");
+}
+
+// ---------------------------------------------------------------------------
+// Pairing without allocation (ulm_pair3d_noalloc).
+//
+// ulm_pair3d takes its scratch from the handle's workspace, which grows with
+// cudaMalloc the first time a longer list arrives.  Some callers must not
+// allocate once they are running: an acquisition loop that sized its device
+// memory before the first ensemble cannot afford the device-wide stall of an
+// allocation, or its failure, in the middle of a scan; a program whose own
+// memory pool already holds the free HBM would see the allocation fail.
+// For them the same kernels run on a fixed scratch array compiled into this
+// file.  Being a file-scope __device__ variable, the array exists once per
+// device, shared by every handle and call on it: calls whose work overlaps
+// on the GPU race on it.  Its address is looked up once per device, on the
+// first call made with that device current.
+//
+// Nothing in it needs clearing between calls: each call writes every entry
+// it reads (plane offsets for all planes, flags for all list slots, match
+// indices and scan offsets for all live entries, one partial per scan
+// chunk), so the previous call's contents are never seen.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr int NA_CHUNKS = (ULM_PAIR3D_NOALLOC_MAX_2D + SCAN_CHUNK - 1) / SCAN_CHUNK;
+constexpr size_t NA_POFF = 0;
+constexpr size_t NA_MATCH = NA_POFF + na_round((size_t)(ULM_PAIR3D_NOALLOC_MAX_PLANES + 1) * sizeof(int));
+constexpr size_t NA_FLAGS = NA_MATCH + na_round((size_t)ULM_PAIR3D_NOALLOC_MAX_2D * sizeof(int));
+constexpr size_t NA_OFF = NA_FLAGS + na_round((size_t)ULM_PAIR3D_NOALLOC_MAX_2D * sizeof(int));
+constexpr size_t NA_PART = NA_OFF + na_round((size_t)(ULM_PAIR3D_NOALLOC_MAX_2D + 1) * sizeof(int));
+constexpr size_t NA_BYTES = NA_PART + na_round((size_t)2 * NA_CHUNKS * sizeof(long long));
+static_assert(NA_BYTES == ULM_PAIR3D_NOALLOC_SCRATCH_BYTES, "scratch size stated in rca.h is stale");
+static_assert(NA_CHUNKS <= 1024, "device_scan handles at most 1024 chunks");
+
+constexpr int NA_MAX_DEVICES = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_pair_scratch[NA_BYTES];
+
+static std::mutex g_pair_scratch_mu;
+static unsigned char* g_pair_scratch_dev[NA_MAX_DEVICES];  // per device, null until looked up
+
+// device address of g_pair_scratch on the handle's device (which is current)
+static rca_status pair_scratch(rca_handle* h, unsigned char** base)
+{
+    if (h->device < 0 || h->device >= NA_MAX_DEVICES)
+        return set_error(h, RCA_ERR_UNSUPPORTED, "ulm_pair3d_noalloc: device %d beyond %d", h->device, NA_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_pair_scratch_mu);
+    if (!g_pair_scratch_dev[h->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pair_scratch);
+        if (e != cudaSuccess) return cuda_check(h, e, "ulm_pair3d_noalloc scratch address");
+        if (!p) return set_error(h, RCA_ERR_CUDA, "ulm_pair3d_noalloc: null scratch address");
+        g_pair_scratch_dev[h->device] = static_cast<unsigned char*>(p);
+    }
+    *base = g_pair_scratch_dev[h->device];
+    return RCA_OK;
+}
+
+rca_status launch_pair3d_noalloc(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d, int cap2d,
+                                 int F, ulm_loc3d* out, int cap3d, int* n3d)
+{
+    const GeomDev& g = t->gd;
+    const long long nplanes = (long long)F * 2 * g.S;
+    if (cap2d > ULM_PAIR3D_NOALLOC_MAX_2D)
+        return set_error(h, RCA_ERR_UNSUPPORTED, "ulm_pair3d_noalloc: cap2d %d exceeds its fixed scratch of %d entries",
+                         cap2d, ULM_PAIR3D_NOALLOC_MAX_2D);
+    if (nplanes > ULM_PAIR3D_NOALLOC_MAX_PLANES)
+        return set_error(h, RCA_ERR_UNSUPPORTED, "ulm_pair3d_noalloc: %lld planes exceed its fixed scratch of %d planes",
+                         nplanes, ULM_PAIR3D_NOALLOC_MAX_PLANES);
+    unsigned char* base = nullptr;
+    rca_status st = pair_scratch(h, &base);
+    if (st != RCA_OK) return st;
+    int* poff = reinterpret_cast<int*>(base + NA_POFF);
+    int* match = reinterpret_cast<int*>(base + NA_MATCH);
+    int* flags = reinterpret_cast<int*>(base + NA_FLAGS);
+    int* off = reinterpret_cast<int*>(base + NA_OFF);
+    long long* part = reinterpret_cast<long long*>(base + NA_PART);
+    const int nn = std::max(cap2d, 1);
+    const int np = (int)nplanes;
+    k_list_plane_offsets<<<(np + 1 + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, g.S, np, poff);
+    k_pair_match<<<(nn + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, g.S, g.P, poff, match);
+    k_match_flags<<<(nn + 255) / 256, 256, 0, h->stream>>>(match, n2d, cap2d, flags);
+    if ((st = device_scan(h, flags, nn, n2d, 0, off, n3d, part)) != RCA_OK) return st;
+    k_pair_write<<<(nn + 255) / 256, 256, 0, h->stream>>>(L, n2d, cap2d, match, off, out, cap3d, h->d_status);
+    return cuda_check(h, cudaGetLastError(), "pair kernels (no-alloc)");
 }
 
 rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* map, int up, const float* A, const float* M,

@@ -173,6 +173,8 @@ rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* ma
                              int F, float score_min, float alpha, ulm_loc2d* out, int cap, int* n2d);
 rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d, int cap2d,
                          int F, ulm_loc3d* out, int cap3d, int* n3d);
+rca_status launch_pair3d_noalloc(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d,
+                                 int cap2d, int F, ulm_loc3d* out, int cap3d, int* n3d);
 
 // ---------------------------------------------------------------------------
 // device-side element access for the supported complex / real dtypes

@@ -186,6 +186,11 @@ def ulm_pair3d(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
     _check(L.load().ulm_pair3d(h, t, _ptr(list2d), _ptr(n2d), cap2d, n_frames, _ptr(out3d), cap3d, _ptr(n3d)), h)
 
 
+def ulm_pair3d_noalloc(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
+    """ulm_pair3d on the library's fixed per-device scratch (no allocation)."""
+    _check(L.load().ulm_pair3d_noalloc(h, t, _ptr(list2d), _ptr(n2d), cap2d, n_frames, _ptr(out3d), cap3d, _ptr(n3d)), h)
+
+
 def ulm_localize(h, t, planes, planes_dtype, n_frames, prm: ulm_params, out2d, cap2d, n2d, out3d, cap3d, n3d):
     _check(L.load().ulm_localize(h, t, _ptr(planes), planes_dtype, n_frames, C.byref(prm), _ptr(out2d), cap2d,
                                  _ptr(n2d), _ptr(out3d), cap3d, _ptr(n3d)), h)
