@@ -23,6 +23,9 @@ UNITS = {
     "api.cu": [],
     "tables.cu": ["-fmad=false"],
     "beamform.cu": [],
+    "batch_c32.cu": [],
+    "batch_c16f.cu": [],
+    "batch_c16bf.cu": [],
     "localize.cu": [],
     "cnn.cu": [],
 }

@@ -394,6 +394,7 @@ extern "C" rca_status rca_stage1(rca_handle* h, const rca_tables* t, const void*
     if (st != RCA_OK) return st;
     if (!iq || !slices) return set_error(h, RCA_ERR_INVALID_ARG, "null iq or slices");
     if (!is_complex(iq_t)) return set_error(h, RCA_ERR_UNSUPPORTED, "iq dtype must be C32, C16F or C16BF");
+    if (reinterpret_cast<uintptr_t>(iq) % 16 != 0) return set_error(h, RCA_ERR_INVALID_ARG, "iq must be 16-byte aligned");
     DeviceGuard dg(h->device);
     return launch_stage1(h, t, iq, iq_t, F, (float2*)slices);
 }

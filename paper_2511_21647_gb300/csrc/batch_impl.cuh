@@ -1,0 +1,187 @@
+// batch_impl.cuh -- the persistent batched beamforming kernel, instantiated
+// once per IQ dtype (batch_c32.cu, batch_c16f.cu, batch_c16bf.cu) so the
+// translation units compile in parallel.
+#pragma once
+#include "beamform_body.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Persistent batched beamforming.  Every CTA repeatedly takes the next work
+// unit from a device queue (mean units of all ensembles first, then per
+// ensemble demodulation, Stage 1 and Stage 2 units), waits -- bounded -- until
+// the unit's inputs are complete (per-ensemble counters), runs the same body
+// as the standalone kernel, and publishes its completion.  Units only wait
+// on units earlier in the queue, which were taken by CTAs already running,
+// so the queue always drains.  A wait that runs out sets ST_TIMEOUT and an
+// abort flag that stops every CTA at its next unit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename TS, int MAXR, int ZP>
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
+                                                 int nseg, int total, int* __restrict__ cnt, int n_counters,
+                                                 long long wait_limit, Fir fir, int rf_t, int iq_t, int pt,
+                                                 unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint64_t bars[2];
+    __shared__ int s_unit, s_ok;
+    int* next = cnt + n_counters;
+    int* abort_flag = cnt + n_counters + 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(next, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= total) break;
+        int sg = 0;
+        while (sg + 1 < nseg && segs[sg + 1].z <= u) ++sg;
+        const int4 SG = segs[sg];
+        const int stage = SG.x, e = SG.y, loc = u - SG.z;
+        const BatchEns& E = ens[e];
+        const GeomDev& g = E.g;
+        const int nt = 2 * g.K;
+        // decode the unit, its dependency and the counter it completes
+        int dep = -1, dep_target = 0, done = -1;
+        int a0 = 0, a1 = 0, a2 = 0;
+        if (stage == BS_MEAN) {
+            a0 = loc;
+            done = E.cA;
+        } else if (stage == BS_DEMOD) {
+            const int nbx = (g.ns + DM_NT - 1) / DM_NT, nby = (g.N + DM_NE - 1) / DM_NE;
+            a0 = loc % nbx;
+            a1 = (loc / nbx) % nby;
+            a2 = loc / (nbx * nby);  // f * nt + k
+            dep = E.cA;
+            dep_target = E.nA;
+            done = E.cB0 + a2;
+        } else if (stage == BS_STAGE1) {
+            a0 = loc % E.n_tiles;                // tile
+            a1 = (loc / E.n_tiles) % nt;         // k
+            a2 = loc / (E.n_tiles * nt);         // f
+            dep = E.cB0 + a2 * nt + a1;
+            dep_target = E.nB_fk;
+            done = E.cC0 + a2;
+        } else {
+            a0 = loc % E.n_tiles2;               // tile
+            a1 = (loc / E.n_tiles2) % 2;         // family
+            a2 = loc / (E.n_tiles2 * 2);         // f
+            dep = E.cC0 + a2;
+            dep_target = E.n_tiles * nt;
+        }
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (dep >= 0) {
+                const long long t0 = clock64();
+                while (ld_acquire(cnt + dep) < dep_target) {
+                    if (*(volatile int*)abort_flag) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > wait_limit) {
+                        atomicOr(status, ST_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                // order the producers' global writes before this CTA's TMA reads
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            if (*(volatile int*)abort_flag) ok = 0;
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        bool ok = true;
+        if (stage == BS_MEAN) {
+            mean_body(a0, E.rf, rf_t, E.scale, E.F, g.ns, nt * g.N * g.ns, E.mean);
+        } else if (stage == BS_DEMOD) {
+            demod_body(a0, a1, a2, reinterpret_cast<float2*>(smraw), E.rf, rf_t, E.scale, E.mean, E.mix, fir, nt, g.N,
+                       g.ns, E.iq, iq_t);
+        } else if (stage == BS_STAGE1) {
+            ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.tx_q16, E.rx_q16, E.W, E.dmax, E.chunks,
+                                       E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);
+        } else {
+            ok = stage2_body<ZP>(a0, a1, a2, E.zp, reinterpret_cast<float2*>(smraw), &bars[0], g, E.slices, E.sfl,
+                                 E.sfr, E.psi, E.ec, E.coef, E.tmin, E.T, E.rows, E.smin0, E.smin1, E.planes, pt,
+                                 status);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (stage == BS_STAGE1) {
+                mbar_inval(&bars[0]);
+                mbar_inval(&bars[1]);
+            } else if (stage == BS_STAGE2) {
+                mbar_inval(&bars[0]);
+            }
+            if (!ok) {
+                atomicExch(abort_flag, 1);
+            } else if (done >= 0) {
+                __threadfence();
+                atomicAdd(cnt + done, 1);
+            }
+        }
+        if (!ok) break;
+    }
+}
+
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// batched launch
+// ---------------------------------------------------------------------------
+template <typename TS, int MAXR, int ZP>
+static rca_status batch_launch(rca_handle* h, rca_batch* b)
+{
+    auto kern = k_batch<TS, MAXR, ZP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "batch smem attribute");
+    if (b->grid == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, b->smem);
+        b->grid = std::max(1, per_sm) * sms;
+    }
+    Fir fir;
+    for (int q = 0; q < 31; ++q) fir.h[q] = b->fir[q];
+    cudaMemsetAsync(b->d_cnt, 0, sizeof(int) * (b->n_counters + 2), h->stream);
+    kern<<<b->grid, 256, b->smem, h->stream>>>(b->d_ens, b->d_segs, (int)b->segs.size(), b->total, b->d_cnt,
+                                               b->n_counters, b->wait_limit, fir, (int)b->rf_t, (int)b->iq_t,
+                                               (int)b->pl_t, h->d_status);
+    return cuda_check(h, cudaGetLastError(), "batch kernel");
+}
+
+template <typename TS, int MAXR>
+static rca_status batch_zp(rca_handle* h, rca_batch* b)
+{
+    switch (b->zpmax) {
+    case 1: return batch_launch<TS, MAXR, 1>(h, b);
+    case 2: return batch_launch<TS, MAXR, 2>(h, b);
+    case 4: return batch_launch<TS, MAXR, 4>(h, b);
+    case 8: return batch_launch<TS, MAXR, 8>(h, b);
+    default: return batch_launch<TS, MAXR, 16>(h, b);
+    }
+}
+
+template <typename TS>
+static rca_status batch_maxr(rca_handle* h, rca_batch* b)
+{
+    if (b->maxr <= 2) return batch_zp<TS, 2>(h, b);
+    if (b->maxr <= 4) return batch_zp<TS, 4>(h, b);
+    if (b->maxr <= 8) return batch_zp<TS, 8>(h, b);
+    return batch_zp<TS, 16>(h, b);
+}

@@ -428,3 +428,7 @@ struct rca_batch {
 };
 
 rca_status launch_batch(rca_handle* h, rca_batch* b);
+// one per IQ dtype (separate translation units)
+rca_status launch_batch_c32(rca_handle* h, rca_batch* b);
+rca_status launch_batch_c16f(rca_handle* h, rca_batch* b);
+rca_status launch_batch_c16bf(rca_handle* h, rca_batch* b);

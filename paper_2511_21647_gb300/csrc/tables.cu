@@ -364,10 +364,11 @@ int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* out)
     return win;
 }
 
-// double-buffered windows + per-(row, d) records (32 B) + per-row counts
+// double-buffered windows + per-(d, row) weight records (16 B) and row
+// addresses (4 B) + per-row counts
 size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t esz)
 {
-    return 2 * (size_t)win * t->gd.N * esz + 2 * (size_t)zt * dc * 32 + 2 * (size_t)zt * 4;
+    return 2 * (size_t)win * t->gd.N * esz + 2 * (size_t)zt * dc * (16 + 4) + 2 * (size_t)zt * 4;
 }
 
 rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
