@@ -245,7 +245,7 @@ static void free_tables(rca_tables* t)
 {
     void* ptrs[] = {t->tx_f64, t->rx_f64, t->tx_q16, t->rx_q16, t->W, t->dmax, t->s2_shift, t->s2_sfl,
                     t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin, t->dtx_q16, t->dtx_ph, t->mix,
-                    t->s1.d_chunks};
+                    t->s1.d_chunks, t->s1.d_rec32, t->s1.d_rec16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -636,6 +636,8 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.W = t->W;
         E.dmax = t->dmax;
         E.chunks = t->s1.d_chunks;
+        E.rtab = iq_t == RCA_C16F ? t->s1.d_rec16 : t->s1.d_rec32;
+        E.rblk = t->s1.rblk;
         E.zt = t->s1.zt;
         E.dc = t->s1.dc;
         E.n_tiles = t->s1.n_tiles;

@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ e
             demod_body(a0, a1, a2, reinterpret_cast<float2*>(smraw), E.rf, rf_t, E.scale, E.mean, E.mix, fir, nt, g.N,
                        g.ns, E.iq, iq_t);
         } else if (stage == BS_STAGE1) {
-            ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.tx_q16, E.rx_q16, E.W, E.dmax, E.chunks,
-                                       E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);
+            ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.rtab, E.rblk, E.dmax, E.chunks,
+                                              E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);
         } else {
             ok = stage2_body<ZP>(a0, a1, a2, E.zp, reinterpret_cast<float2*>(smraw), &bars[0], g, E.slices, E.sfl,
                                  E.sfr, E.psi, E.ec, E.coef, E.tmin, E.T, E.rows, E.smin0, E.smin1, E.planes, pt,

@@ -23,15 +23,15 @@ __global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int 
 
 template <typename TS, int MAXR>
 __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __restrict__ iq,
-                                                const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
-                                                const float2* __restrict__ W, const int* __restrict__ dmax,
-                                                const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch,
-                                                int win, float2* __restrict__ slices, unsigned* __restrict__ status)
+                                                const unsigned char* __restrict__ rtab, int rblk,
+                                                const int* __restrict__ dmax, const int4* __restrict__ chunks, int zt,
+                                                int dc, int n_tiles, int nch, int win, float2* __restrict__ slices,
+                                                unsigned* __restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bars[2];
-    stage1_body<TS, MAXR, true>(blockIdx.x, blockIdx.y, blockIdx.z, smraw, bars, g, iq, tx_q16, rx_q16, W, dmax, chunks,
-                          zt, dc, n_tiles, nch, win, slices, status);
+    stage1_body<TS, MAXR, true>(blockIdx.x, blockIdx.y, blockIdx.z, smraw, bars, g, iq, rtab, rblk, dmax, chunks, zt,
+                                dc, n_tiles, nch, win, slices, status);
 }
 
 template <int ZP>
@@ -204,8 +204,9 @@ static rca_status stage1_launch(rca_handle* h, const rca_tables* t, const void* 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage1 smem attribute");
     dim3 grid(p.n_tiles, 2 * g.K, F);
-    kern<<<grid, threads, smem, h->stream>>>(g, iq, t->tx_q16, t->rx_q16, t->W, t->dmax, p.d_chunks, p.zt, p.dc,
-                                             p.n_tiles, p.nch, p.win, slices, h->d_status);
+    const unsigned char* rtab = std::is_same<TS, __half2>::value ? p.d_rec16 : p.d_rec32;
+    kern<<<grid, threads, smem, h->stream>>>(g, iq, rtab, p.rblk, t->dmax, p.d_chunks, p.zt, p.dc, p.n_tiles, p.nch,
+                                             p.win, slices, h->d_status);
     return cuda_check(h, cudaGetLastError(), "stage1 kernel");
 }
 

@@ -169,9 +169,9 @@ __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __res
 // stored d-major so that its rows sit at fixed offsets from one address.
 // ---------------------------------------------------------------------------
 // per-(d, row) weights, 16 bytes.  FP32 arithmetic: Re a, Re b, Im a, Im b
-// as floats, with the shared-memory address of the window row in a separate
-// array.  FP16 arithmetic: {Re a, Re b} and {Im a, Im b} as half pairs, then
-// the row address.
+// as floats, with the byte offset of the window row in a separate array.
+// FP16 arithmetic: {Re a, Re b} and {Im a, Im b} as half pairs, then the
+// row offset.
 template <typename TS>
 struct S1Rec {
     static constexpr bool HALF = std::is_same<TS, __half2>::value;
@@ -235,7 +235,7 @@ enum { S1_NONE = 0, S1_FULL = 1, S1_PRED = 2 };
 template <typename TS, int MAXR, bool EXACT, int XM, int YM>
 __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
                                              int d1, int cz, int zt, int l, int Lx, int Ly, int row0, int nrow,
-                                             unsigned rbase, unsigned obase, int RS)
+                                             unsigned rbase, unsigned obase, unsigned wbase, int RS)
 {
     constexpr bool HALF = S1Rec<TS>::HALF;
     constexpr int RB = S1Rec<TS>::BYTES, ESZ = (int)sizeof(TS);
@@ -243,7 +243,8 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
     for (int d = d0; d < d1; ++d) {
         const bool hx = XM == S1_FULL || (XM == S1_PRED && d <= Lx);
         const bool hy = YM == S1_FULL || (YM == S1_PRED && d <= Ly);
-        const unsigned ox = (unsigned)((l - d) * ESZ), oy = (unsigned)((l + d) * ESZ);
+        // window offsets of the two mirror elements (records hold the row offset)
+        const unsigned ox = wbase + (unsigned)((l - d) * ESZ), oy = wbase + (unsigned)((l + d) * ESZ);
         const unsigned ox1 = ox + RS, oy1 = oy + RS;
         const int base = (d - cz) * zt + row0;    // record index of the thread's first row
         const unsigned rp = rbase + base * RB, op = obase + base * 4;
@@ -287,7 +288,8 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
                         else
                             rowq[0] = lds_u32(op + j * 4);
                     }
-                    const unsigned row = rowq[QUAD ? (j & 3) : 0];
+                    // FP32-weight records hold offsets for 8-byte samples: halve for 4-byte ones
+                    const unsigned row = rowq[QUAD ? (j & 3) : 0] >> (ESZ == 4 ? 1 : 0);
                     uint64_t x0 = 0ull, x1 = 0ull, y0 = 0ull, y1 = 0ull;
                     if (XM != S1_NONE && hx) {
                         x0 = s1_ld<TS>(row + ox);
@@ -324,22 +326,21 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
 // Returns false if a bounded wait ran out (the CTA must stop).  The thread
 // owns rows [rg * per, rg * per + per) of the tile, per = ceil(zt / RG)
 // (per <= MAXR; EXACT: per == MAXR and zt == RG * MAXR, or MAXR == 1).
+// rtab: the plan's record table for this arithmetic (FP16 weights for FP16
+// samples, FP32 weights otherwise), one block of rblk bytes per chunk.
 template <typename TS, int MAXR, bool EXACT>
 __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned char* __restrict__ smraw,
                                             uint64_t* bars, const GeomDev& g, const void* __restrict__ iq,
-                                            const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
-                                            const float2* __restrict__ W, const int* __restrict__ dmax,
-                                            const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch,
-                                            int win, float2* __restrict__ slices, unsigned* __restrict__ status)
+                                            const unsigned char* __restrict__ rtab, int rblk,
+                                            const int* __restrict__ dmax, const int4* __restrict__ chunks, int zt,
+                                            int dc, int n_tiles, int nch, int win, float2* __restrict__ slices,
+                                            unsigned* __restrict__ status)
 {
-    constexpr bool HALF = S1Rec<TS>::HALF;
-    constexpr int RB = S1Rec<TS>::BYTES, ESZ = (int)sizeof(TS);
+    constexpr int ESZ = (int)sizeof(TS);
     const int E = g.N, N = g.N;
     const int RS = E * ESZ;                                   // window row (bytes)
     unsigned char* bufs = smraw;                              // [2][win][RS]
-    unsigned char* recs = bufs + 2 * (size_t)win * RS;        // [2][dc][zt] records
-    unsigned* raddr = reinterpret_cast<unsigned*>(recs + 2 * (size_t)zt * dc * RB);  // [2][dc][zt] row addresses
-    int* dcnt = reinterpret_cast<int*>(raddr + 2 * zt * dc);  // [2][zt]
+    unsigned char* recs = bufs + 2 * (size_t)win * RS;        // [2][rblk]
     const int nt = 2 * g.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int LW = (N + 31) >> 5;
@@ -352,9 +353,13 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
     const int nrow = max(0, min(per, zt - row0));
     const int r0 = tile * zt;
     const int rend = min(r0 + zt, g.nzs);
-    const int qmax = (g.ns - 1) << 16;
     const int4* ch = chunks + ((size_t)k * n_tiles + tile) * nch;
+    const unsigned char* rsrc = rtab + ((size_t)k * n_tiles + tile) * nch * rblk;
     const unsigned char* blk = reinterpret_cast<const unsigned char*>(iq) + ((size_t)f * nt + k) * g.ns * RS;
+    // largest (aperture limit + 1) over this thread's rows: its distance count in a chunk
+    int dmx = 0;
+    for (int j = 0; j < nrow; ++j)
+        if (r0 + row0 + j < rend) dmx = max(dmx, __ldg(dmax + r0 + row0 + j) + 1);
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -363,7 +368,8 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
     }
     __syncthreads();
 
-    // zero the window rows outside the record, then (thread 0) bulk-copy the rest
+    // zero the window rows outside the record, then (thread 0) bulk-copy the
+    // rest and the chunk's record block on one barrier
     auto issue = [&](int c, int b) {
         const int4 cc = ch[c];
         unsigned char* dst = bufs + (size_t)b * win * RS;
@@ -377,8 +383,9 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
         if (threadIdx.x == 0) {
             fence_proxy_async();
             const unsigned bytes = (unsigned)((hi - lo) * RS);
-            mbar_arrive_expect_tx(&bars[b], bytes);
+            mbar_arrive_expect_tx(&bars[b], bytes + (unsigned)rblk);
             if (bytes) bulk_g2s(dst + (size_t)(lo - cc.x) * RS, blk + (size_t)lo * RS, bytes, &bars[b]);
+            bulk_g2s(recs + (size_t)b * rblk, rsrc + (size_t)c * rblk, (unsigned)rblk, &bars[b]);
         }
     };
 
@@ -398,54 +405,16 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
         const int4 cc = ch[c];
-        unsigned char* rc = recs + (size_t)b * zt * dc * RB;
-        unsigned* ac = raddr + b * zt * dc;
-        const unsigned wbase = smem_u32(bufs + (size_t)b * win * RS);
-        for (int idx = threadIdx.x; idx < zt * dc; idx += blockDim.x) {
-            const int dd = idx / zt, rr = idx - dd * zt;
-            const int r = r0 + rr, d = cc.z + dd;
-            float ax = 0.f, bx = 0.f, ay = 0.f, by = 0.f;
-            int off = 0;
-            if (r < rend && d < cc.w && d <= __ldg(dmax + r)) {
-                const int q = __ldg(tx_q16 + (size_t)k * g.nzs + r) + __ldg(rx_q16 + (size_t)r * N + d);
-                if (q >= 0 && q <= qmax) {
-                    const float2 w = __ldg(W + (size_t)r * N + d);
-                    const float fr = (float)(q & 0xffff) * (1.0f / 65536.0f);
-                    const float h = d == 0 ? 0.5f : 1.0f;
-                    ax = h * w.x * (1.0f - fr);
-                    bx = h * w.x * fr;
-                    ay = h * w.y * (1.0f - fr);
-                    by = h * w.y * fr;
-                    off = ((q >> 16) - cc.x) * RS;
-                }
-            }
-            const unsigned rowaddr = wbase + (unsigned)off;
-            if constexpr (HALF) {
-                const __half2 re = __floats2half2_rn(ax, bx), im = __floats2half2_rn(ay, by);
-                reinterpret_cast<uint4*>(rc)[idx] =
-                    make_uint4(*reinterpret_cast<const unsigned*>(&re), *reinterpret_cast<const unsigned*>(&im),
-                               rowaddr, 0u);
-            } else {
-                reinterpret_cast<uint4*>(rc)[idx] =
-                    make_uint4(__float_as_uint(ax), __float_as_uint(bx), __float_as_uint(ay), __float_as_uint(by));
-                ac[idx] = rowaddr;
-            }
-        }
-        for (int rr = threadIdx.x; rr < zt; rr += blockDim.x) {
-            const int r = r0 + rr;
-            dcnt[b * zt + rr] = r < rend ? max(0, min(cc.w, __ldg(dmax + r) + 1) - cc.z) : 0;
-        }
         if (!cta_wait_copies(&bars[b], (phase >> b) & 1u, status)) return false;
         phase ^= 1u << b;
         if (c + 1 < nch) issue(c + 1, b ^ 1);
         if (cc.y == 0 || nrow == 0) continue;
-        const unsigned rbase = smem_u32(rc), obase = smem_u32(ac);
+        const unsigned wbase = smem_u32(bufs + (size_t)b * win * RS);
+        const unsigned rbase = smem_u32(recs + (size_t)b * rblk);
+        const unsigned obase = rbase + (unsigned)(zt * dc * 16);
         // the thread's rows advance together: each d step updates its rows'
         // independent accumulators (records past a row's aperture have zero weights)
-        int ndw = 0;
-#pragma unroll
-        for (int j = 0; j < MAXR; ++j)
-            if (EXACT || j < nrow) ndw = max(ndw, dcnt[b * zt + row0 + j]);
+        const int ndw = max(0, min(cc.w, dmx) - cc.z);
         const int dend = cc.z + min(ndw, max(xe, ye) - cc.z + 1);
         for (int d = cc.z; d < dend;) {
             const int xm = d <= xf ? S1_FULL : (d <= xe ? S1_PRED : S1_NONE);
@@ -455,8 +424,8 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
             if (xe + 1 > d) nx = min(nx, xe + 1);
             if (yf + 1 > d) nx = min(nx, yf + 1);
             if (ye + 1 > d) nx = min(nx, ye + 1);
-#define RCA_S1_RANGE(XM, YM)                                                                                  \
-    stage1_range<TS, MAXR, EXACT, XM, YM>(H, d, nx, cc.z, zt, l, Lx, Ly, row0, nrow, rbase, obase, RS)
+#define RCA_S1_RANGE(XM, YM)                                                                                     \
+    stage1_range<TS, MAXR, EXACT, XM, YM>(H, d, nx, cc.z, zt, l, Lx, Ly, row0, nrow, rbase, obase, wbase, RS)
             switch (xm * 3 + ym) {
             case S1_FULL * 3 + S1_FULL: RCA_S1_RANGE(S1_FULL, S1_FULL); break;
             case S1_FULL * 3 + S1_PRED: RCA_S1_RANGE(S1_FULL, S1_PRED); break;

@@ -82,6 +82,13 @@ struct Stage1Plan {
     int nch = 0;              // chunks per tile
     int win = 0;              // max nrows over all chunks
     int4* d_chunks = nullptr; // [2K][n_tiles][nch] {nlo, nrows, d0, d1}
+    // per-(d, row) weight records of every chunk, one block of rblk bytes per
+    // (k, tile, chunk): [dc][zt] 16-byte records, then [dc][zt] window byte
+    // offsets.  rec32: FP32 weights, offsets for 8-byte samples (4-byte
+    // samples use half of them); rec16: FP16 weights, offsets for 4-byte samples.
+    int rblk = 0;
+    unsigned char* d_rec32 = nullptr;
+    unsigned char* d_rec16 = nullptr;
 };
 
 struct Stage2Plan {
@@ -377,6 +384,8 @@ struct BatchEns {
     const float2* W;
     const int* dmax;
     const int4* chunks;
+    const unsigned char* rtab;  // Stage-1 record table for the batch's IQ dtype
+    int rblk;
     int zt, dc, n_tiles, nch, win;
     const float2* mix;
     const int* sfl;

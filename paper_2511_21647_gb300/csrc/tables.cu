@@ -364,11 +364,67 @@ int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* out)
     return win;
 }
 
-// double-buffered windows + per-(d, row) weight records (16 B) and row
-// addresses (4 B) + per-row counts
+// bytes of one chunk's record block: [dc][zt] 16-byte records + [dc][zt]
+// 4-byte window offsets, rounded up to 16 (a TMA bulk copy unit)
+static int stage1_rblk(int zt, int dc) { return ((zt * dc * 20) + 15) / 16 * 16; }
+
+// double-buffered sample windows and record blocks
 size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t esz)
 {
-    return 2 * (size_t)win * t->gd.N * esz + 2 * (size_t)zt * dc * (16 + 4) + 2 * (size_t)zt * 4;
+    return 2 * (size_t)win * t->gd.N * esz + 2 * (size_t)stage1_rblk(zt, dc);
+}
+
+// Stage-1 records of every (k, tile, chunk): one thread per (d, row) slot.
+// HALF: FP16 weights {Re a, Re b}, {Im a, Im b}, then the window offset for
+// 4-byte samples; otherwise FP32 {Re a, Re b, Im a, Im b} with the offsets
+// (for 8-byte samples) in the block's second array.  a = w (1 - fr),
+// b = w fr, halved at d = 0 (the two mirror elements coincide there); zero
+// where the distance is outside the row's aperture or the delay leaves the
+// record.
+template <bool HALF>
+__global__ void k_s1_records(GeomDev g, const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
+                             const float2* __restrict__ W, const int* __restrict__ dmax,
+                             const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch, int rblk,
+                             unsigned char* __restrict__ out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int per_blk = zt * dc;
+    const long long total = (long long)2 * g.K * n_tiles * nch * per_blk;
+    if (idx >= total) return;
+    const int slot = (int)(idx % per_blk);
+    const long long cb = idx / per_blk;             // (k * n_tiles + tile) * nch + c
+    const int tile = (int)((cb / nch) % n_tiles), k = (int)(cb / ((long long)nch * n_tiles));
+    const int dd = slot / zt, rr = slot - dd * zt;
+    const int4 cc = chunks[cb];
+    const int r = tile * zt + rr, d = cc.z + dd;
+    const int RS = g.N * (HALF ? 4 : 8);
+    const int qmax = (g.ns - 1) << 16;
+    float ax = 0.f, bx = 0.f, ay = 0.f, by = 0.f;
+    int off = 0;
+    if (r < g.nzs && d < cc.w && d <= dmax[r]) {
+        const int q = tx_q16[(size_t)k * g.nzs + r] + rx_q16[(size_t)r * g.N + d];
+        if (q >= 0 && q <= qmax) {
+            const float2 w = W[(size_t)r * g.N + d];
+            const float fr = (float)(q & 0xffff) * (1.0f / 65536.0f);
+            const float h = d == 0 ? 0.5f : 1.0f;
+            ax = h * w.x * (1.0f - fr);
+            bx = h * w.x * fr;
+            ay = h * w.y * (1.0f - fr);
+            by = h * w.y * fr;
+            off = ((q >> 16) - cc.x) * RS;
+        }
+    }
+    unsigned char* blk = out + cb * rblk;
+    uint4 rec;
+    if (HALF) {
+        const __half2 re = __floats2half2_rn(ax, bx), im = __floats2half2_rn(ay, by);
+        rec = make_uint4(*reinterpret_cast<const unsigned*>(&re), *reinterpret_cast<const unsigned*>(&im),
+                         (unsigned)off, 0u);
+    } else {
+        rec = make_uint4(__float_as_uint(ax), __float_as_uint(bx), __float_as_uint(ay), __float_as_uint(by));
+    }
+    reinterpret_cast<uint4*>(blk)[slot] = rec;
+    reinterpret_cast<int*>(blk + (size_t)per_blk * 16)[slot] = off;
 }
 
 rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
@@ -389,13 +445,42 @@ rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
         cudaFree(d);
         return st;
     }
+    const int n_tiles = (t->gd.nzs + zt - 1) / zt, nch = (t->gd.N + dc - 1) / dc;
+    const int rblk = stage1_rblk(zt, dc);
+    const size_t nblk = (size_t)2 * t->gd.K * n_tiles * nch;
+    unsigned char* r32 = dalloc<unsigned char>(h, nblk * rblk, &st);
+    unsigned char* r16 = st == RCA_OK ? dalloc<unsigned char>(h, nblk * rblk, &st) : nullptr;
+    if (st != RCA_OK) {
+        cudaFree(d);
+        if (r32) cudaFree(r32);
+        return st;
+    }
+    const long long slots = (long long)nblk * zt * dc;
+    const unsigned grid = (unsigned)((slots + 255) / 256);
+    k_s1_records<false><<<grid, 256, 0, h->stream>>>(t->gd, t->tx_q16, t->rx_q16, t->W, t->dmax, d, zt, dc, n_tiles,
+                                                      nch, rblk, r32);
+    k_s1_records<true><<<grid, 256, 0, h->stream>>>(t->gd, t->tx_q16, t->rx_q16, t->W, t->dmax, d, zt, dc, n_tiles,
+                                                     nch, rblk, r16);
+    st = cuda_check(h, cudaGetLastError(), "Stage-1 record kernels");
+    if (st == RCA_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "Stage-1 record build");
+    if (st != RCA_OK) {
+        cudaFree(d);
+        cudaFree(r32);
+        cudaFree(r16);
+        return st;
+    }
     if (t->s1.d_chunks) cudaFree(t->s1.d_chunks);
+    if (t->s1.d_rec32) cudaFree(t->s1.d_rec32);
+    if (t->s1.d_rec16) cudaFree(t->s1.d_rec16);
     t->s1.d_chunks = d;
+    t->s1.d_rec32 = r32;
+    t->s1.d_rec16 = r16;
+    t->s1.rblk = rblk;
     t->s1.zt = zt;
     t->s1.dc = dc;
     t->s1.win = win;
-    t->s1.n_tiles = (t->gd.nzs + zt - 1) / zt;
-    t->s1.nch = (t->gd.N + dc - 1) / dc;
+    t->s1.n_tiles = n_tiles;
+    t->s1.nch = nch;
     return RCA_OK;
 }
 
