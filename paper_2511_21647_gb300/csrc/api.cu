@@ -244,7 +244,7 @@ extern "C" rca_status rca_geometry_destroy(rca_geometry* g)
 static void free_tables(rca_tables* t)
 {
     void* ptrs[] = {t->tx_f64, t->rx_f64, t->tx_q16, t->rx_q16, t->W, t->dmax, t->s2_shift, t->s2_sfl,
-                    t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin, t->dtx_q16, t->dtx_ph, t->mix,
+                    t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin, t->s2_c2, t->dtx_q16, t->dtx_ph, t->mix,
                     t->s1.d_chunks, t->s1.d_rec32, t->s1.d_rec16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -613,7 +613,7 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
     };
     int counters = 0;
     size_t smem = (size_t)32 * 159 * 8;  // demodulation tile (DM_NE x DM_PITCH float2)
-    int maxr = 1, zpmax = 1;
+    int maxr = 1, tmax = 1, tmin_all = 1 << 30;
     std::vector<int4> segA, segRest;
     int unit = 0;
     b->ens.resize(n);
@@ -656,13 +656,24 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.smin0 = t->s2.smin[0];
         E.smin1 = t->s2.smin[1];
         E.n_tiles2 = t->s2.n_tiles;
+        E.c2 = t->s2_c2;
+        E.iA = t->s2_iA;
+        E.iB = t->s2_iB;
+        {
+            const int GW = s2_group_width(g.P);
+            if (GW == 0) {
+                st = set_error(h, RCA_ERR_UNSUPPORTED, "Stage 2 needs an even multiple of P (%d) up to 32", g.P);
+                break;
+            }
+            E.LG = (g.N + GW - 1) / GW;
+        }
         const int ncol = nt * g.N * g.ns;
         const int nbx = (g.ns + 127) / 128, nby = (g.N + 31) / 32;
         E.nA = (ncol / 4 + 255) / 256;
         E.nB_fk = nbx * nby;
         E.nB = E.nB_fk * F * nt;
         E.nC = E.n_tiles * nt * F;
-        E.nD = E.n_tiles2 * 2 * F;
+        E.nD = E.n_tiles2 * E.LG * 2 * F;
         E.cA = counters;
         E.cB0 = counters + 1;
         E.cC0 = counters + 1 + F * nt;
@@ -673,7 +684,8 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         segRest.push_back(make_int4(BS_STAGE2, e, 0, E.nD));
         int LW = (g.N + 31) / 32, RG = std::max(1, 8 / LW);
         maxr = std::max(maxr, (E.zt + RG - 1) / RG);
-        while (zpmax < E.zp) zpmax <<= 1;
+        tmax = std::max(tmax, t->T);
+        tmin_all = std::min(tmin_all, t->T);
         smem = std::max(smem, stage1_smem_bytes(t, E.zt, E.dc, E.win, esz));
         smem = std::max(smem, stage2_smem_bytes(t, E.zp));
         if (prm) {
@@ -702,7 +714,8 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
     b->total = unit;
     b->n_counters = counters;
     b->maxr = maxr;
-    b->zpmax = zpmax;
+    b->tmax = tmax;
+    b->tmin_all = tmin_all;
     b->smem = smem;
     if (cudaMalloc(&b->d_ens, sizeof(BatchEns) * n) != cudaSuccess ||
         cudaMalloc(&b->d_segs, sizeof(int4) * b->segs.size()) != cudaSuccess ||

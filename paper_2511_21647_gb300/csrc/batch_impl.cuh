@@ -28,7 +28,7 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar)
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <typename TS, int MAXR, int ZP>
+template <typename TS, int MAXR, int TM>
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
                                                  int nseg, int total, int* __restrict__ cnt, int n_counters,
                                                  long long wait_limit, Fir fir, int rf_t, int iq_t, int pt,
@@ -74,8 +74,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ e
             done = E.cC0 + a2;
         } else {
             a0 = loc % E.n_tiles2;               // tile
-            a1 = (loc / E.n_tiles2) % 2;         // family
-            a2 = loc / (E.n_tiles2 * 2);         // f
+            a1 = (loc / E.n_tiles2) % (2 * E.LG);  // lateral group * 2 + family
+            a2 = loc / (E.n_tiles2 * 2 * E.LG);  // f
             dep = E.cC0 + a2;
             dep_target = E.n_tiles * nt;
         }
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ e
             ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.rtab, E.rblk, E.dmax, E.chunks,
                                               E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);
         } else {
-            ok = stage2_body<ZP>(a0, a1, a2, E.zp, reinterpret_cast<float2*>(smraw), &bars[0], g, E.slices, E.sfl,
-                                 E.sfr, E.psi, E.ec, E.coef, E.tmin, E.T, E.rows, E.smin0, E.smin1, E.planes, pt,
+            ok = stage2_body<TM>(a0, a1 >> 1, a1 & 1, a2, smraw, &bars[0], g, E.slices, E.sfl, E.sfr, E.psi, E.ec,
+                                 E.coef, E.c2, E.tmin, E.T, E.iA, E.iB, E.zp, E.rows, E.smin0, E.smin1, E.planes, pt,
                                  status);
         }
         __syncthreads();
@@ -143,10 +143,10 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ e
 // ---------------------------------------------------------------------------
 // batched launch
 // ---------------------------------------------------------------------------
-template <typename TS, int MAXR, int ZP>
+template <typename TS, int MAXR, int TM>
 static rca_status batch_launch(rca_handle* h, rca_batch* b)
 {
-    auto kern = k_batch<TS, MAXR, ZP>;
+    auto kern = k_batch<TS, MAXR, TM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     if (e != cudaSuccess) return cuda_check(h, e, "batch smem attribute");
     if (b->grid == 0) {
@@ -166,22 +166,18 @@ static rca_status batch_launch(rca_handle* h, rca_batch* b)
 }
 
 template <typename TS, int MAXR>
-static rca_status batch_zp(rca_handle* h, rca_batch* b)
+static rca_status batch_tm(rca_handle* h, rca_batch* b)
 {
-    switch (b->zpmax) {
-    case 1: return batch_launch<TS, MAXR, 1>(h, b);
-    case 2: return batch_launch<TS, MAXR, 2>(h, b);
-    case 4: return batch_launch<TS, MAXR, 4>(h, b);
-    case 8: return batch_launch<TS, MAXR, 8>(h, b);
-    default: return batch_launch<TS, MAXR, 16>(h, b);
-    }
+    // one tap count shared by every ensemble: exact, else the generic loop
+    if (b->tmax == 3 && b->tmin_all == 3) return batch_launch<TS, MAXR, 3>(h, b);
+    return batch_launch<TS, MAXR, 0>(h, b);
 }
 
 template <typename TS>
 static rca_status batch_maxr(rca_handle* h, rca_batch* b)
 {
-    if (b->maxr <= 2) return batch_zp<TS, 2>(h, b);
-    if (b->maxr <= 4) return batch_zp<TS, 4>(h, b);
-    if (b->maxr <= 8) return batch_zp<TS, 8>(h, b);
-    return batch_zp<TS, 16>(h, b);
+    if (b->maxr <= 2) return batch_tm<TS, 2>(h, b);
+    if (b->maxr <= 4) return batch_tm<TS, 4>(h, b);
+    if (b->maxr <= 8) return batch_tm<TS, 8>(h, b);
+    return batch_tm<TS, 16>(h, b);
 }

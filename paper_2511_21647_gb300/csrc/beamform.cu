@@ -34,18 +34,19 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
                                 dc, n_tiles, nch, win, slices, status);
 }
 
-template <int ZP>
-__global__ void __launch_bounds__(512) k_stage2(GeomDev g, const float2* __restrict__ slices,
-                                                const int* __restrict__ sfl, const float* __restrict__ sfr,
-                                                const float2* __restrict__ psi, const float2* __restrict__ ec,
-                                                const float2* __restrict__ coef, const int* __restrict__ tmin, int T,
-                                                int rows, int smin0, int smin1, void* __restrict__ planes, int pt,
-                                                unsigned* __restrict__ status)
+template <int TM>
+__global__ void __launch_bounds__(S2_THREADS) k_stage2(GeomDev g, const float2* __restrict__ slices,
+                                                       const int* __restrict__ sfl, const float* __restrict__ sfr,
+                                                       const float2* __restrict__ psi, const float2* __restrict__ ec,
+                                                       const float2* __restrict__ coef, const float2* __restrict__ c2,
+                                                       const int* __restrict__ tmin, int T, int iA, int iB, int zp,
+                                                       int rows, int smin0, int smin1, void* __restrict__ planes,
+                                                       int pt, unsigned* __restrict__ status)
 {
-    extern __shared__ __align__(128) float2 sm[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bar;
-    stage2_body<ZP>(blockIdx.x, blockIdx.y, blockIdx.z, ZP, sm, &bar, g, slices, sfl, sfr, psi, ec, coef, tmin, T,
-                    rows, smin0, smin1, planes, pt, status);
+    stage2_body<TM>(blockIdx.x, blockIdx.y, blockIdx.z & 1, blockIdx.z >> 1, smraw, &bar, g, slices, sfl, sfr, psi, ec,
+                    coef, c2, tmin, T, iA, iB, zp, rows, smin0, smin1, planes, pt, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -238,34 +239,33 @@ rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca
     return set_error(h, RCA_ERR_UNSUPPORTED, "iq dtype must be C32, C16F or C16BF");
 }
 
-template <int ZP>
+template <int TM>
 static rca_status stage2_launch(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes,
                                 rca_dtype pt)
 {
     const GeomDev& g = t->gd;
-    const int rows = t->s2.rows, K = g.K, S = g.S, T = t->T;
-    size_t smem = ((size_t)K * rows * g.N + (size_t)K * S * rows + (size_t)K * S * ZP * T + (size_t)K * g.N +
-                   (size_t)K * ZP) * sizeof(float2) +
-                  ((size_t)2 * K * g.N + (size_t)K * S) * sizeof(int);
-    auto kern = k_stage2<ZP>;
+    const int GW = s2_group_width(g.P);
+    if (GW == 0) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage 2 needs an even multiple of P (%d) up to 32", g.P);
+    if (2 * (long long)F > 65535) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 32767 frames in one call");
+    const size_t smem = stage2_smem_bytes(t, t->s2.zp);
+    auto kern = k_stage2<TM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage2 smem attribute");
-    dim3 grid(t->s2.n_tiles, 2, F);
-    kern<<<grid, 512, smem, h->stream>>>(g, slices, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin,
-                                         T, rows, t->s2.smin[0], t->s2.smin[1], planes, (int)pt, h->d_status);
+    dim3 grid(t->s2.n_tiles, (g.N + GW - 1) / GW, 2 * F);
+    kern<<<grid, S2_THREADS, smem, h->stream>>>(g, slices, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef,
+                                                t->s2_c2, t->s2_tmin, t->T, t->s2_iA, t->s2_iB, t->s2.zp, t->s2.rows,
+                                                t->s2.smin[0], t->s2.smin[1], planes, (int)pt, h->d_status);
     return cuda_check(h, cudaGetLastError(), "stage2 kernel");
 }
 
 rca_status launch_stage2(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes, rca_dtype pt)
 {
     if (!complex_dtype(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
-    switch (t->s2.zp) {
-    case 1: return stage2_launch<1>(h, t, slices, F, planes, pt);
-    case 2: return stage2_launch<2>(h, t, slices, F, planes, pt);
-    case 4: return stage2_launch<4>(h, t, slices, F, planes, pt);
-    case 8: return stage2_launch<8>(h, t, slices, F, planes, pt);
-    default: return stage2_launch<16>(h, t, slices, F, planes, pt);
-    }
+    // exact tap counts of the usual steering ranges; any other count runs the generic loop
+    if (t->T == 2) return stage2_launch<2>(h, t, slices, F, planes, pt);
+    if (t->T == 3) return stage2_launch<3>(h, t, slices, F, planes, pt);
+    if (t->T == 4) return stage2_launch<4>(h, t, slices, F, planes, pt);
+    return stage2_launch<0>(h, t, slices, F, planes, pt);
 }
 
 template <int MAXR>

@@ -454,173 +454,267 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
 // Stage 2 + block sum-projection, written straight to the planes.
 // For a family, the "transverse-slab" plane sums over the transverse
 // coordinate u inside slab b: each u shifts the slice by its own dz_k(u), so
-// the per-(k, b, i) sum of P linear interpolations is a short filter along
-// the slice rows with precomputed coefficients.  The "lateral-slab" plane sums
-// over lateral pixels inside slab b: the shift does not depend on the lateral
-// pixel, so the slice is first summed over the slab and interpolated once.
+// the per-(k, b) sum of P linear interpolations is a short filter along the
+// slice rows.  Its taps are the same for every plane row up to the row's
+// carrier, coef[k][b][i][t] = ec[k][i] c2[k][b][t], except in the few rows
+// near the slice ends where a shifted row leaves the slice (there the exact
+// per-row taps are used).  The "lateral-slab" plane sums over lateral pixels
+// inside slab b: the shift does not depend on the lateral pixel, so the
+// slice is first summed over the slab and interpolated once per u.
 // RC: transverse = y -> XZ planes (axis 0), lateral-slab -> YZ (axis 1).
 // CR: transverse = x -> YZ planes (axis 1), lateral-slab -> XZ (axis 0).
+// A CTA covers one frame and family, up to S2_ZP plane rows and one group of
+// GW lateral pixels: it stages the group's slice columns for all K
+// transmissions, then its warps write the transverse-slab planes of every
+// slab at those pixels and the lateral-slab planes of the group's slabs at
+// every u, S2_RH plane rows per warp task.
 // ---------------------------------------------------------------------------
-template <int ZP>
-__device__ __forceinline__ bool stage2_body(int tile, int fam, int f, int zp, float2* __restrict__ sm, uint64_t* barp,
-                                            const GeomDev& g, const float2* __restrict__ slices,
+#define S2_RH 8        // plane rows per warp task
+
+// transverse-slab plane rows [q0, q0 + S2_RH) of slab b at lateral pixel g0 + lane.
+// TT: tap count (0: t->T at run time, up to 16).  INTERIOR: every row of the
+// tile has carrier-separable taps.
+template <int TT, bool INTERIOR>
+__device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, int ib, int lane, int gw, int fam,
+                                              int f, int i0, int axT, const GeomDev& g, int T, int rows,
+                                              unsigned sSa, const float4* __restrict__ sEc,
+                                              const float2* __restrict__ sC2, const int* __restrict__ sTb,
+                                              const float2* __restrict__ sS, const float2* __restrict__ coef,
+                                              void* __restrict__ planes, int pt, int g0)
+{
+    const int K = g.K, S = g.S, N = g.N, us = g.us;
+    constexpr int TMX = TT > 0 ? TT : 16;
+    const int nT = TT > 0 ? TT : T;
+    uint64_t O1[S2_RH], O2[S2_RH];   // out = (O1.x - O2.y, O1.y + O2.x)
+#pragma unroll
+    for (int q = 0; q < S2_RH; ++q) O1[q] = O2[q] = 0ull;
+    for (int kk = 0; kk < K; ++kk) {
+        const int tb = sTb[kk * S + b];
+        uint64_t cx[TMX], cy[TMX];
+#pragma unroll
+        for (int t = 0; t < TMX; ++t) {
+            const float2 c = t < nT ? sC2[(kk * S + b) * T + t] : make_float2(0.f, 0.f);
+            cx[t] = f2_pack(c.x, c.x);
+            cy[t] = f2_pack(c.y, c.y);
+        }
+        // this lane's column in transmission kk at the window row of plane row q0
+        const unsigned col = sSa + (unsigned)((((kk * rows + tb + us * q0) * 32) + lane) * 8);
+        const unsigned rstep = (unsigned)(us * 32 * 8);
+#pragma unroll
+        for (int q = 0; q < S2_RH; ++q) {
+            const int ii = q0 + q;
+            if (INTERIOR || (ii >= ia && ii < ib)) {
+                uint64_t A1 = 0ull, A2 = 0ull;
+#pragma unroll
+                for (int t = 0; t < TMX; ++t) {
+                    if (TT > 0 || t < nT) {
+                        const uint64_t v = lds_u64(col + q * rstep + (unsigned)(t * 32 * 8));
+                        A1 = f2_fma(cx[t], v, A1);
+                        A2 = f2_fma(cy[t], v, A2);
+                    }
+                }
+                const float2 p1 = f2_unpack(A1), p2 = f2_unpack(A2);
+                const uint64_t y = f2_pack(p1.x - p2.y, p1.y + p2.x);
+                uint64_t ex, ey;
+                lds_u64x2(smem_u32(sEc + kk * S2_ZP + ii), ex, ey);
+                O1[q] = f2_fma(ex, y, O1[q]);
+                O2[q] = f2_fma(ey, y, O2[q]);
+            } else if (ii < nrow) {
+                // rows near the slice ends: exact per-row taps (carrier included)
+                const float2* cf = coef + (((size_t)(fam * K + kk) * S + b) * g.nz + i0 + ii) * T;
+                float2 y = make_float2(0.f, 0.f);
+                for (int t = 0; t < T; ++t) cfma(y, __ldg(cf + t), sS[((size_t)kk * rows + tb + us * ii + t) * 32 + lane]);
+                O1[q] = f2_add(O1[q], f2_pack(y.x, y.y));
+            }
+        }
+    }
+    if (lane < gw) {
+        const size_t plane_sz = (size_t)g.nz * N;
+        const size_t ob = ((((size_t)f * 2 + axT) * 2 + fam) * S + b) * plane_sz + (size_t)(i0 + q0) * N + g0 + lane;
+#pragma unroll
+        for (int q = 0; q < S2_RH; ++q) {
+            if (INTERIOR || q0 + q < nrow) {
+                const float2 p1 = f2_unpack(O1[q]), p2 = f2_unpack(O2[q]);
+                store_c_cs(planes, ob + (size_t)q * N, pt, make_float2(p1.x - p2.y, p1.y + p2.x));
+            }
+        }
+    }
+}
+
+// lateral-slab plane rows [q0, q0 + S2_RH) of group slab sb at transverse position u
+template <bool INTERIOR>
+__device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int ia, int ib, int fam, int f, int i0,
+                                           int axL, int rlo, int grp, int SG, const GeomDev& g, int rows,
+                                           const float4* __restrict__ sEc, const float4* __restrict__ sLw,
+                                           const int* __restrict__ sSh, const float2* __restrict__ sSum,
+                                           const float* __restrict__ sfr, void* __restrict__ planes, int pt)
+{
+    const int K = g.K, S = g.S, N = g.N, us = g.us;
+    float2 O[S2_RH];
+#pragma unroll
+    for (int q = 0; q < S2_RH; ++q) O[q] = make_float2(0.f, 0.f);
+    for (int kk = 0; kk < K; ++kk) {
+        const float4 w = sLw[kk * N + u];            // a = psi (1 - fr), b = psi fr
+        const int sh = sSh[kk * N + u];
+        const float fr = INTERIOR ? 0.f : __ldg(sfr + (size_t)(fam * K + kk) * N + u);
+        const float2* src = sSum + ((size_t)kk * SG + sb) * rows + sh + us * q0;
+#pragma unroll
+        for (int q = 0; q < S2_RH; ++q) {
+            const int ii = q0 + q;
+            bool valid = true;
+            if (!INTERIOR) {
+                // zero where the interpolation point leaves [0, nzs - 1]
+                const int n0 = rlo + sh + us * ii;
+                valid = ii < nrow && ((ii >= ia && ii < ib) ||
+                                      (n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f))));
+            }
+            if (valid) {
+                const float2 s0 = src[us * q], s1 = src[us * q + 1];
+                float yx = w.x * s0.x;
+                yx = fmaf(-w.y, s0.y, yx);
+                yx = fmaf(w.z, s1.x, yx);
+                yx = fmaf(-w.w, s1.y, yx);
+                float yy = w.x * s0.y;
+                yy = fmaf(w.y, s0.x, yy);
+                yy = fmaf(w.z, s1.y, yy);
+                yy = fmaf(w.w, s1.x, yy);
+                const float4 e = sEc[kk * S2_ZP + ii];
+                O[q].x = fmaf(e.x, yx, fmaf(-e.z, yy, O[q].x));
+                O[q].y = fmaf(e.x, yy, fmaf(e.z, yx, O[q].y));
+            }
+        }
+    }
+    const size_t plane_sz = (size_t)g.nz * N;
+    const size_t ob = ((((size_t)f * 2 + axL) * 2 + fam) * S + grp * SG + sb) * plane_sz + (size_t)(i0 + q0) * N + u;
+#pragma unroll
+    for (int q = 0; q < S2_RH; ++q)
+        if (INTERIOR || q0 + q < nrow) store_c_cs(planes, ob + (size_t)q * N, pt, O[q]);
+}
+
+template <int TT>
+__device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, unsigned char* __restrict__ smraw,
+                                            uint64_t* barp, const GeomDev& g, const float2* __restrict__ slices,
                                             const int* __restrict__ sfl, const float* __restrict__ sfr,
                                             const float2* __restrict__ psi, const float2* __restrict__ ec,
-                                            const float2* __restrict__ coef, const int* __restrict__ tmin, int T,
-                                            int rows, int smin0, int smin1, void* __restrict__ planes, int pt,
+                                            const float2* __restrict__ coef, const float2* __restrict__ c2,
+                                            const int* __restrict__ tmin, int T, int iA, int iB, int zp, int rows,
+                                            int smin0, int smin1, void* __restrict__ planes, int pt,
                                             unsigned* __restrict__ status)
 {
     uint64_t& bar = *barp;
     const int N = g.N, K = g.K, S = g.S, P = g.P, us = g.us;
     const int nt = 2 * K;
-    const int i0 = tile * zp;          // zp <= ZP plane rows per tile
+    const int GW = s2_group_width(P), SG = GW / P;
+    const int g0 = grp * GW;                           // first lateral pixel of the group
+    const int gw = min(GW, N - g0);                    // pixels in this group
+    const int sg = gw / P;                             // slabs in this group
+    const int i0 = tile * zp;
     const int nrow = min(zp, g.nz - i0);
     const int smin = fam ? smin1 : smin0;
-    const int rlo = us * i0 + smin;
-    float2* sS = sm;                                 // [K][rows][N]
-    float2* sSum = sS + (size_t)K * rows * N;        // [K][S][rows]
-    float2* sCoef = sSum + (size_t)K * S * rows;     // [K][S][ZP][T]
-    float2* sPsi = sCoef + (size_t)K * S * ZP * T;   // [K][N]
-    float2* sEc = sPsi + (size_t)K * N;              // [K][ZP]
-    float* sSfr = reinterpret_cast<float*>(sEc + (size_t)K * ZP);  // [K][N]
-    int* sSfl = reinterpret_cast<int*>(sSfr + (size_t)K * N);       // [K][N]  (row offset - smin)
-    int* sTb = sSfl + (size_t)K * N;                                 // [K][S]  (tmin - smin)
+    const int rlo = us * i0 + smin;                    // slice row of window row 0
+    float2* sS = reinterpret_cast<float2*>(smraw);                    // [K][rows][32]
+    float4* sEc = reinterpret_cast<float4*>(sS + (size_t)K * rows * 32);  // [K][S2_ZP] {x, x, y, y}
+    float4* sLw = sEc + (size_t)K * S2_ZP;                             // [K][N] {psi(1-fr), psi fr}
+    float2* sSum = reinterpret_cast<float2*>(sLw + (size_t)K * N);     // [K][SG][rows]
+    float2* sC2 = sSum + (size_t)K * SG * rows;                        // [K][S][T]
+    int* sSh = reinterpret_cast<int*>(sC2 + (size_t)K * S * T);        // [K][N] floor shift - smin
+    int* sTb = sSh + (size_t)K * N;                                    // [K][S] tmin - smin
     const int lo = max(rlo, 0), hi = max(lo, min(rlo + rows, g.nzs));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const unsigned cbytes = (unsigned)(gw * sizeof(float2));       // one row segment
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_fence_init();
+        mbar_arrive_expect_tx(&bar, cbytes * (unsigned)(K * (hi - lo)));
+    }
+    // window rows outside the slice (and columns past the group) read zero
+    for (int rk = warp; rk < K * rows; rk += nwarp) {
+        const int r = rlo + rk % rows;
+        if (lane >= gw || r < lo || r >= hi) sS[(size_t)rk * 32 + lane] = make_float2(0.f, 0.f);
     }
     __syncthreads();
+    // one bulk copy per (k, in-slice row): the group's gw pixels
     {
-        const int z0 = min(lo - rlo, rows), z1 = hi - rlo;
-        const int nzr = z0 + (rows - z1);
-        for (int idx = threadIdx.x; idx < K * nzr * N; idx += blockDim.x) {
-            const int kk = idx / (nzr * N), q = idx - kk * nzr * N, zr = q / N, l = q - zr * N;
-            const int rr = zr < z0 ? zr : z1 + (zr - z0);
-            sS[((size_t)kk * rows + rr) * N + l] = make_float2(0.f, 0.f);
+        const int nr = hi - lo;
+        bool fenced = false;
+        for (int idx = threadIdx.x; idx < K * nr; idx += blockDim.x) {
+            const int kk = idx / nr, r = lo + (idx - kk * nr);
+            if (!fenced) {
+                fence_proxy_async();
+                fenced = true;
+            }
+            bulk_g2s(sS + ((size_t)kk * rows + (r - rlo)) * 32,
+                     slices + (((size_t)f * nt + fam * K + kk) * g.nzs + r) * N + g0, cbytes, &bar);
         }
     }
-    if (threadIdx.x == 0) {
-        fence_proxy_async();
-        const unsigned bytes = (unsigned)((hi - lo) * N * sizeof(float2));
-        mbar_arrive_expect_tx(&bar, bytes * K);
-        if (bytes)
-            for (int kk = 0; kk < K; ++kk)
-                bulk_g2s(sS + ((size_t)kk * rows + (lo - rlo)) * N,
-                         slices + (((size_t)f * nt + fam * K + kk) * g.nzs + lo) * N, bytes, &bar);
+    // per-CTA tables while the copies are in flight
+    for (int idx = threadIdx.x; idx < K * S2_ZP; idx += blockDim.x) {
+        const int kk = idx / S2_ZP, ii = idx - kk * S2_ZP;
+        const float2 e = __ldg(ec + (size_t)(fam * K + kk) * g.nz + min(i0 + ii, g.nz - 1));
+        sEc[idx] = make_float4(e.x, e.x, e.y, e.y);
     }
-    // per-CTA table slices while the copy is in flight
-    for (int idx = threadIdx.x; idx < K * S * ZP * T; idx += blockDim.x) {
-        const int t = idx % T, ii = (idx / T) % ZP, kb = idx / (T * ZP);
-        const int kk = kb / S, b = kb % S, i = min(i0 + ii, g.nz - 1);
-        sCoef[idx] = __ldg(coef + (((size_t)(fam * K + kk) * S + b) * g.nz + i) * T + t);
-    }
+    for (int idx = threadIdx.x; idx < K * S * T; idx += blockDim.x) sC2[idx] = __ldg(c2 + (size_t)fam * K * S * T + idx);
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = fam * K + idx / N, u = idx % N;
-        sPsi[idx] = __ldg(psi + (size_t)k * N + u);
-        sSfr[idx] = __ldg(sfr + (size_t)k * N + u);
-        sSfl[idx] = __ldg(sfl + (size_t)k * N + u) - smin;
-    }
-    for (int idx = threadIdx.x; idx < K * ZP; idx += blockDim.x) {
-        const int kk = idx / ZP, ii = idx % ZP;
-        sEc[idx] = __ldg(ec + (size_t)(fam * K + kk) * g.nz + min(i0 + ii, g.nz - 1));
+        const float2 ps = __ldg(psi + (size_t)k * N + u);
+        const float fr = __ldg(sfr + (size_t)k * N + u);
+        sLw[idx] = make_float4(ps.x * (1.0f - fr), ps.y * (1.0f - fr), ps.x * fr, ps.y * fr);
+        sSh[idx] = __ldg(sfl + (size_t)k * N + u) - smin;
     }
     for (int idx = threadIdx.x; idx < K * S; idx += blockDim.x) sTb[idx] = __ldg(tmin + fam * K * S + idx) - smin;
     if (!cta_wait_copies(&bar, 0, status)) return false;
-    // slab sums over the lateral pixels: one warp per (k, row)
-    for (int o = warp; o < K * rows; o += nwarp) {
-        const int kk = o / rows, rr = o - kk * rows;
-        const float2* src = sS + ((size_t)kk * rows + rr) * N;
-        if ((32 % P) == 0) {
-            for (int c0 = 0; c0 < N; c0 += 32) {
-                const int l = c0 + lane;
-                float2 v = l < N ? src[l] : make_float2(0.f, 0.f);
-                for (int m = 1; m < P; m <<= 1) {
-                    v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
-                    v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
-                }
-                if ((lane % P) == 0 && l < N) sSum[((size_t)kk * S + l / P) * rows + rr] = v;
+    // slab sums of the group's slabs: one warp per (k, window row), lanes over the pixels
+    const bool pow2 = (P & (P - 1)) == 0;
+    for (int rk = warp; rk < K * rows; rk += nwarp) {
+        const int kk = rk / rows, rr = rk - kk * rows;
+        if (pow2) {
+            float2 v = sS[(size_t)rk * 32 + lane];
+            for (int m = 1; m < P; m <<= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
             }
-        } else {
-            for (int b = lane; b < S; b += 32) {
-                float2 a = make_float2(0.f, 0.f);
-                for (int q = 0; q < P; ++q) {
-                    a.x += src[b * P + q].x;
-                    a.y += src[b * P + q].y;
-                }
-                sSum[((size_t)kk * S + b) * rows + rr] = a;
+            if (lane % P == 0 && lane / P < sg) sSum[((size_t)kk * SG + lane / P) * rows + rr] = v;
+        } else if (lane < sg) {
+            float2 a = make_float2(0.f, 0.f);
+            for (int m = 0; m < P; ++m) {
+                const float2 v = sS[(size_t)rk * 32 + lane * P + m];
+                a.x += v.x;
+                a.y += v.y;
             }
+            sSum[((size_t)kk * SG + lane) * rows + rr] = a;
         }
     }
     __syncthreads();
     const int axT = fam == 0 ? 0 : 1;
     const int axL = 1 - axT;
-    const size_t plane_sz = (size_t)g.nz * N;
-    const int LW = (N + 31) >> 5;
-    // transverse-slab planes: out[b][i][l] = sum_k sum_t coef[k][b][i][t] S_k(l, us i + tmin[k][b] + t)
-    for (int o = warp; o < S * LW; o += nwarp) {
-        const int lw = o % LW, b = o / LW;
-        const int l = lw * 32 + lane, lc = l < N ? l : 0;
-        uint64_t a1[ZP], a2[ZP];
-#pragma unroll
-        for (int ii = 0; ii < ZP; ++ii) a1[ii] = a2[ii] = 0ull;
-        for (int kk = 0; kk < K; ++kk) {
-            const int tb = sTb[kk * S + b];
-            const float2* cf = sCoef + (size_t)(kk * S + b) * ZP * T;
-            const uint64_t* col = reinterpret_cast<const uint64_t*>(sS + ((size_t)kk * rows + tb) * N + lc);
-            for (int t = 0; t < T; ++t) {
-#pragma unroll
-                for (int ii = 0; ii < ZP; ++ii) {
-                    if (ii < nrow) {
-                        const float2 c = cf[ii * T + t];
-                        const uint64_t v = col[(size_t)(us * ii + t) * N];
-                        a1[ii] = f2_fma(f2_pack(c.x, c.x), v, a1[ii]);
-                        a2[ii] = f2_fma(f2_pack(c.y, c.y), v, a2[ii]);
-                    }
-                }
+    // the tile's rows with carrier-separable taps: [ia, ib) (tile-relative)
+    const int ia = min(nrow, max(0, iA - i0)), ib = max(ia, min(nrow, iB - i0 + 1));
+    const bool interior = ia == 0 && ib == nrow && nrow == S2_ZP;
+    const int H = (nrow + S2_RH - 1) / S2_RH;          // row halves
+    const int LU = (N + 31) >> 5;
+    const int nTt = S * H, nTl = sg * LU * H;
+    const unsigned sSa = smem_u32(sS);
+    for (int task = warp; task < nTt + nTl; task += nwarp) {
+        if (task < nTt) {
+            const int b = task / H, q0 = (task - b * H) * S2_RH;
+            if (interior)
+                s2_transverse<TT, true>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sSa, sEc, sC2, sTb,
+                                        sS, coef, planes, pt, g0);
+            else
+                s2_transverse<TT, false>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sSa, sEc, sC2, sTb,
+                                         sS, coef, planes, pt, g0);
+        } else {
+            const int o = task - nTt;
+            const int hq = o % H, rest = o / H, sb = rest / LU, u = (rest - sb * LU) * 32 + lane;
+            if (u < N) {
+                if (interior)
+                    s2_lateral<true>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sEc, sLw,
+                                     sSh, sSum, sfr, planes, pt);
+                else
+                    s2_lateral<false>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sEc, sLw,
+                                      sSh, sSum, sfr, planes, pt);
             }
         }
-        if (l < N) {
-            const size_t ob = ((((size_t)f * 2 + axT) * 2 + fam) * S + b) * plane_sz + (size_t)i0 * N + l;
-#pragma unroll
-            for (int ii = 0; ii < ZP; ++ii) {
-                if (ii < nrow) {
-                    const float2 p1 = f2_unpack(a1[ii]), p2 = f2_unpack(a2[ii]);
-                    store_c_cs(planes, ob + (size_t)ii * N, pt, make_float2(p1.x - p2.y, p1.y + p2.x));
-                }
-            }
-        }
-    }
-    // lateral-slab planes: out[b][i][u] = sum_k ec[k][i] psi[k][u] lerp(sum_{l in b} S_k(l, .), us i + s_k(u))
-    for (int o = warp; o < S * LW; o += nwarp) {
-        const int lw = o % LW, b = o / LW;
-        const int u = lw * 32 + lane;
-        if (u >= N) continue;
-        float2 acc[ZP];
-#pragma unroll
-        for (int ii = 0; ii < ZP; ++ii) acc[ii] = make_float2(0.f, 0.f);
-        for (int kk = 0; kk < K; ++kk) {
-            const int n0r = sSfl[kk * N + u];     // row offset relative to rlo at ii = 0
-            const float fr = sSfr[kk * N + u];
-            const float2 ps = sPsi[kk * N + u];
-            const float2* src = sSum + ((size_t)kk * S + b) * rows;
-#pragma unroll
-            for (int ii = 0; ii < ZP; ++ii) {
-                const int nr = us * ii + n0r;
-                const int n0 = rlo + nr;          // slice row
-                const bool valid = ii < nrow && n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f));
-                if (valid) {
-                    const float2 s0 = src[nr], s1 = src[nr + 1];
-                    const float2 v = make_float2(fmaf(fr, s1.x - s0.x, s0.x), fmaf(fr, s1.y - s0.y, s0.y));
-                    cfma(acc[ii], cmul(sEc[kk * ZP + ii], ps), v);
-                }
-            }
-        }
-        const size_t ob = ((((size_t)f * 2 + axL) * 2 + fam) * S + b) * plane_sz + (size_t)i0 * N + u;
-#pragma unroll
-        for (int ii = 0; ii < ZP; ++ii)
-            if (ii < nrow) store_c_cs(planes, ob + (size_t)ii * N, pt, acc[ii]);
     }
     return true;
 }

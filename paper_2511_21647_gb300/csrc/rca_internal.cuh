@@ -118,6 +118,11 @@ struct rca_tables {
     float2* s2_coef = nullptr;  // [2K][S][nz][T]
     int* s2_tmin = nullptr;     // [2K][S]
     int T = 0;
+    // the same taps without the row's carrier: coef[k][b][i][t] = ec[k][i] c2[k][b][t]
+    // for every plane row i in [s2_iA, s2_iB] (all of the slab's shifted rows
+    // inside the slice)
+    float2* s2_c2 = nullptr;    // [2K][S][T]
+    int s2_iA = 0, s2_iB = -1;
     // direct (conventional 3D) tables
     int* dtx_q16 = nullptr;     // [2K][N][nz] transmit delay at transverse u, plane depth
     float2* dtx_ph = nullptr;   // [2K][N][nz] exp(j 2 pi fc (tau_tx + z / c))
@@ -131,6 +136,34 @@ struct rca_tables {
     // host copies used to (re)plan launch shapes
     std::vector<int> h_txq, h_rxq, h_dm, h_sfl;
 };
+
+// Stage-2 CTA geometry (shared by the planner and the kernels)
+#define S2_ZP 16       // plane rows per CTA (at most)
+#define S2_THREADS 256
+
+// lateral pixels per CTA: the largest even multiple of P up to 32 (even, so
+// that a row segment of complex FP32 values is a whole number of 16-byte
+// units); 0 where no such multiple exists (P odd above 15, or P > 32)
+inline __host__ __device__ int s2_group_width(int P)
+{
+    if (P > 32) return 0;
+    int m = 32 / P;
+    if (P & 1) m &= ~1;
+    return m * P;
+}
+
+// shared-memory bytes of one Stage-2 CTA
+inline __host__ __device__ size_t s2_smem_bytes(int K, int S, int N, int P, int T, int rows)
+{
+    const int GW = s2_group_width(P), SG = GW > 0 ? GW / P : 1;
+    return (size_t)K * rows * 32 * 8          // slice columns [K][rows][32]
+           + (size_t)K * S2_ZP * 16           // carrier pairs [K][ZP] {x, x, y, y}
+           + (size_t)K * N * 16               // lateral weights [K][N] {psi (1 - fr), psi fr}
+           + (size_t)K * SG * rows * 8        // slab sums [K][SG][rows]
+           + (size_t)K * S * T * 8            // row-independent taps [K][S][T]
+           + (size_t)K * N * 4 + (size_t)K * S * 4;  // shift rows [K][N], tap rows [K][S]
+}
+
 
 // launch-shape planning (tables.cu)
 int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* chunks);
@@ -335,6 +368,13 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
     return d;
 }
 
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
 {
     uint64_t d;
@@ -395,6 +435,8 @@ struct BatchEns {
     const float2* coef;
     const int* tmin;
     int T, zp, rows, smin0, smin1, n_tiles2;
+    const float2* c2;
+    int iA, iB, LG;
     // work units and counters
     int nA, nB, nC, nD;      // units per stage
     int nB_fk;               // demodulation units per (frame, transmission)
@@ -415,7 +457,7 @@ struct rca_batch {
     std::vector<void*> owned;     // per-ensemble workspace
     float fir[31];
     long long wait_limit = RCA_WAIT_CYCLES;
-    int maxr = 2, zpmax = 1;
+    int maxr = 2, tmax = 1, tmin_all = 1 << 30;
     size_t smem = 0;
     int grid = 0;
     // optional localisation

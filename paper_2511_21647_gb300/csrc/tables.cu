@@ -154,6 +154,40 @@ __global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, i
     for (int t = 0; t < T; ++t) coef[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
 }
 
+// Row-independent transverse-slab taps: for slab b,
+//   c2[k][b][t] = sum_{u in slab} exp(j 2 pi fc (1 + cos th_k) dz_k(u) / c) lerp_weights,
+// so that coef[k][b][i][t] = ec[k][i] c2[k][b][t] wherever every shifted row
+// of the slab lies inside the slice (the carrier phase of tau_c is linear in z).
+__global__ void k_tables_coef2(GeomDev g, const double* shift, const int* tmin, int T, float2* c2, unsigned* status)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int nt = 2 * g.K;
+    if (idx >= nt * g.S) return;
+    int b = idx % g.S, k = idx / g.S;
+    double accr[16], acci[16];
+    for (int t = 0; t < T; ++t) accr[t] = acci[t] = 0.0;
+    for (int m = b * g.P; m < (b + 1) * g.P; ++m) {
+        double s = shift[(size_t)k * g.N + m];
+        double fl = floor(s);
+        double fr = s - fl;
+        double sh = elem_pos(g, m) * g.sin_th[k] / (1.0 + g.cos_th[k]);
+        double sn, cs;
+        sincos(TWO_PI_D * g.fc * (1.0 + g.cos_th[k]) * sh / g.c, &sn, &cs);
+        int t = (int)fl - tmin[idx];
+        if (t < 0 || t + (fr > 0.0 ? 1 : 0) >= T) {
+            atomicOr(status, ST_BOUNDS);
+            continue;
+        }
+        accr[t] += (1.0 - fr) * cs;
+        acci[t] += (1.0 - fr) * sn;
+        if (fr > 0.0) {
+            accr[t + 1] += fr * cs;
+            acci[t + 1] += fr * sn;
+        }
+    }
+    for (int t = 0; t < T; ++t) c2[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
+}
+
 // Conventional-DAS transmit tables at every transverse position and plane row.
 __global__ void k_tables_direct(GeomDev g, int* dtx_q16, float2* dtx_ph)
 {
@@ -284,6 +318,22 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     k_tables_coef<<<(nt * g.S * g.nz + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_tmin, T, t->s2_coef,
                                                                  h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "coef kernel")) != RCA_OK) return st;
+    t->s2_c2 = dalloc<float2>(h, (size_t)nt * g.S * T, &st);
+    if (st != RCA_OK) return st;
+    k_tables_coef2<<<(nt * g.S + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_tmin, T, t->s2_c2, h->d_status);
+    if ((st = cuda_check(h, cudaGetLastError(), "coef2 kernel")) != RCA_OK) return st;
+    // plane rows whose shifted slice rows (floor(shift) .. floor(shift) + 1
+    // around us * i) all lie inside [0, nzs - 1]
+    {
+        int iA = 0, iB = g.nz - 1;
+        for (int v : sfl) {
+            iA = std::max(iA, v < 0 ? (-v + g.us - 1) / g.us : 0);
+            const int room = g.nzs - 2 - v;
+            iB = std::min(iB, room >= 0 ? room / g.us : -1);
+        }
+        t->s2_iA = iA;
+        t->s2_iB = iB;
+    }
 
     t->h_txq = txq;
     t->h_rxq = rxq;
@@ -301,8 +351,8 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     }
     if ((st = plan_stage1(h, t, zt, dc)) != RCA_OK) return st;
     // Stage 2: the tallest plane-row tile that fits the same budget
-    int zp = 16;
-    while (zp > 1 && stage2_smem_bytes(t, zp) > 110 * 1024) zp /= 2;
+    int zp = S2_ZP;
+    while (zp > 1 && stage2_smem_bytes(t, zp) > 100 * 1024) zp /= 2;
     if (stage2_smem_bytes(t, zp) > 200 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-2 tile exceeds shared memory");
     plan_stage2(t, zp);
 
@@ -486,11 +536,9 @@ rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
 
 size_t stage2_smem_bytes(const rca_tables* t, int zp)
 {
-    const GeomDev& g = t->gd;
     const int span = std::max(t->s2.smax[0] - t->s2.smin[0], t->s2.smax[1] - t->s2.smin[1]) + 2;
-    const int rows = g.us * (zp - 1) + span;
-    return (size_t)g.K * rows * g.N * 8 + (size_t)g.K * g.S * rows * 8 + (size_t)g.K * g.S * zp * t->T * 8 +
-           (size_t)g.K * g.N * 8 + (size_t)g.K * zp * 8 + ((size_t)2 * g.K * g.N + (size_t)g.K * g.S) * 4;
+    const int rows = t->gd.us * (zp - 1) + span;
+    return s2_smem_bytes(t->gd.K, t->gd.S, t->gd.N, t->gd.P, t->T, rows);
 }
 
 void plan_stage2(rca_tables* t, int zp)
