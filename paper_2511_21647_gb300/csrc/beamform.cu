@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
 }
 
 template <int TM>
-__global__ void __launch_bounds__(S2_THREADS) k_stage2(GeomDev g, const float2* __restrict__ slices,
+__global__ void __launch_bounds__(S2_THREADS, 3) k_stage2(GeomDev g, const float2* __restrict__ slices,
                                                        const int* __restrict__ sfl, const float* __restrict__ sfr,
                                                        const float2* __restrict__ psi, const float2* __restrict__ ec,
                                                        const float2* __restrict__ coef, const float2* __restrict__ c2,

@@ -471,6 +471,37 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
 // ---------------------------------------------------------------------------
 #define S2_RH 8        // plane rows per warp task
 
+// Streaming stores of n (<= S2_RH) plane values at ob, ob + N, ...: the
+// dtype is chosen once for the group.
+__device__ __forceinline__ void s2_store_rows(void* __restrict__ planes, int pt, size_t ob, int N, const float2* v,
+                                              int n)
+{
+    if (pt == RCA_C32) {
+        float2* p = reinterpret_cast<float2*>(planes) + ob;
+#pragma unroll
+        for (int q = 0; q < S2_RH; ++q)
+            if (q < n) __stcs(p + (size_t)q * N, v[q]);
+    } else if (pt == RCA_C16F) {
+        unsigned* p = reinterpret_cast<unsigned*>(planes) + ob;
+#pragma unroll
+        for (int q = 0; q < S2_RH; ++q) {
+            if (q < n) {
+                __half2 hv = __float22half2_rn(v[q]);
+                __stcs(p + (size_t)q * N, *reinterpret_cast<unsigned*>(&hv));
+            }
+        }
+    } else {
+        unsigned* p = reinterpret_cast<unsigned*>(planes) + ob;
+#pragma unroll
+        for (int q = 0; q < S2_RH; ++q) {
+            if (q < n) {
+                __nv_bfloat162 bv = __float22bfloat162_rn(v[q]);
+                __stcs(p + (size_t)q * N, *reinterpret_cast<unsigned*>(&bv));
+            }
+        }
+    }
+}
+
 // transverse-slab plane rows [q0, q0 + S2_RH) of slab b at lateral pixel g0 + lane.
 // TT: tap count (0: t->T at run time, up to 16).  INTERIOR: every row of the
 // tile has carrier-separable taps.
@@ -500,6 +531,7 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
         // this lane's column in transmission kk at the window row of plane row q0
         const unsigned col = sSa + (unsigned)((((kk * rows + tb + us * q0) * 32) + lane) * 8);
         const unsigned rstep = (unsigned)(us * 32 * 8);
+        const unsigned ecb = smem_u32(sEc + kk * S2_ZP + q0);
 #pragma unroll
         for (int q = 0; q < S2_RH; ++q) {
             const int ii = q0 + q;
@@ -516,7 +548,7 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
                 const float2 p1 = f2_unpack(A1), p2 = f2_unpack(A2);
                 const uint64_t y = f2_pack(p1.x - p2.y, p1.y + p2.x);
                 uint64_t ex, ey;
-                lds_u64x2(smem_u32(sEc + kk * S2_ZP + ii), ex, ey);
+                lds_u64x2(ecb + (unsigned)(q * 16), ex, ey);
                 O1[q] = f2_fma(ex, y, O1[q]);
                 O2[q] = f2_fma(ey, y, O2[q]);
             } else if (ii < nrow) {
@@ -531,13 +563,13 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
     if (lane < gw) {
         const size_t plane_sz = (size_t)g.nz * N;
         const size_t ob = ((((size_t)f * 2 + axT) * 2 + fam) * S + b) * plane_sz + (size_t)(i0 + q0) * N + g0 + lane;
+        float2 v[S2_RH];
 #pragma unroll
         for (int q = 0; q < S2_RH; ++q) {
-            if (INTERIOR || q0 + q < nrow) {
-                const float2 p1 = f2_unpack(O1[q]), p2 = f2_unpack(O2[q]);
-                store_c_cs(planes, ob + (size_t)q * N, pt, make_float2(p1.x - p2.y, p1.y + p2.x));
-            }
+            const float2 p1 = f2_unpack(O1[q]), p2 = f2_unpack(O2[q]);
+            v[q] = make_float2(p1.x - p2.y, p1.y + p2.x);
         }
+        s2_store_rows(planes, pt, ob, N, v, INTERIOR ? S2_RH : min(S2_RH, nrow - q0));
     }
 }
 
@@ -586,9 +618,7 @@ __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int 
     }
     const size_t plane_sz = (size_t)g.nz * N;
     const size_t ob = ((((size_t)f * 2 + axL) * 2 + fam) * S + grp * SG + sb) * plane_sz + (size_t)(i0 + q0) * N + u;
-#pragma unroll
-    for (int q = 0; q < S2_RH; ++q)
-        if (INTERIOR || q0 + q < nrow) store_c_cs(planes, ob + (size_t)q * N, pt, O[q]);
+    s2_store_rows(planes, pt, ob, N, O, INTERIOR ? S2_RH : min(S2_RH, nrow - q0));
 }
 
 template <int TT>
@@ -628,9 +658,12 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
         mbar_arrive_expect_tx(&bar, cbytes * (unsigned)(K * (hi - lo)));
     }
     // window rows outside the slice (and columns past the group) read zero
-    for (int rk = warp; rk < K * rows; rk += nwarp) {
-        const int r = rlo + rk % rows;
-        if (lane >= gw || r < lo || r >= hi) sS[(size_t)rk * 32 + lane] = make_float2(0.f, 0.f);
+    if (gw < 32 || lo > rlo || hi < rlo + rows) {
+        for (int kk = 0; kk < K; ++kk)
+            for (int rr = warp; rr < rows; rr += nwarp) {
+                const int r = rlo + rr;
+                if (lane >= gw || r < lo || r >= hi) sS[((size_t)kk * rows + rr) * 32 + lane] = make_float2(0.f, 0.f);
+            }
     }
     __syncthreads();
     // one bulk copy per (k, in-slice row): the group's gw pixels
@@ -665,8 +698,9 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
     if (!cta_wait_copies(&bar, 0, status)) return false;
     // slab sums of the group's slabs: one warp per (k, window row), lanes over the pixels
     const bool pow2 = (P & (P - 1)) == 0;
-    for (int rk = warp; rk < K * rows; rk += nwarp) {
-        const int kk = rk / rows, rr = rk - kk * rows;
+    for (int kk = 0; kk < K; ++kk)
+    for (int rr = warp; rr < rows; rr += nwarp) {
+        const int rk = kk * rows + rr;
         if (pow2) {
             float2 v = sS[(size_t)rk * 32 + lane];
             for (int m = 1; m < P; m <<= 1) {
