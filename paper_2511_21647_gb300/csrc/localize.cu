@@ -8,21 +8,6 @@
 
 namespace {
 
-__device__ __forceinline__ float block_max_256(float v, float* red)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    float m = 0.f;
-    if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    __syncthreads();
-    return m;  // valid in thread 0
-}
-
 // ---------------------------------------------------------------------------
 // XDoppler: each thread owns one pixel (axis, slab, row, lateral) and walks
 // the frames with a sliding 3-frame window, so every plane is read once:
@@ -83,26 +68,38 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
 // Candidates are compacted in raster order into a fixed-capacity slot of
 // the strip; the true count is kept.
 // ---------------------------------------------------------------------------
-#define DET_SEG 8   // outputs per thread along a row / column in the separable passes
+// Separable NCC on packed pairs.  Vertical pass first, on column pairs
+// (one 64-bit shared load gives two columns of an input row): per output row
+// the box sum, the box sum of squares and the g_z-weighted sum.  The sums are
+// stored transposed into row pairs, so the horizontal pass works on two
+// output rows at once (box sums and the g_l-weighted sum along the row).
+// Thread-to-data maps keep both passes free of bank conflicts: consecutive
+// lanes take consecutive column pairs in the vertical pass and consecutive
+// row pairs (row-pair stride of N + 1 pairs) in the horizontal pass.
+#define DET_RB 4    // output rows per thread in the vertical pass (one column pair)
+#define DET_CB 4    // output columns per thread in the horizontal pass (one row pair)
 
 template <int H>
-__global__ void __launch_bounds__(256, 2) k_detect(const float* __restrict__ A, const float* __restrict__ Mf, int S,
+__global__ void __launch_bounds__(256, 3) k_detect(const float* __restrict__ A, const float* __restrict__ Mf, int S,
                                                 int nz, int N, NccConst nc, ulm_loc2d* __restrict__ cand,
                                                 int* __restrict__ cnt, float* __restrict__ ncc_out,
                                                 unsigned* __restrict__ status)
 {
     constexpr int D = 2 * H + 1;
+    constexpr int RN = DET_RS + 2;          // NCC rows: the strip and one row above and below
+    constexpr int RP = RN / 2;              // row pairs
+    static_assert(RN % DET_RB == 0 && DET_RB % 2 == 0, "row blocks must tile the NCC rows in pairs");
     extern __shared__ __align__(128) float sm[];
     const int strip = blockIdx.x, plane = blockIdx.y;
     const int nstrip = gridDim.x;
     const int t = plane / (2 * S), axis = (plane / S) % 2, b = plane % S;
     const int i0 = strip * DET_RS;
-    const int rin = DET_RS + 2 + 2 * H, rn = DET_RS + 2;
-    float* sA = sm;
-    float* H1 = sA + rin * N;
-    float* H2 = H1 + rin * N;
-    float* HG = H2 + rin * N;
-    float* sN = HG + rin * N;
+    const int rin = RN + 2 * H;
+    const int VS = (N + 1) * 2;             // floats per row pair of a vertical-sum array
+    const int NS = N + 1;                   // NCC row stride (odd: conflict-light column writes)
+    float* sA = sm;                         // [rin][N] amplitude rows i0-1-H ...
+    float* sV = sA + max((size_t)rin * N, (size_t)RN * NS);  // [3][RP][N + 1][2] vertical sums (row pairs)
+    float* sN = sA;                         // [RN][NS] NCC, over the amplitude rows once the vertical pass is done
     __shared__ int wsum[32];
     __shared__ int base_count;
     __shared__ uint64_t bar;
@@ -128,92 +125,147 @@ __global__ void __launch_bounds__(256, 2) k_detect(const float* __restrict__ A, 
         }
         if (!cta_wait_copies(&bar, 0, status)) return;
     }
-    // horizontal pass: lanes over consecutive columns (conflict-free), each
-    // output sums its own D-wide window
-    for (int w = threadIdx.x; w < rin * N; w += blockDim.x) {
-        const int rr = w / N, c = w - rr * N;
-        const float* row = sA + rr * N;
-        float s1 = 0.f, s2 = 0.f, sg = 0.f;
-        if (c >= H && c < N - H) {
+    // ---- vertical pass: thread = (column pair, DET_RB output rows)
+    {
+        uint64_t gz[D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) {
-                const float x = row[c - H + q];
-                s1 += x;
-                s2 = fmaf(x, x, s2);
-                sg = fmaf(nc.gl[q], x, sg);
-            }
-        }
-        H1[w] = s1;
-        H2[w] = s2;
-        HG[w] = sg;
-    }
-    __syncthreads();
-    // vertical pass + NCC: each thread owns DET_SEG consecutive output rows of one column
-    const float flat = nc.flat_coef * Mt * Mt;
-    const float inv_d2 = 1.0f / (float)(D * D);
-    const int nrs = (rn + DET_SEG - 1) / DET_SEG;
-    for (int w = threadIdx.x; w < nrs * N; w += blockDim.x) {
-        const int rs = w / N, l = w - rs * N;
-        const int ro0 = rs * DET_SEG;
-        float h1[DET_SEG + 2 * H], h2[DET_SEG + 2 * H], hg[DET_SEG + 2 * H];
+        for (int q = 0; q < D; ++q) gz[q] = f2_pack(nc.gz[q], nc.gz[q]);
+        const int NP = N / 2;
+        const unsigned sAa = smem_u32(sA), sVa = smem_u32(sV);
+        for (int task = threadIdx.x; task < NP * (RN / DET_RB); task += blockDim.x) {
+            const int cp = task % NP, rb = task / NP;
+            const int ro0 = rb * DET_RB;
+            uint64_t v1[DET_RB], v2[DET_RB], vg[DET_RB];
 #pragma unroll
-        for (int q = 0; q < DET_SEG + 2 * H; ++q) {
-            const int rr = min(ro0 + q, rin - 1);
-            h1[q] = H1[rr * N + l];
-            h2[q] = H2[rr * N + l];
-            hg[q] = HG[rr * N + l];
-        }
+            for (int j = 0; j < DET_RB; ++j) v1[j] = v2[j] = vg[j] = 0ull;
+            const unsigned src = sAa + (unsigned)((ro0 * N + 2 * cp) * 4);
 #pragma unroll
-        for (int o = 0; o < DET_SEG; ++o) {
-            const int ro = ro0 + o, i = i0 - 1 + ro;
-            if (ro < rn) {
-                float v = 0.f;
-                if (i >= H && i < nz - H && l >= H && l < N - H && Mt > 0.f) {
-                    float s1 = 0.f, s2 = 0.f, sg = 0.f;
+            for (int m = 0; m < DET_RB + 2 * H; ++m) {
+                const uint64_t x = lds_u64(src + (unsigned)(m * N * 4));
+                const uint64_t x2 = f2_mul(x, x);
 #pragma unroll
-                    for (int q = 0; q < D; ++q) {
-                        s1 += h1[o + q];
-                        s2 += h2[o + q];
-                        sg = fmaf(nc.gz[q], hg[o + q], sg);
+                for (int j = 0; j < DET_RB; ++j) {
+                    const int q = m - j;
+                    if (q >= 0 && q < D) {
+                        v1[j] = f2_add(v1[j], x);
+                        v2[j] = f2_add(v2[j], x2);
+                        vg[j] = f2_fma(gz[q], x, vg[j]);
                     }
-                    const float ssA = s2 - s1 * s1 * inv_d2;
-                    if (ssA > flat) v = (sg - nc.muG * s1) * nc.inv_ssG_sqrt * rsqrtf(ssA);
                 }
-                sN[ro * N + l] = v;
-                if (ncc_out && ro >= 1 && ro <= DET_RS && i < nz) ncc_out[((size_t)plane * nz + i) * N + l] = v;
+            }
+            // transpose 2 x 2 blocks into row pairs: [arr][rp][column][row parity]
+#pragma unroll
+            for (int j = 0; j < DET_RB; j += 2) {
+                const int rp = (ro0 + j) / 2;
+                const uint64_t* arrs[3] = {v1, v2, vg};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float2 r0 = f2_unpack(arrs[a][j]), r1 = f2_unpack(arrs[a][j + 1]);
+                    // row-pair stride 2 (N + 1) floats keeps the horizontal pass conflict-free
+                    // but aligns pairs to 8 bytes only: two 64-bit stores
+                    const unsigned dst = sVa + (unsigned)(((a * RP + rp) * VS + 4 * cp) * 4);
+                    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst), "f"(r0.x), "f"(r1.x) : "memory");
+                    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst + 8u), "f"(r0.y), "f"(r1.y) : "memory");
+                }
             }
         }
     }
     __syncthreads();
-    // peaks: each thread tests a contiguous run of pixels (raster order), one
-    // block-wide exclusive scan of the per-thread counts places them
+    // ---- horizontal pass + NCC: thread = (row pair, DET_CB output columns);
+    // the amplitude rows are no longer read, so the NCC rows take their place
+    {
+        const float flat = nc.flat_coef * Mt * Mt;
+        const float inv_d2 = 1.0f / (float)(D * D);
+        const int ncb = (N + DET_CB - 1) / DET_CB;
+        uint64_t gl[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) gl[q] = f2_pack(nc.gl[q], nc.gl[q]);
+        const uint64_t nid2 = f2_pack(-inv_d2, -inv_d2), nmu = f2_pack(-nc.muG, -nc.muG);
+        const unsigned sVa = smem_u32(sV);
+        for (int task = threadIdx.x; task < RP * ncb; task += blockDim.x) {
+            const int rp = task % RP, cb = task / RP;
+            const int c0 = cb * DET_CB;
+            uint64_t s1[DET_CB], s2[DET_CB], sg[DET_CB];
+#pragma unroll
+            for (int j = 0; j < DET_CB; ++j) s1[j] = s2[j] = sg[j] = 0ull;
+#pragma unroll
+            for (int m = 0; m < DET_CB + 2 * H; ++m) {
+                const int c = min(max(c0 - H + m, 0), N - 1);   // border outputs are zeroed below
+                const unsigned at = sVa + (unsigned)((rp * VS + 2 * c) * 4);
+                const uint64_t a1 = lds_u64(at), a2 = lds_u64(at + (unsigned)(RP * VS * 4)),
+                               ag = lds_u64(at + (unsigned)(2 * RP * VS * 4));
+#pragma unroll
+                for (int j = 0; j < DET_CB; ++j) {
+                    const int q = m - j;
+                    if (q >= 0 && q < D) {
+                        s1[j] = f2_add(s1[j], a1);
+                        s2[j] = f2_add(s2[j], a2);
+                        sg[j] = f2_fma(gl[q], ag, sg[j]);
+                    }
+                }
+            }
+            const int ia = i0 - 1 + 2 * rp;    // plane row of the pair's first row
+#pragma unroll
+            for (int j = 0; j < DET_CB; ++j) {
+                const int c = c0 + j;
+                if (c >= N) continue;
+                // ssA = s2 - s1^2 / d^2, numerator = sg - mu_G s1 (both rows of the pair)
+                const float2 ss = f2_unpack(f2_fma(f2_mul(s1[j], s1[j]), nid2, s2[j]));
+                const float2 nu = f2_unpack(f2_fma(nmu, s1[j], sg[j]));
+                const bool colok = c >= H && c < N - H && Mt > 0.f;
+                float v[2] = {0.f, 0.f};
+                if (colok && ia >= H && ia < nz - H && ss.x > flat) v[0] = nu.x * nc.inv_ssG_sqrt * rsqrtf(ss.x);
+                if (colok && ia + 1 >= H && ia + 1 < nz - H && ss.y > flat)
+                    v[1] = nu.y * nc.inv_ssG_sqrt * rsqrtf(ss.y);
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int ro = 2 * rp + pr;
+                    sN[ro * NS + c] = v[pr];
+                    if (ncc_out && ro >= 1 && ro <= DET_RS && ia + pr < nz)
+                        ncc_out[((size_t)plane * nz + ia + pr) * N + c] = v[pr];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---- peaks: each thread tests a contiguous run of pixels (raster order) once,
+    // one block-wide exclusive scan of the per-thread counts places them
     const float athr = nc.alpha * Mt;
     ulm_loc2d* slot = cand + ((size_t)plane * nstrip + strip) * CAND_CAP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npx = DET_RS * N;
-    const int per = (npx + blockDim.x - 1) / blockDim.x;
+    const int per = (npx + blockDim.x - 1) / blockDim.x;   // <= 32 for N <= 256
     const int p0 = threadIdx.x * per, p1 = min(npx, p0 + per);
-    auto is_peak = [&](int p, float& c) {
-        const int ro = 1 + p / N, l = p % N;
-        const int i = i0 - 1 + ro;
-        if (i < 1 || i >= nz - 1 || l < 1 || l >= N - 1) return false;
-        c = sN[ro * N + l];
-        if (!(c >= nc.ncc_min) || !(sA[(ro + H) * N + l] >= athr)) return false;
-#pragma unroll
-        for (int a = -1; a <= 1; ++a)
-#pragma unroll
-            for (int bb = -1; bb <= 1; ++bb) {
-                if (a == 0 && bb == 0) continue;
-                const float q = sN[(ro + a) * N + l + bb];
-                const bool earlier = (a < 0) || (a == 0 && bb < 0);
-                if (earlier ? !(c > q) : !(c >= q)) return false;
-            }
-        return true;
-    };
+    unsigned mask = 0u;
     int mine = 0;
-    for (int p = p0; p < p1; ++p) {
-        float c;
-        mine += is_peak(p, c) ? 1 : 0;
+    {
+        int ro = 1 + p0 / N, l = p0 - (ro - 1) * N;
+        for (int p = p0; p < p1; ++p) {
+            const int i = i0 - 1 + ro;
+            if (i >= 1 && i < nz - 1 && l >= 1 && l < N - 1) {
+                const float c = sN[ro * NS + l];
+                if (c >= nc.ncc_min && __ldg(Ap + (size_t)i * N + l) >= athr) {
+                    bool pk = true;
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+                        for (int bb = -1; bb <= 1; ++bb) {
+                            if (a == 0 && bb == 0) continue;
+                            const float q = sN[(ro + a) * NS + l + bb];
+                            const bool earlier = (a < 0) || (a == 0 && bb < 0);
+                            pk = pk && (earlier ? (c > q) : (c >= q));
+                        }
+                    if (pk) {
+                        mask |= 1u << (p - p0);
+                        ++mine;
+                    }
+                }
+            }
+            if (++l == N) {
+                l = 0;
+                ++ro;
+            }
+        }
     }
     int x = mine;
     for (int o = 1; o < 32; o <<= 1) {
@@ -224,33 +276,33 @@ __global__ void __launch_bounds__(256, 2) k_detect(const float* __restrict__ A, 
     __syncthreads();
     int before = x - mine;
     for (int w = 0; w < warp; ++w) before += wsum[w];
-    if (mine) {
-        for (int p = p0; p < p1; ++p) {
-            float c;
-            if (!is_peak(p, c)) continue;
-            if (before < CAND_CAP) {
-                const int ro = 1 + p / N, l = p % N, i = i0 - 1 + ro;
-                auto para = [](float fm, float f0, float fp) {
-                    const float den = fm - 2.f * f0 + fp;
-                    if (den >= 0.f) return 0.f;
-                    const float dl = (fm - fp) / (2.f * den);
-                    return fminf(0.5f, fmaxf(-0.5f, dl));
-                };
-                ulm_loc2d e;
-                e.frame = t;
-                e.axis = axis;
-                e.slab = b;
-                e.iz = i;
-                e.ilat = l;
-                e.z = (float)i + para(sN[(ro - 1) * N + l], c, sN[(ro + 1) * N + l]);
-                e.lat = (float)l + para(sN[ro * N + l - 1], c, sN[ro * N + l + 1]);
-                e.ncc = c;
-                e.amp = sA[(ro + H) * N + l];
-                e.reserved = 0;
-                slot[before] = e;
-            }
-            ++before;
+    while (mask) {
+        const int bit = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (before < CAND_CAP) {
+            const int p = p0 + bit;
+            const int ro = 1 + p / N, l = p - (ro - 1) * N, i = i0 - 1 + ro;
+            const float c = sN[ro * NS + l];
+            auto para = [](float fm, float f0, float fp) {
+                const float den = fm - 2.f * f0 + fp;
+                if (den >= 0.f) return 0.f;
+                const float dl = (fm - fp) / (2.f * den);
+                return fminf(0.5f, fmaxf(-0.5f, dl));
+            };
+            ulm_loc2d e;
+            e.frame = t;
+            e.axis = axis;
+            e.slab = b;
+            e.iz = i;
+            e.ilat = l;
+            e.z = (float)i + para(sN[(ro - 1) * NS + l], c, sN[(ro + 1) * NS + l]);
+            e.lat = (float)l + para(sN[ro * NS + l - 1], c, sN[ro * NS + l + 1]);
+            e.ncc = c;
+            e.amp = __ldg(Ap + (size_t)i * N + l);
+            e.reserved = 0;
+            slot[before] = e;
         }
+        ++before;
     }
     if (threadIdx.x == blockDim.x - 1) base_count = before;
     __syncthreads();
@@ -678,7 +730,9 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     int* off = (int*)ws_get(h, WS_SCAN, (size_t)(nslots + 1) * sizeof(int), &st);
     if (!off) return st;
     const int rin = DET_RS + 2 + 2 * hh;
-    size_t smem = ((size_t)4 * rin * g.N + (size_t)(DET_RS + 2) * g.N) * sizeof(float);
+    // amplitude rows (later the NCC rows, stride N + 1) + three vertical-sum arrays of row pairs
+    size_t smem = (std::max((size_t)rin * g.N, (size_t)(DET_RS + 2) * (g.N + 1)) +
+                   (size_t)3 * ((DET_RS + 2) / 2) * (g.N + 1) * 2) * sizeof(float);
     dim3 grid(nstrip, nplanes);
     cudaError_t e = cudaSuccess;
     switch (hh) {

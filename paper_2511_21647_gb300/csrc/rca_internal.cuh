@@ -177,7 +177,7 @@ void plan_stage2(rca_tables* t, int zp);
 // ---------------------------------------------------------------------------
 #define RCA_MAX_NCC_D 15
 #define CAND_CAP 64       // 2D candidates per (plane, row strip)
-#define DET_RS 32         // rows per detect strip
+#define DET_RS 30         // rows per detect strip (the NCC rows, one above and below, pair up)
 
 struct NccConst {
     int d, h;
