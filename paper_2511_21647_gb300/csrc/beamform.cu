@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(256) k_mean(const void* __restrict__ rf, int r
     mean_body(blockIdx.x, rf, rf_t, scale, F, ns, ncol, mean);
 }
 
-__global__ void __launch_bounds__(256) k_demod(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
+__global__ void __launch_bounds__(256, 4) k_demod(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
                                                const float* __restrict__ mean, const float2* __restrict__ mix, Fir fir,
                                                int nt, int E, int ns, void* __restrict__ iq, int iq_t)
 {

@@ -103,7 +103,12 @@ __device__ __forceinline__ void mean_body(int bx, const void* __restrict__ rf, i
 #define DM_PITCH (DM_NT + 31)  // odd float2 pitch: conflict-free column reads
 
 // CTA = (128 samples, 32 elements, one frame-transmission).  Reads RF rows
-// [e][n] coalesced along n, writes IQ [n][e] coalesced along e.
+// [e][n] coalesced along n (warps over elements, lanes over samples), writes
+// IQ [n][e] coalesced along e (lanes over elements).  Each thread filters
+// DM_OB consecutive samples of one element from a register window, so every
+// staged sample is read DM_OB + 30 times per DM_OB outputs instead of 17 times
+// per output.
+#define DM_OB 8             // consecutive outputs per thread
 __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __restrict__ xs,
                                            const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
                                            const float* __restrict__ mean, const float2* __restrict__ mix,
@@ -114,34 +119,52 @@ __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __res
     const int fk = bz;
     const int k = fk % nt;
     const size_t chan0 = (size_t)fk * E;
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < DM_NE * (DM_NT + 30); idx += blockDim.x) {
-        int el = idx / (DM_NT + 30), s = idx - el * (DM_NT + 30);
-        int n = n0 - 15 + s, e = e0 + el;
-        float2 v = make_float2(0.f, 0.f);
-        if (n >= 0 && n < ns && e < E) {
-            float x = rf_value(rf, rf_t, (chan0 + e) * ns + n);
-            if (rf_t == RCA_I16) x *= scale[k * E + e];
-            if (mean) x -= mean[((size_t)k * E + e) * ns + n];
-            float2 m = mix[n];
-            v = make_float2(x * m.x, x * m.y);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // stage (rf - mean) * exp(-j 2 pi fc t_n) for samples n0-15 .. n0+DM_NT+14
+    for (int el = warp; el < DM_NE; el += nwarp) {
+        const int e = e0 + el;
+        const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
+        const float* mrow = mean ? mean + ((size_t)k * E + e) * ns : nullptr;
+        for (int s = lane; s < DM_NT + 30; s += 32) {
+            const int n = n0 - 15 + s;
+            float2 v = make_float2(0.f, 0.f);
+            if (n >= 0 && n < ns && e < E) {
+                float x = rf_value(rf, rf_t, (chan0 + e) * ns + n) * sc;
+                if (mrow) x -= mrow[n];
+                const float2 m = mix[n];
+                v = make_float2(x * m.x, x * m.y);
+            }
+            xs[el * DM_PITCH + s] = v;
         }
-        xs[el * DM_PITCH + s] = v;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < DM_NE * DM_NT; idx += blockDim.x) {
-        int el = idx % DM_NE, s = idx / DM_NE;
-        int n = n0 + s, e = e0 + el;
-        if (n >= ns || e >= E) continue;
-        const float2* x = xs + el * DM_PITCH + s + 15;
-        float re = fir.h[15] * x[0].x, im = fir.h[15] * x[0].y;
+    // half-band low-pass x2: out[n] = 2 (h15 x[n] + sum_{odd m} h[15+m] (x[n-m] + x[n+m])).
+    // Each staged sample is read once and added into the DM_OB outputs it feeds.
+    uint64_t hp[16];                                  // 2 h[15 + d], d = 0 .. 15 (even d > 0 are zero)
 #pragma unroll
-        for (int m = 1; m <= 15; m += 2) {  // even taps are zero (half-band)
-            float hm = fir.h[15 + m];
-            re = fmaf(hm, x[-m].x + x[m].x, re);
-            im = fmaf(hm, x[-m].y + x[m].y, im);
+    for (int d = 0; d < 16; ++d) hp[d] = f2_pack(2.f * fir.h[15 + d], 2.f * fir.h[15 + d]);
+    const int e = e0 + lane;
+    const unsigned row = smem_u32(xs + lane * DM_PITCH);
+    for (int ob = warp; ob < DM_NT / DM_OB; ob += nwarp) {
+        const int s0 = ob * DM_OB;                    // output o sits at window sample o + 15
+        uint64_t acc[DM_OB];
+#pragma unroll
+        for (int o = 0; o < DM_OB; ++o) acc[o] = 0ull;
+#pragma unroll
+        for (int j = 0; j < DM_OB + 30; ++j) {
+            const uint64_t w = lds_u64(row + (unsigned)((s0 + j) * 8));
+#pragma unroll
+            for (int o = 0; o < DM_OB; ++o) {
+                const int d = j - o - 15 < 0 ? o + 15 - j : j - o - 15;
+                if (d <= 15 && (d == 0 || (d & 1))) acc[o] = f2_fma(hp[d], w, acc[o]);
+            }
         }
-        store_c(iq, ((size_t)fk * ns + n) * E + e, iq_t, make_float2(2.f * re, 2.f * im));
+        if (e >= E) continue;
+#pragma unroll
+        for (int o = 0; o < DM_OB; ++o) {
+            const int n = n0 + s0 + o;
+            if (n < ns) store_c(iq, ((size_t)fk * ns + n) * E + e, iq_t, f2_unpack(acc[o]));
+        }
     }
 }
 
