@@ -614,7 +614,10 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
     int counters = 0;
     size_t smem = (size_t)32 * 159 * 8;  // demodulation tile (DM_NE x DM_PITCH float2)
     int maxr = 1, tmax = 1, tmin_all = 1 << 30;
-    std::vector<int4> segA, segRest;
+    // queue order is stage-major (all means, all demodulations, all Stage 1,
+    // all Stage 2): a unit's inputs are then normally complete long before it
+    // is taken, and every unit still depends only on units earlier in the queue
+    std::vector<int4> segA, segB, segC, segD;
     int unit = 0;
     b->ens.resize(n);
     for (int e = 0; e < n && st == RCA_OK; ++e) {
@@ -679,9 +682,9 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.cC0 = counters + 1 + F * nt;
         counters += 1 + F * nt + F;
         segA.push_back(make_int4(BS_MEAN, e, 0, E.nA));
-        segRest.push_back(make_int4(BS_DEMOD, e, 0, E.nB));
-        segRest.push_back(make_int4(BS_STAGE1, e, 0, E.nC));
-        segRest.push_back(make_int4(BS_STAGE2, e, 0, E.nD));
+        segB.push_back(make_int4(BS_DEMOD, e, 0, E.nB));
+        segC.push_back(make_int4(BS_STAGE1, e, 0, E.nC));
+        segD.push_back(make_int4(BS_STAGE2, e, 0, E.nD));
         int LW = (g.N + 31) / 32, RG = std::max(1, 8 / LW);
         maxr = std::max(maxr, (E.zt + RG - 1) / RG);
         tmax = std::max(tmax, t->T);
@@ -703,14 +706,11 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         delete b;
         return set_error(h, RCA_ERR_UNSUPPORTED, "batch tile shapes exceed the persistent kernel limits");
     }
-    for (auto& sg : segA) {
-        b->segs.push_back(make_int4(sg.x, sg.y, unit, sg.w));
-        unit += sg.w;
-    }
-    for (auto& sg : segRest) {
-        b->segs.push_back(make_int4(sg.x, sg.y, unit, sg.w));
-        unit += sg.w;
-    }
+    for (const auto* seg : {&segA, &segB, &segC, &segD})
+        for (auto& sg : *seg) {
+            b->segs.push_back(make_int4(sg.x, sg.y, unit, sg.w));
+            unit += sg.w;
+        }
     b->total = unit;
     b->n_counters = counters;
     b->maxr = maxr;

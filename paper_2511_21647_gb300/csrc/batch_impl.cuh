@@ -8,8 +8,8 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Persistent batched beamforming.  Every CTA repeatedly takes the next work
-// unit from a device queue (mean units of all ensembles first, then per
-// ensemble demodulation, Stage 1 and Stage 2 units), waits -- bounded -- until
+// unit from a device queue (stage-major: the mean units of all ensembles,
+// then all demodulation, all Stage 1 and all Stage 2 units), waits -- bounded -- until
 // the unit's inputs are complete (per-ensemble counters), runs the same body
 // as the standalone kernel, and publishes its completion.  Units only wait
 // on units earlier in the queue, which were taken by CTAs already running,
@@ -29,7 +29,7 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar)
 }
 
 template <typename TS, int MAXR, int TM>
-__global__ void __launch_bounds__(256, 2) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
+__global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
                                                  int nseg, int total, int* __restrict__ cnt, int n_counters,
                                                  long long wait_limit, Fir fir, int rf_t, int iq_t, int pt,
                                                  unsigned* __restrict__ status)

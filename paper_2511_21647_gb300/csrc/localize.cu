@@ -12,16 +12,19 @@ namespace {
 // XDoppler: each thread owns one pixel (axis, slab, row, lateral) and walks
 // the frames with a sliding 3-frame window, so every plane is read once:
 //   Q_t = P_RC,t conj(P_CR,t),  A_t = sqrt(|Q_{t-1} + Q_t + Q_{t+1}|).
-// The planes of frame t+2 are loaded while frame t is finished.  M_t = max
-// A_t: warp max, shared-memory atomicMax per frame, one global atomicMax per
-// block and frame at the end (non-negative floats order like their bits).
+// The planes of frame t+2 are loaded while frame t is finished.  Frames are
+// split into chunks across blockIdx.y (each chunk re-reads the frame before
+// it) when the planes alone would give too few blocks.  M_t = max A_t: warp
+// max, shared-memory atomicMax per frame, one global atomicMax per block and
+// frame at the end (non-negative floats order like their bits).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes, int pt, int F, int S,
-                                                 size_t plane_sz, int enh, float* __restrict__ A,
+                                                 size_t plane_sz, int enh, int tf, float* __restrict__ A,
                                                  unsigned* __restrict__ M)
 {
-    extern __shared__ unsigned mx[];  // [F]
-    for (int t = threadIdx.x; t < F; t += blockDim.x) mx[t] = 0u;
+    extern __shared__ unsigned mx[];  // [tf] maxima of this chunk's frames
+    const int t0 = blockIdx.y * tf, t1 = min(F, t0 + tf);
+    for (int t = threadIdx.x; t < t1 - t0; t += blockDim.x) mx[t] = 0u;
     __syncthreads();
     const size_t per_axis = (size_t)S * plane_sz;
     const size_t npx = 2 * per_axis;
@@ -34,10 +37,11 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
         return (act && t < F) ? load_c(planes, at(t, fam), pt) : make_float2(0.f, 0.f);
     };
     auto xq = [](float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); };
-    float2 r0 = ld(0, 0), c0 = ld(0, 1), r1 = ld(1, 0), c1 = ld(1, 1);
-    float2 r2 = ld(2, 0), c2 = ld(2, 1);
+    float2 r0 = ld(t0, 0), c0 = ld(t0, 1), r1 = ld(t0 + 1, 0), c1 = ld(t0 + 1, 1);
+    float2 r2 = ld(t0 + 2, 0), c2 = ld(t0 + 2, 1);
     float2 qm = make_float2(0.f, 0.f);
-    for (int t = 0; t < F; ++t) {
+    if (t0 > 0 && enh == ULM_ENH_XDOPPLER) qm = xq(ld(t0 - 1, 0), ld(t0 - 1, 1));
+    for (int t = t0; t < t1; ++t) {
         const float2 r3 = ld(t + 3, 0), c3 = ld(t + 3, 1);  // prefetch
         float a;
         if (enh == ULM_ENH_XDOPPLER) {
@@ -52,11 +56,11 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
         if (act) __stcs(A + (size_t)t * npx + p, a);
         float m = act ? a : 0.f;
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) atomicMax(mx + t, __float_as_uint(m));
+        if (lane == 0) atomicMax(mx + (t - t0), __float_as_uint(m));
         r0 = r1; c0 = c1; r1 = r2; c1 = c2; r2 = r3; c2 = c3;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < F; t += blockDim.x) atomicMax(M + t, mx[t]);
+    for (int t = threadIdx.x; t < t1 - t0; t += blockDim.x) atomicMax(M + t0 + t, mx[t]);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,11 +687,20 @@ rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes
     const size_t npx = 2 * (size_t)g.S * plane_sz;
     if (F > 48 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 49152 frames in one call");
     cudaMemsetAsync(M, 0, sizeof(float) * F, h->stream);
-    const size_t smem = (size_t)F * sizeof(unsigned);
+    // enough blocks to fill the GPU: split the frames when the planes are small
+    const unsigned pblocks = (unsigned)((npx + 255) / 256);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int want = std::max(1, (int)((4u * (unsigned)sms + pblocks - 1) / pblocks));
+    const int nchunk = std::min(want, std::max(1, F / 16));
+    const int tf = (F + nchunk - 1) / nchunk;
+    const size_t smem = (size_t)tf * sizeof(unsigned);
     cudaError_t e = cudaFuncSetAttribute(k_enhance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "enhance smem attribute");
-    k_enhance<<<(unsigned)((npx + 255) / 256), 256, smem, h->stream>>>(planes, (int)pt, F, g.S, plane_sz, enh, A,
-                                                                      reinterpret_cast<unsigned*>(M));
+    dim3 grid(pblocks, (unsigned)((F + tf - 1) / tf));
+    k_enhance<<<grid, 256, smem, h->stream>>>(planes, (int)pt, F, g.S, plane_sz, enh, tf, A,
+                                              reinterpret_cast<unsigned*>(M));
     return cuda_check(h, cudaGetLastError(), "enhance kernel");
 }
 
