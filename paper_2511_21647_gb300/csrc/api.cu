@@ -555,12 +555,20 @@ extern "C" rca_status ulm_detect_map(rca_handle* h, const rca_tables* t, const f
 // ---------------------------------------------------------------------------
 static void batch_free(rca_batch* b)
 {
-    if (b->lh) {
-        for (auto& w : b->lh->ws)
+    for (rca_handle* lh : b->lhs) {
+        for (auto& w : lh->ws)
             if (w.p) cudaFree(w.p);
-        delete b->lh;  // its status word belongs to the caller's handle
-        b->lh = nullptr;
+        delete lh;  // its status word belongs to the caller's handle
     }
+    b->lhs.clear();
+    for (cudaStream_t st : b->lstreams)
+        if (st) cudaStreamDestroy(st);
+    b->lstreams.clear();
+    for (cudaEvent_t ev : b->ldone)
+        if (ev) cudaEventDestroy(ev);
+    b->ldone.clear();
+    if (b->bf_done) cudaEventDestroy(b->bf_done);
+    b->bf_done = nullptr;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (void* p : b->owned)
@@ -614,10 +622,13 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
     int counters = 0;
     size_t smem = (size_t)32 * 159 * 8;  // demodulation tile (DM_NE x DM_PITCH float2)
     int maxr = 1, tmax = 1, tmin_all = 1 << 30;
-    // queue order is stage-major (all means, all demodulations, all Stage 1,
-    // all Stage 2): a unit's inputs are then normally complete long before it
-    // is taken, and every unit still depends only on units earlier in the queue
-    std::vector<int4> segA, segB, segC, segD;
+    // Queue order: the mean units of every ensemble, then ensemble by ensemble
+    // a software pipeline over chunks of BQ_CHUNK frames -- demodulation of
+    // chunk c, Stage 1 of chunk c - BQ_LAG1, Stage 2 of chunk c - BQ_LAG2 --
+    // so a unit's inputs are normally complete when it is taken and the IQ and
+    // slices in flight stay small enough to be passed on through L2.  Every
+    // unit depends only on units earlier in the queue.
+    std::vector<int4> segA;
     int unit = 0;
     b->ens.resize(n);
     for (int e = 0; e < n && st == RCA_OK; ++e) {
@@ -682,9 +693,7 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.cC0 = counters + 1 + F * nt;
         counters += 1 + F * nt + F;
         segA.push_back(make_int4(BS_MEAN, e, 0, E.nA));
-        segB.push_back(make_int4(BS_DEMOD, e, 0, E.nB));
-        segC.push_back(make_int4(BS_STAGE1, e, 0, E.nC));
-        segD.push_back(make_int4(BS_STAGE2, e, 0, E.nD));
+
         int LW = (g.N + 31) / 32, RG = std::max(1, 8 / LW);
         maxr = std::max(maxr, (E.zt + RG - 1) / RG);
         tmax = std::max(tmax, t->T);
@@ -706,11 +715,39 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         delete b;
         return set_error(h, RCA_ERR_UNSUPPORTED, "batch tile shapes exceed the persistent kernel limits");
     }
-    for (const auto* seg : {&segA, &segB, &segC, &segD})
-        for (auto& sg : *seg) {
-            b->segs.push_back(make_int4(sg.x, sg.y, unit, sg.w));
-            unit += sg.w;
+    // segment = {stage | ensemble << 4, first unit, units, first stage-local unit}
+    auto push = [&](int stage, int e, int loc0, int count) {
+        if (count <= 0) return;
+        b->segs.push_back(make_int4(stage | (e << 4), unit, count, loc0));
+        unit += count;
+    };
+    for (auto& sg : segA) push(sg.x, sg.y, 0, sg.w);
+    constexpr int BQ_CHUNK = 16, BQ_LAG1 = 2, BQ_LAG2 = 4;
+    for (int e = 0; e < n; ++e) {
+        const BatchEns& E = b->ens[e];
+        const int F = E.F, nt = 2 * E.g.K, nc = (F + BQ_CHUNK - 1) / BQ_CHUNK;
+        const int perB = E.nB / F, perC = E.nC / F, perD = E.nD / F;   // units per frame
+        for (int c = 0; c < nc + BQ_LAG2; ++c) {
+            auto frames = [&](int cc, int* f0, int* f1) {
+                *f0 = cc * BQ_CHUNK;
+                *f1 = std::min(F, *f0 + BQ_CHUNK);
+            };
+            int f0, f1;
+            if (c < nc) {
+                frames(c, &f0, &f1);
+                push(BS_DEMOD, e, f0 * perB, (f1 - f0) * perB);
+            }
+            if (c - BQ_LAG1 >= 0 && c - BQ_LAG1 < nc) {
+                frames(c - BQ_LAG1, &f0, &f1);
+                push(BS_STAGE1, e, f0 * perC, (f1 - f0) * perC);
+            }
+            if (c - BQ_LAG2 >= 0 && c - BQ_LAG2 < nc) {
+                frames(c - BQ_LAG2, &f0, &f1);
+                push(BS_STAGE2, e, f0 * perD, (f1 - f0) * perD);
+            }
         }
+        (void)nt;
+    }
     b->total = unit;
     b->n_counters = counters;
     b->maxr = maxr;
@@ -729,14 +766,28 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
     if (prm) {
         b->localise = true;
         b->prm = *prm;
-        b->lh = new (std::nothrow) rca_handle();
-        if (!b->lh) {
+        bool okh = cudaEventCreateWithFlags(&b->bf_done, cudaEventDisableTiming) == cudaSuccess;
+        for (int e = 0; e < n && okh; ++e) {
+            rca_handle* lh = new (std::nothrow) rca_handle();
+            if (!lh) {
+                okh = false;
+                break;
+            }
+            lh->device = h->device;
+            lh->d_status = h->d_status;
+            b->lhs.push_back(lh);
+            cudaStream_t ls = nullptr;
+            cudaEvent_t ev = nullptr;
+            okh = cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) == cudaSuccess;
+            b->lstreams.push_back(ls);
+            okh = okh && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+            b->ldone.push_back(ev);
+        }
+        if (!okh) {
             batch_free(b);
             delete b;
-            return set_error(h, RCA_ERR_CUDA, "out of host memory");
+            return set_error(h, RCA_ERR_CUDA, "localisation streams / handles for the batch");
         }
-        b->lh->device = h->device;
-        b->lh->d_status = h->d_status;
         for (int e = 0; e < n; ++e) {
             b->tabs.push_back(items[e].tables);
             b->out2d.push_back(items[e].out2d);
@@ -755,20 +806,27 @@ static rca_status batch_enqueue(rca_batch* b)
 {
     rca_status st = launch_batch(b->h, b);
     if (st != RCA_OK || !b->localise) return st;
-    rca_handle* h = b->lh;
-    h->stream = b->h->stream;
-    for (int e = 0; e < b->n; ++e) {
+    // fork: every ensemble's localisation on its own stream after the beamforming
+    cudaStream_t main = b->h->stream;
+    if ((st = cuda_check(b->h, cudaEventRecord(b->bf_done, main), "batch fork")) != RCA_OK) return st;
+    for (int e = 0; e < b->n && st == RCA_OK; ++e) {
+        rca_handle* h = b->lhs[e];
+        h->stream = b->lstreams[e];
         const rca_tables* t = b->tabs[e];
         const int F = b->ens[e].F;
-        if ((st = launch_enhance(h, t, b->ens[e].planes, b->pl_t, F, b->prm.enh, b->A[e], b->M[e])) != RCA_OK) return st;
-        if ((st = launch_detect2d(h, t, b->A[e], b->M[e], F, &b->prm, b->out2d[e], b->cap2d[e], b->n2d[e], nullptr,
-                                  nullptr)) != RCA_OK)
-            return st;
-        if ((st = launch_pair3d(h, t, b->out2d[e], b->n2d[e], b->cap2d[e], F, b->out3d[e], b->cap3d[e], b->n3d[e])) != RCA_OK)
-            return st;
+        st = cuda_check(b->h, cudaStreamWaitEvent(h->stream, b->bf_done, 0), "batch fork wait");
+        if (st == RCA_OK) st = launch_enhance(h, t, b->ens[e].planes, b->pl_t, F, b->prm.enh, b->A[e], b->M[e]);
+        if (st == RCA_OK)
+            st = launch_detect2d(h, t, b->A[e], b->M[e], F, &b->prm, b->out2d[e], b->cap2d[e], b->n2d[e], nullptr,
+                                 nullptr);
+        if (st == RCA_OK)
+            st = launch_pair3d(h, t, b->out2d[e], b->n2d[e], b->cap2d[e], F, b->out3d[e], b->cap3d[e], b->n3d[e]);
+        if (!h->last_error.empty()) b->h->last_error = h->last_error;
+        // join (also after a failed launch, so a capture stays well formed)
+        cudaEventRecord(b->ldone[e], h->stream);
+        cudaStreamWaitEvent(main, b->ldone[e], 0);
     }
-    if (!h->last_error.empty()) b->h->last_error = h->last_error;
-    return RCA_OK;
+    return st;
 }
 
 extern "C" rca_status rca_batch_run(rca_batch* b, int use_graph)

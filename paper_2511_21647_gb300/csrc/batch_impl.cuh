@@ -36,19 +36,41 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bars[2];
-    __shared__ int s_unit, s_ok;
+    __shared__ int s_unit, s_ok, s_sg, s_cur;
+    __shared__ int4 s_seg;
+    // the current ensemble's descriptor, copied once per ensemble change
+    __shared__ __align__(16) BatchEns sE;
     int* next = cnt + n_counters;
     int* abort_flag = cnt + n_counters + 1;
+    if (threadIdx.x == 0) {
+        s_sg = 0;
+        s_cur = -1;
+    }
     for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(next, 1);
+        if (threadIdx.x == 0) {
+            const int u = atomicAdd(next, 1);
+            s_unit = u;
+            if (u < total) {
+                // units are taken in increasing order: advance from the last segment
+                int sg = s_sg;
+                while (sg + 1 < nseg && segs[sg + 1].y <= u) ++sg;
+                s_sg = sg;
+                s_seg = segs[sg];
+            }
+        }
         __syncthreads();
         const int u = s_unit;
         if (u >= total) break;
-        int sg = 0;
-        while (sg + 1 < nseg && segs[sg + 1].z <= u) ++sg;
-        const int4 SG = segs[sg];
-        const int stage = SG.x, e = SG.y, loc = u - SG.z;
-        const BatchEns& E = ens[e];
+        const int4 SG = s_seg;
+        const int stage = SG.x & 15, e = SG.x >> 4, loc = u - SG.y + SG.w;
+        if (e != s_cur) {
+            const int* src = reinterpret_cast<const int*>(ens + e);
+            int* dst = reinterpret_cast<int*>(&sE);
+            for (int i = threadIdx.x; i < (int)(sizeof(BatchEns) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+            if (threadIdx.x == 0) s_cur = e;
+        }
+        const BatchEns& E = sE;
         const GeomDev& g = E.g;
         const int nt = 2 * g.K;
         // decode the unit, its dependency and the counter it completes

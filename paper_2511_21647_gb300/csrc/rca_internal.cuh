@@ -448,7 +448,7 @@ struct rca_batch {
     int n = 0;
     rca_dtype rf_t = RCA_F32, iq_t = RCA_C32, pl_t = RCA_C32;
     std::vector<BatchEns> ens;
-    std::vector<int4> segs;       // {stage, ensemble, first unit, count}
+    std::vector<int4> segs;       // {stage | ensemble << 4, first unit, count, first stage-local unit}
     int total = 0;                // work units
     int n_counters = 0;
     BatchEns* d_ens = nullptr;
@@ -469,10 +469,14 @@ struct rca_batch {
     std::vector<int> cap2d, cap3d;
     std::vector<int*> n2d, n3d;
     std::vector<float*> A, M;
-    // private handle for the localisation workspace (shares the caller's
-    // status word), so a captured graph never points at buffers that other
-    // calls on the caller's handle could reallocate
-    rca_handle* lh = nullptr;
+    // private handles for the localisation workspace, one per ensemble (they
+    // share the caller's status word), so a captured graph never points at
+    // buffers that other calls on the caller's handle could reallocate, and
+    // the ensembles' localisations can run concurrently on their own streams
+    std::vector<rca_handle*> lhs;
+    std::vector<cudaStream_t> lstreams;
+    std::vector<cudaEvent_t> ldone;
+    cudaEvent_t bf_done = nullptr;
     // CUDA graph of one batch run
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
