@@ -97,15 +97,20 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # distributed helpers (replicas only)
 # ---------------------------------------------------------------------------
-def dist_init(args):
+def dist_init(args=None):
+    """Join the torchrun job (env:// rendezvous).  NCCL with one GPU per rank;
+    gloo when CUDA is unavailable (the host-side logic is tested that way)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return rank, world, local
 
 
@@ -116,13 +121,27 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Largest value over the ranks (the slowest replica sets the job time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(frames_per_rank: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job frames/s: every rank processed frames_per_rank x steps frames
+    and the job took the slowest rank's time."""
+    return world * frames_per_rank * steps / (max_ms / 1e3)
+
+
+def emit(line: dict, rank: int) -> None:
+    """The one JSON line of a run, printed by rank 0 only."""
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -242,7 +261,7 @@ def main():
     ms_total = sum(totals)
     ms_max = max_over_ranks(ms_total, world)
     ms_step = ms_max / K
-    value = world * F * K / (ms_max / 1e3)
+    value = job_throughput(F, K, ms_max, world)
     stage_ms = {s: sum(v) / K for s, v in per_stage.items()}
     n2d_v, n3d_v = int(n2d.item()), int(n3d.item())
 
@@ -370,7 +389,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-        e2e = {"value": round(world * F * K / (e_ms / 1e3), 1), "unit": "frames/s",
+        e2e = {"value": round(job_throughput(F, K, e_ms, world), 1), "unit": "frames/s",
                "ms_per_ensemble": round(e_ms / K, 3),
                "h2d_bytes_per_step": int(rf_dev.numel() * rf_dev.element_size() + (scale.numel() * 4 if scale is not None else 0)),
                "d2h_bytes_per_step": int(out_host.numel() * 4 + cnt_host.numel() * 4),
@@ -421,7 +440,7 @@ def main():
             "device_status": [dev_status, status_after],
             "generate_s": round(gen_s, 1),
         }
-        print(json.dumps(line), flush=True)
+        emit(line, rank)
     sess.close()
     if world > 1:
         import torch.distributed as dist
@@ -462,8 +481,27 @@ def reduced_form(R, L, sess, rf, F, prm, W, K, stream):
         bf.append(ev[0].elapsed_time(ev[1]))
         lo.append(ev[1].elapsed_time(ev[2]))
     ms = (sum(bf) + sum(lo)) / K
+    # the beamforming split by stage (stage-level calls on preallocated buffers)
+    iq = complex_buffer(sess.iq_shape(F), L.RCA_C16F, rf.device)
+    sl = complex_buffer(sess.slices_shape(F), L.RCA_C32, rf.device)
+    se = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    st_ms = {"ingest": 0.0, "stage1": 0.0, "stage2": 0.0}
+    for rep in range(K + 1):
+        se[0].record(stream)
+        R.rca_ingest(sess.h, sess.t, q, L.RCA_I16, scale, F, L.RCA_CLUTTER_MEAN, iq, L.RCA_C16F)
+        se[1].record(stream)
+        R.rca_stage1(sess.h, sess.t, iq, L.RCA_C16F, F, sl)
+        se[2].record(stream)
+        R.rca_stage2_project(sess.h, sess.t, sl, F, planes, L.RCA_C16BF)
+        se[3].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            for q_, name in enumerate(("ingest", "stage1", "stage2")):
+                st_ms[name] += se[q_].elapsed_time(se[q_ + 1]) / K
+    del iq, sl
     return {"ms_per_ensemble": round(ms, 3), "value": round(F / (ms / 1e3), 1), "unit": "frames/s",
             "beamform_ms": round(sum(bf) / K, 3), "localise_ms": round(sum(lo) / K, 3),
+            "stages_ms": {k: round(v, 3) for k, v in st_ms.items()},
             "dtype": "int16 RF + per-channel scale, FP16 IQ, BF16 planes, FP32 accumulation",
             "n3d": int(bufs[3].item()), "status": R.rca_sync_status(sess.h)}
 
@@ -665,7 +703,7 @@ def reference_arm(args):
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
 
 
 if __name__ == "__main__":
