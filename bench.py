@@ -218,7 +218,9 @@ def main():
     h, t = sess.h, sess.t
 
     stages = ["ingest", "stage1", "stage2", "enhance", "detect2d", "pair3d"]
-    launches = {"ingest": 2, "stage1": 1, "stage2": 1, "enhance": 1, "detect2d": 3, "pair3d": 5}
+    # kernels per call: mean + demodulation; detect + three scan passes + gather;
+    # list offsets + match + flags + three scan passes + write
+    launches = {"ingest": 2, "stage1": 1, "stage2": 1, "enhance": 1, "detect2d": 5, "pair3d": 7}
 
     def step(ev=None):
         def mark(i):
