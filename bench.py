@@ -212,7 +212,10 @@ def main():
     planes = complex_buffer(sess.planes_shape(F), pl_t, dev)
     A = torch.empty(sess.a_shape(F), dtype=torch.float32, device=dev)
     M = torch.empty(F, dtype=torch.float32, device=dev)
-    cap2d, cap3d = 1 << 21, 1 << 19
+    # list capacities sized to the workload: 256 detections per projection
+    # plane (2D) and 64 per frame and slab (3D), several times what the method finds
+    cap2d = min(1 << 22, max(1 << 12, 256 * F * 2 * g.S))
+    cap3d = min(1 << 19, max(1 << 12, 64 * F * g.S))
     out2d, n2d, out3d, n3d = sess.loc_buffers(cap2d, cap3d)
     prm = R.make_ulm_params(d=w.ncc_d, sig_z=0.81, sig_lat=1.45, alpha=0.1, ncc_min=0.5)
     h, t = sess.h, sess.t
@@ -296,7 +299,9 @@ def main():
         ach = flops_stage1 / (stage_ms["stage1"] / 1e3) / 1e12
         roof = {"kernel": "k_stage1", "bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak_tflops, 1),
                 "unit": "TFLOP/s", "frac": round(ach / fp32_peak_tflops, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)",
+                "limiter": "shared-memory data path: each term reads two complex FP32 samples (16 B); "
+                           "84 % of L1/shared throughput in profiles/kernels_paper_40frames_full.md"}
     else:
         ach = bytes_alg[dominant] / (stage_ms[dominant] / 1e3) / 1e9
         roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
