@@ -214,8 +214,8 @@ def main():
     M = torch.empty(F, dtype=torch.float32, device=dev)
     # list capacities sized to the workload: 256 detections per projection
     # plane (2D) and 64 per frame and slab (3D), several times what the method finds
-    cap2d = min(1 << 22, max(1 << 12, 256 * F * 2 * g.S))
-    cap3d = min(1 << 19, max(1 << 12, 64 * F * g.S))
+    cap2d = min(1 << 22, max(1 << 12, 256 * F * 2 * g.n_slab))
+    cap3d = min(1 << 19, max(1 << 12, 64 * F * g.n_slab))
     out2d, n2d, out3d, n3d = sess.loc_buffers(cap2d, cap3d)
     prm = R.make_ulm_params(d=w.ncc_d, sig_z=0.81, sig_lat=1.45, alpha=0.1, ncc_min=0.5)
     h, t = sess.h, sess.t

@@ -130,8 +130,13 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
         if (stage == BS_MEAN) {
             mean_body(a0, E.rf, rf_t, E.scale, E.F, g.ns, nt * g.N * g.ns, E.mean);
         } else if (stage == BS_DEMOD) {
-            demod_body(a0, a1, a2, reinterpret_cast<float2*>(smraw), E.rf, rf_t, E.scale, E.mean, E.mix, fir, nt, g.N,
-                       g.ns, E.iq, iq_t);
+            float2* xs = reinterpret_cast<float2*>(smraw);
+            if (rf_t == RCA_F32)
+                demod_body<RCA_F32>(a0, a1, a2, xs, E.rf, E.scale, E.mean, E.mix, fir, nt, g.N, g.ns, E.iq, iq_t);
+            else if (rf_t == RCA_F16)
+                demod_body<RCA_F16>(a0, a1, a2, xs, E.rf, E.scale, E.mean, E.mix, fir, nt, g.N, g.ns, E.iq, iq_t);
+            else
+                demod_body<RCA_I16>(a0, a1, a2, xs, E.rf, E.scale, E.mean, E.mix, fir, nt, g.N, g.ns, E.iq, iq_t);
         } else if (stage == BS_STAGE1) {
             ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.rtab, E.rblk, E.dmax, E.chunks,
                                               E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);

@@ -13,12 +13,13 @@ __global__ void __launch_bounds__(256) k_mean(const void* __restrict__ rf, int r
     mean_body(blockIdx.x, rf, rf_t, scale, F, ns, ncol, mean);
 }
 
-__global__ void __launch_bounds__(256, 4) k_demod(const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
-                                               const float* __restrict__ mean, const float2* __restrict__ mix, Fir fir,
-                                               int nt, int E, int ns, void* __restrict__ iq, int iq_t)
+template <int RT>
+__global__ void __launch_bounds__(256, 4) k_demod(const void* __restrict__ rf, const float* __restrict__ scale,
+                                                  const float* __restrict__ mean, const float2* __restrict__ mix,
+                                                  Fir fir, int nt, int E, int ns, void* __restrict__ iq, int iq_t)
 {
     __shared__ float2 xs[DM_NE * DM_PITCH];
-    demod_body(blockIdx.x, blockIdx.y, blockIdx.z, xs, rf, rf_t, scale, mean, mix, fir, nt, E, ns, iq, iq_t);
+    demod_body<RT>(blockIdx.x, blockIdx.y, blockIdx.z, xs, rf, scale, mean, mix, fir, nt, E, ns, iq, iq_t);
 }
 
 template <typename TS, int MAXR>
@@ -181,7 +182,12 @@ rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca
     Fir fir;
     for (int q = 0; q < 31; ++q) fir.h[q] = t->fir[q];
     dim3 grid((g.ns + DM_NT - 1) / DM_NT, (g.N + DM_NE - 1) / DM_NE, F * nt);
-    k_demod<<<grid, 256, 0, h->stream>>>(rf, rf_t, scale, mean, t->mix, fir, nt, g.N, g.ns, iq, iq_t);
+    if (rf_t == RCA_F32)
+        k_demod<RCA_F32><<<grid, 256, 0, h->stream>>>(rf, scale, mean, t->mix, fir, nt, g.N, g.ns, iq, iq_t);
+    else if (rf_t == RCA_F16)
+        k_demod<RCA_F16><<<grid, 256, 0, h->stream>>>(rf, scale, mean, t->mix, fir, nt, g.N, g.ns, iq, iq_t);
+    else
+        k_demod<RCA_I16><<<grid, 256, 0, h->stream>>>(rf, scale, mean, t->mix, fir, nt, g.N, g.ns, iq, iq_t);
     return cuda_check(h, cudaGetLastError(), "ingest kernels");
 }
 

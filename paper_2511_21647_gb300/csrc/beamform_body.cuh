@@ -109,11 +109,31 @@ __device__ __forceinline__ void mean_body(int bx, const void* __restrict__ rf, i
 // staged sample is read DM_OB + 30 times per DM_OB outputs instead of 17 times
 // per output.
 #define DM_OB 8             // consecutive outputs per thread
+// four consecutive channel samples n .. n + 3 (n a multiple of 4) as floats
+template <int RT>
+__device__ __forceinline__ float4 rf_quad(const void* __restrict__ rf, size_t i)
+{
+    if constexpr (RT == RCA_F32) {
+        return __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(rf) + i));
+    } else if constexpr (RT == RCA_F16) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const __half*>(rf) + i));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&x.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&x.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        const uint2 x = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const int16_t*>(rf) + i));
+        return make_float4((float)(short)(x.x & 0xffff), (float)(short)(x.x >> 16), (float)(short)(x.y & 0xffff),
+                           (float)(short)(x.y >> 16));
+    }
+}
+
+template <int RT>
 __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __restrict__ xs,
-                                           const void* __restrict__ rf, int rf_t, const float* __restrict__ scale,
+                                           const void* __restrict__ rf, const float* __restrict__ scale,
                                            const float* __restrict__ mean, const float2* __restrict__ mix,
                                            const Fir& fir, int nt, int E, int ns, void* __restrict__ iq, int iq_t)
 {
+    constexpr int rf_t = RT;
     const int n0 = bx * DM_NT;
     const int e0 = by * DM_NE;
     const int fk = bz;
@@ -121,20 +141,58 @@ __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __res
     const size_t chan0 = (size_t)fk * E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     // stage (rf - mean) * exp(-j 2 pi fc t_n) for samples n0-15 .. n0+DM_NT+14
-    for (int el = warp; el < DM_NE; el += nwarp) {
-        const int e = e0 + el;
-        const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
-        const float* mrow = mean ? mean + ((size_t)k * E + e) * ns : nullptr;
-        for (int s = lane; s < DM_NT + 30; s += 32) {
-            const int n = n0 - 15 + s;
-            float2 v = make_float2(0.f, 0.f);
-            if (n >= 0 && n < ns && e < E) {
-                float x = rf_value(rf, rf_t, (chan0 + e) * ns + n) * sc;
-                if (mrow) x -= mrow[n];
-                const float2 m = mix[n];
-                v = make_float2(x * m.x, x * m.y);
+    const bool quads = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(rf) & 15) == 0 &&
+                       (reinterpret_cast<uintptr_t>(mean) & 15) == 0;
+    if (quads) {
+        // whole aligned quads n0-16+4q .. n0-13+4q (q < 40): each inside or outside [0, ns)
+        for (int el = warp; el < DM_NE; el += nwarp) {
+            const int e = e0 + el;
+            const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
+            for (int q = lane; q < (DM_NT + 32) / 4; q += 32) {
+                const int nb = n0 - 16 + 4 * q;
+                float x[4] = {0.f, 0.f, 0.f, 0.f};
+                float4 m01 = make_float4(0.f, 0.f, 0.f, 0.f), m23 = m01;
+                if (nb >= 0 && nb < ns && e < E) {
+                    const float4 r = rf_quad<RT>(rf, (chan0 + e) * ns + nb);
+                    x[0] = r.x * sc;
+                    x[1] = r.y * sc;
+                    x[2] = r.z * sc;
+                    x[3] = r.w * sc;
+                    if (mean) {
+                        const float4 mu = __ldg(reinterpret_cast<const float4*>(mean + ((size_t)k * E + e) * ns + nb));
+                        x[0] -= mu.x;
+                        x[1] -= mu.y;
+                        x[2] -= mu.z;
+                        x[3] -= mu.w;
+                    }
+                    m01 = __ldg(reinterpret_cast<const float4*>(mix + nb));
+                    m23 = __ldg(reinterpret_cast<const float4*>(mix + nb + 2));
+                }
+                const float2 v[4] = {make_float2(x[0] * m01.x, x[0] * m01.y), make_float2(x[1] * m01.z, x[1] * m01.w),
+                                     make_float2(x[2] * m23.x, x[2] * m23.y), make_float2(x[3] * m23.z, x[3] * m23.w)};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int sidx = 4 * q - 1 + j;
+                    if (sidx >= 0 && sidx < DM_NT + 30) xs[el * DM_PITCH + sidx] = v[j];
+                }
             }
-            xs[el * DM_PITCH + s] = v;
+        }
+    } else {
+        for (int el = warp; el < DM_NE; el += nwarp) {
+            const int e = e0 + el;
+            const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
+            const float* mrow = mean ? mean + ((size_t)k * E + e) * ns : nullptr;
+            for (int sidx = lane; sidx < DM_NT + 30; sidx += 32) {
+                const int n = n0 - 15 + sidx;
+                float2 v = make_float2(0.f, 0.f);
+                if (n >= 0 && n < ns && e < E) {
+                    float x = rf_value(rf, rf_t, (chan0 + e) * ns + n) * sc;
+                    if (mrow) x -= mrow[n];
+                    const float2 m = mix[n];
+                    v = make_float2(x * m.x, x * m.y);
+                }
+                xs[el * DM_PITCH + sidx] = v;
+            }
         }
     }
     __syncthreads();
