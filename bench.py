@@ -651,15 +651,26 @@ def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):
     flop = px * (2 * 9 * 32 + 2 * 2 * 288 * 32 + 2 * 288 * 16)
     tflops = flop / (cnn_ms / 1e3) / 1e12
     peak = peaks.get("bf16_tflops", 1900.0)
+    # algorithmic bytes per plane pixel of the forward pass: input plane read, FP32
+    # input written and read, three 32-channel BF16 activations written and read,
+    # 16 FP32 heatmap values written -- 460 B against 46 656 FLOP (below the
+    # FLOP/B ridge of this GPU: the network is bound by HBM)
+    cnn_bytes = px * (4 + 4 + 4 + 3 * (64 + 64) + 64)
+    cnn_gbs = cnn_bytes / (cnn_ms / 1e3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
     R.ulm_cnn_destroy(c)
     return {"train_planes": n_train,
             "train_steps": steps, "batch": 64, "loss_first_last": [hist[0][1], hist[-1][1]],
             "dataset_s": round(build_s, 1), "train_s": round(train_s, 1), "eval_tiny": ev,
             "paper_frames": frames, "localise_ms_per_300_frames": round(total_ms * 300 / frames, 3),
             "cnn_ms_per_300_frames": round(cnn_ms * 300 / frames, 3),
-            "cnn_roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
-                             "frac": round(tflops / peak, 4), "kernel": "k_conv_mma (mma.sync BF16)",
-                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+            "cnn_roofline": {"bound": "hbm", "achieved": round(cnn_gbs, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(cnn_gbs / hbm, 4), "bytes_per_pixel": 460,
+                             "kernel": "k_conv_tc (tcgen05 BF16, TMEM accumulators) + k_conv1_fwd",
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                             "tensor": {"achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+                                        "frac": round(tflops / peak, 4),
+                                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}},
             "status": R.rca_sync_status(h)}
 
 

@@ -23,10 +23,6 @@ __device__ __forceinline__ int ld_acquire(const int* p)
     return v;
 }
 
-__device__ __forceinline__ void mbar_inval(uint64_t* bar)
-{
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 template <typename TS, int MAXR, int TM>
 __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,

@@ -220,6 +220,245 @@ __global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16* __restric
 }
 
 // ---------------------------------------------------------------------------
+// 3x3 convolution on the 5th-generation tensor cores (tcgen05, TMEM).
+// A CTA of 128 threads owns a tile of 8 rows x 16 columns (M = 128 pixels,
+// ordered column-major: pixel m = 8 x + y), so that one image column of the
+// tile is one 8-row core matrix of the MMA's A operand.  The input tile with
+// its one-pixel halo (10 x 18 pixels, CIN channels) sits in shared memory in
+// the K-major, no-swizzle core-matrix layout
+//   [CIN / 8][18 columns][10 rows][8 channels] (16-byte rows),
+// so the A operand of tap (dy, dx) is the same array seen from start offset
+// dx x 160 + dy x 16 bytes: a column step is 160 bytes (SBO) and an 8-channel
+// step 18 x 160 bytes (LBO).  No im2col copy is made.  The weights of all nine
+// taps (B operand, [9][CIN / 8][COUT / 8][8 outputs][8 channels]) are staged
+// once per CTA.  One thread issues the 9 x CIN / 16 MMAs (M = 128, N = COUT,
+// K = 16, BF16 in, FP32 accumulators in TMEM) and commits them to an
+// mbarrier; each warp then reads its 32 pixels' rows of the accumulator with
+// tcgen05.ld for the epilogue.
+// ---------------------------------------------------------------------------
+#define TC_HALO_C 18                        // tile columns + halo
+#define TC_HALO_R 10                        // tile rows + halo
+#define TC_CM_BYTES (TC_HALO_R * 16)        // one column of the halo tile: 10 rows x 16 bytes
+
+__device__ __forceinline__ uint64_t tc_sdesc(unsigned saddr, unsigned lbo, unsigned sbo)
+{
+    // shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+    // offsets in 16-byte units, descriptor version 1, no swizzle
+    return (uint64_t)((saddr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr unsigned tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, uint64_t da, uint64_t db, unsigned idesc, int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+template <int NC>
+__device__ __forceinline__ void tc_ld(unsigned taddr, float* v);
+template <>
+__device__ __forceinline__ void tc_ld<16>(unsigned taddr, float* v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+template <>
+__device__ __forceinline__ void tc_ld<32>(unsigned taddr, float* v)
+{
+    tc_ld<16>(taddr, v);
+    tc_ld<16>(taddr + 16, v + 16);
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict__ x,
+                                                 const __nv_bfloat16* __restrict__ wt,
+                                                 const float* __restrict__ bias,
+                                                 const __nv_bfloat16* __restrict__ mask, int B, int H, int W,
+                                                 void* __restrict__ out, unsigned* __restrict__ status)
+{
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 32, "shapes of the 3x3 layers");
+    constexpr int KC = CIN / 8, NG = COUT / 8;
+    constexpr int TAPB = KC * NG * 128;                 // bytes of one tap's weights
+    constexpr int ABYTES = KC * TC_HALO_C * TC_CM_BYTES;
+    constexpr unsigned IDESC = tc_idesc(128, COUT);
+    constexpr unsigned TMEM_COLS = 64;                  // two 32-column accumulators
+    extern __shared__ __align__(16) unsigned char smtc[];
+    unsigned char* sB = smtc;                           // [9][KC][NG][8][8] bf16
+    unsigned char* sA = smtc + 9 * TAPB;                // [2][KC][18][10][8] bf16
+    __shared__ uint64_t bars[2];
+    __shared__ unsigned s_tmem;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // weights: element (o, t, c) of [COUT][9][CIN] -> tap t, core (c / 8, o / 8), row o % 8, column c % 8
+    for (int q = threadIdx.x; q < COUT * 9 * KC; q += blockDim.x) {
+        const int o = q / (9 * KC), r = q % (9 * KC), t = r / KC, kc = r % KC;
+        const uint4 v = reinterpret_cast<const uint4*>(wt)[q];   // 8 channels kc*8 .. of (o, t)
+        *reinterpret_cast<uint4*>(sB + t * TAPB + (kc * NG + o / 8) * 128 + (o % 8) * 16) = v;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    const unsigned sAa = smem_u32(sA), sBa = smem_u32(sB);
+    const int tiles_i = (H + CONV_TH - 1) / CONV_TH, tiles_j = (W + CONV_TW - 1) / CONV_TW;
+    const int ntiles = B * tiles_i * tiles_j;
+    auto coords = [&](int tile, int& b, int& i0, int& j0) {
+        b = tile / (tiles_i * tiles_j);
+        const int tij = tile % (tiles_i * tiles_j);
+        i0 = (tij / tiles_j) * CONV_TH;
+        j0 = (tij % tiles_j) * CONV_TW;
+    };
+    // halo tile of `tile` into buffer `buf`: 8-channel chunk kc of pixel (row yr, column xg)
+    auto load = [&](int tile, int buf) {
+        int b, i0, j0;
+        coords(tile, b, i0, j0);
+        unsigned char* dst = sA + buf * ABYTES;
+        for (int q = threadIdx.x; q < TC_HALO_R * TC_HALO_C * KC; q += blockDim.x) {
+            const int kc = q % KC, p = q / KC, xg = p % TC_HALO_C, yr = p / TC_HALO_C;
+            const int ii = i0 - 1 + yr, jj = j0 - 1 + xg;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (ii >= 0 && ii < H && jj >= 0 && jj < W)
+                v = reinterpret_cast<const uint4*>(x + (((size_t)b * H + ii) * W + jj) * CIN)[kc];
+            *reinterpret_cast<uint4*>(dst + (kc * TC_HALO_C + xg) * TC_CM_BYTES + yr * 16) = v;
+        }
+        // generic-proxy writes of the tile before the tensor cores read it
+        fence_proxy_async();
+    };
+    // the 9 x CIN / 16 MMAs of buffer `buf` into accumulator `buf` (one thread)
+    auto issue = [&](int buf) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned aB = sAa + buf * ABYTES, dcol = tmem + (unsigned)(32 * buf);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int dy = t / 3, dx = t % 3;
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk) {
+                const uint64_t da = tc_sdesc(aB + (2 * kk * TC_HALO_C + dx) * TC_CM_BYTES + dy * 16,
+                                             TC_HALO_C * TC_CM_BYTES, TC_CM_BYTES);
+                const uint64_t db = tc_sdesc(sBa + t * TAPB + 2 * kk * NG * 128, NG * 128, 128);
+                tc_mma(dcol, da, db, IDESC, (t | kk) != 0);
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bars[buf]))
+                     : "memory");
+    };
+    // software pipeline: the load and MMAs of tile k + 1 run while tile k's epilogue drains
+    unsigned phase = 0;   // bit b: parity of the next completion of bars[b]
+    bool ok = true;
+    int tile = blockIdx.x;
+    if (tile < ntiles) {
+        load(tile, 0);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) issue(0);
+    }
+    for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+        const int cur = k & 1, nxt = cur ^ 1;
+        const int ntile = tile + gridDim.x;
+        if (ntile < ntiles) load(ntile, nxt);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (ntile < ntiles && threadIdx.x == 0) issue(nxt);
+        // bounded wait for tile k's accumulators
+        if (!mbar_wait_bounded(&bars[cur], (phase >> cur) & 1u)) ok = false;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+            // the MMAs in flight finish (bounded) before the accumulators are freed
+            mbar_wait_bounded(&bars[cur], (phase >> cur) & 1u);
+            if (ntile < ntiles) mbar_wait_bounded(&bars[nxt], (phase >> nxt) & 1u);
+            break;
+        }
+        phase ^= 1u << cur;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        int b, i0, j0;
+        coords(tile, b, i0, j0);
+        // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 = pixels m of the tile
+        float v[COUT];
+        tc_ld<COUT>(tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(32 * cur), v);
+        const int m = 32 * warp + lane;
+        const int i = i0 + (m & 7), j = j0 + (m >> 3);
+        if (i < H && j < W) {
+            const size_t pix = ((size_t)b * H + i) * W + j;
+            if (MODE == 0) {
+                unsigned pk[COUT / 2];
+#pragma unroll
+                for (int o = 0; o < COUT; o += 2)
+                    pk[o / 2] = pack_bf2(fmaxf(v[o] + bias[o], 0.f), fmaxf(v[o + 1] + bias[o + 1], 0.f));
+#pragma unroll
+                for (int q = 0; q < COUT / 8; ++q)
+                    reinterpret_cast<uint4*>(out)[pix * (COUT / 8) + q] =
+                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            } else if (MODE == 1) {
+                // channel c = 4 a + s -> heatmap pixel (4 i + a, 4 j + s)
+                float* heat = reinterpret_cast<float*>(out);
+                const size_t W4 = (size_t)W * CNN_UP;
+#pragma unroll
+                for (int a = 0; a < CNN_UP; ++a) {
+                    const float4 r4 = make_float4(v[4 * a] + bias[4 * a], v[4 * a + 1] + bias[4 * a + 1],
+                                                  v[4 * a + 2] + bias[4 * a + 2], v[4 * a + 3] + bias[4 * a + 3]);
+                    __stcs(reinterpret_cast<float4*>(heat + ((size_t)b * H * CNN_UP + (size_t)i * CNN_UP + a) * W4 +
+                                                     (size_t)j * CNN_UP),
+                           r4);
+                }
+            } else {
+                const unsigned* mk = reinterpret_cast<const unsigned*>(mask) + pix * (COUT / 2);
+                unsigned pk[COUT / 2];
+#pragma unroll
+                for (int o = 0; o < COUT; o += 2) {
+                    const float2 mm = unpack_bf2(mk[o / 2]);
+                    pk[o / 2] = pack_bf2(mm.x > 0.f ? v[o] : 0.f, mm.y > 0.f ? v[o + 1] : 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < COUT / 8; ++q)
+                    reinterpret_cast<uint4*>(out)[pix * (COUT / 8) + q] =
+                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            }
+        }
+        // every warp's reads of accumulator `cur` are done before MMAs write it again
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_inval(&bars[0]);
+        mbar_inval(&bars[1]);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient on tensor cores: dW[o][t][c] = sum_p dY[p][o] X[p + t][c],
 // a GEMM with M = COUT, N = 9 x CIN and the reduction over pixels.  Each CTA
 // accumulates its tiles in registers and writes one partial [COUT][9 CIN]
@@ -480,6 +719,7 @@ struct ulm_cnn {
     float* part = nullptr;  // scratch for per-CTA partials
     size_t part_len = 0;
     int grid_conv = 0;
+    int grid_conv_tc = 0;
 };
 
 static rca_status cnn_check_shape(ulm_cnn* c, int B, int H, int W)
@@ -506,14 +746,15 @@ template <int CIN, int COUT, int MODE>
 static rca_status conv_launch(ulm_cnn* c, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
                               const __nv_bfloat16* mask, int B, int H, int W, void* out)
 {
-    constexpr int PS = CIN + 8, WS = 9 * CIN + 8;
-    const size_t smem = ((size_t)COUT * WS + (size_t)(CONV_TH + 2) * (CONV_TW + 2) * PS) * sizeof(__nv_bfloat16);
-    auto kern = k_conv_mma<CIN, COUT, MODE>;
+    // weights of the nine taps + two halo tiles
+    constexpr size_t smem = (size_t)9 * CIN * COUT * 2 + (size_t)2 * (CIN / 8) * TC_HALO_C * TC_CM_BYTES;
+    static_assert(smem <= 100 * 1024, "conv tile exceeds its shared-memory budget");
+    auto kern = k_conv_tc<CIN, COUT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(c->h, e, "conv smem attribute");
     const int ntiles = B * ((H + CONV_TH - 1) / CONV_TH) * ((W + CONV_TW - 1) / CONV_TW);
-    const int grid = std::min(ntiles, c->grid_conv);
-    kern<<<grid, 256, smem, c->h->stream>>>(x, w, bias, mask, B, H, W, out);
+    const int grid = std::min(ntiles, c->grid_conv_tc);
+    kern<<<grid, 128, smem, c->h->stream>>>(x, w, bias, mask, B, H, W, out, c->h->d_status);
     return cuda_check(c->h, cudaGetLastError(), "conv kernel");
 }
 
@@ -567,6 +808,7 @@ extern "C" rca_status ulm_cnn_create(rca_handle* h, const ulm_cnn_desc* d, ulm_c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->grid_conv = 4 * sms;
+    c->grid_conv_tc = 4 * sms;   // four CTAs per SM (64 TMEM columns each)
     c->part_len = (size_t)c->grid_conv * (CNN_C * 9 * CNN_C + CNN_C) + 4096;
     const size_t P = c->lay.total, px = c->cap_px;
     bool ok = cudaMalloc(&c->params, P * 4) == cudaSuccess && cudaMalloc(&c->grads, P * 4) == cudaSuccess &&

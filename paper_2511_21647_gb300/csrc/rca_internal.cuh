@@ -298,6 +298,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase)
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // bounded wait for the given phase parity; false if the budget ran out
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase)
 {
