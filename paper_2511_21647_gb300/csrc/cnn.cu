@@ -6,9 +6,12 @@
 // (Sec. IV); the network is the build's reading of that form.
 //
 //   L1 conv3x3(1 -> 32) + ReLU     FP32 CUDA cores (K = 9)
-//   L2 conv3x3(32 -> 32) + ReLU    mma.sync m16n8k16 BF16, FP32 accumulate
+//   L2 conv3x3(32 -> 32) + ReLU    tcgen05 MMA (BF16, FP32 accumulators in TMEM)
 //   L3 conv3x3(32 -> 32) + ReLU    idem
 //   L4 conv3x3(32 -> 16)           idem, epilogue = pixel shuffle to 4x
+// The input gradients run the same tcgen05 kernel on flipped weights; the
+// weight gradients (M = COUT is below the tcgen05 minimum of 64) use
+// mma.sync m16n8k16.
 //
 // Activations NHWC BF16; weights [Cout][9 taps][Cin] (tap = 3 (dy+1) + dx+1).
 #include <algorithm>
@@ -115,110 +118,11 @@ __global__ void k_conv1_fwd(const float* __restrict__ x, const float* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Implicit-GEMM 3x3 convolution on tensor cores.  Rows of the GEMM are the
-// 16 pixels of a tile row (one warp), columns the output channels, the
-// reduction runs over 9 taps x CIN input channels in steps of 16.  The input
-// tile (with a one-pixel halo) and all weights sit in shared memory with
-// padded strides (conflict-free fragment loads).  CTAs loop over tiles.
+// Epilogue modes of the 3x3 convolution kernels:
 //   MODE 0: + bias, ReLU, BF16 NHWC out
 //   MODE 1: + bias, pixel shuffle (COUT = 16) to the FP32 4x heatmap
 //   MODE 2: no bias, times (mask > 0) of a BF16 NHWC tensor, BF16 out (dgrad)
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ wt,
-                                                  const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
-                                                  int B, int H, int W, void* __restrict__ out)
-{
-    constexpr int PS = CIN + 8;          // pixel stride in the input tile (bf16)
-    constexpr int WS = 9 * CIN + 8;      // weight row stride (bf16)
-    constexpr int HH = CONV_TH + 2, HW2 = CONV_TW + 2;
-    constexpr int NT = COUT / 8;         // n-tiles
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smraw);     // [COUT][WS]
-    __nv_bfloat16* Xs = Ws + COUT * WS;                             // [HH][HW2][PS]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, tig = lane & 3;
-    // weights once per CTA
-    for (int q = threadIdx.x; q < COUT * 9 * CIN / 8; q += blockDim.x) {
-        const int o = q / (9 * CIN / 8), r = q % (9 * CIN / 8);
-        *reinterpret_cast<uint4*>(Ws + o * WS + r * 8) = reinterpret_cast<const uint4*>(wt)[q];
-    }
-    const int tiles_i = (H + CONV_TH - 1) / CONV_TH, tiles_j = (W + CONV_TW - 1) / CONV_TW;
-    const int ntiles = B * tiles_i * tiles_j;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int b = tile / (tiles_i * tiles_j), tij = tile % (tiles_i * tiles_j);
-        const int i0 = (tij / tiles_j) * CONV_TH, j0 = (tij % tiles_j) * CONV_TW;
-        __syncthreads();  // previous tile's readers are done
-        for (int q = threadIdx.x; q < HH * HW2 * (CIN / 8); q += blockDim.x) {
-            const int pix = q / (CIN / 8), v = q % (CIN / 8);
-            const int ii = i0 - 1 + pix / HW2, jj = j0 - 1 + pix % HW2;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (ii >= 0 && ii < H && jj >= 0 && jj < W)
-                val = reinterpret_cast<const uint4*>(x + (((size_t)b * H + ii) * W + jj) * CIN)[v];
-            *reinterpret_cast<uint4*>(Xs + pix * PS + v * 8) = val;
-        }
-        __syncthreads();
-        float acc[NT][4];
-#pragma unroll
-        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-        const int r = warp;  // tile row of this warp
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int dy = t / 3, dx = t % 3;  // halo offsets (dy - 1 + 1)
-            const __nv_bfloat16* xa = Xs + ((r + dy) * HW2 + dx) * PS;
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                unsigned a[4];
-                a[0] = *reinterpret_cast<const unsigned*>(xa + g * PS + kc * 16 + 2 * tig);
-                a[1] = *reinterpret_cast<const unsigned*>(xa + (g + 8) * PS + kc * 16 + 2 * tig);
-                a[2] = *reinterpret_cast<const unsigned*>(xa + g * PS + kc * 16 + 2 * tig + 8);
-                a[3] = *reinterpret_cast<const unsigned*>(xa + (g + 8) * PS + kc * 16 + 2 * tig + 8);
-#pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    const __nv_bfloat16* wb = Ws + (n * 8 + g) * WS + t * CIN + kc * 16 + 2 * tig;
-                    unsigned bb[2];
-                    bb[0] = *reinterpret_cast<const unsigned*>(wb);
-                    bb[1] = *reinterpret_cast<const unsigned*>(wb + 8);
-                    mma_bf16(acc[n], a, bb);
-                }
-            }
-        }
-        // epilogue: rows g and g + 8 of the tile row, channels n*8 + 2 tig (+1)
-        const int i = i0 + r;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int j = j0 + g + 8 * half;
-            if (i >= H || j >= W) continue;
-            const size_t pix = ((size_t)b * H + i) * W + j;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int o = n * 8 + 2 * tig;
-                float v0 = acc[n][2 * half], v1 = acc[n][2 * half + 1];
-                if (MODE == 0) {
-                    v0 = fmaxf(v0 + bias[o], 0.f);
-                    v1 = fmaxf(v1 + bias[o + 1], 0.f);
-                    reinterpret_cast<unsigned*>(out)[(pix * COUT + o) / 2] = pack_bf2(v0, v1);
-                } else if (MODE == 1) {
-                    // channel c = 4 a + s -> heatmap pixel (4 i + a, 4 j + s)
-                    float* heat = reinterpret_cast<float*>(out);
-                    const size_t W4 = (size_t)W * CNN_UP;
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int c = o + e, aa = c / CNN_UP, ss = c % CNN_UP;
-                        heat[((size_t)b * H * CNN_UP + (size_t)i * CNN_UP + aa) * W4 + (size_t)j * CNN_UP + ss] =
-                            (e ? v1 : v0) + bias[c];
-                    }
-                } else {
-                    const float2 m = unpack_bf2(reinterpret_cast<const unsigned*>(mask)[(pix * COUT + o) / 2]);
-                    v0 = m.x > 0.f ? v0 : 0.f;
-                    v1 = m.y > 0.f ? v1 : 0.f;
-                    reinterpret_cast<unsigned*>(out)[(pix * COUT + o) / 2] = pack_bf2(v0, v1);
-                }
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // 3x3 convolution on the 5th-generation tensor cores (tcgen05, TMEM).
 // A CTA of 128 threads owns a tile of 8 rows x 16 columns (M = 128 pixels,
