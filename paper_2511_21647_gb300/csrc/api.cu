@@ -926,8 +926,7 @@ extern "C" rca_status rca_autotune(rca_handle* h, rca_tables* t, const void* iq,
         const int zt = sh[0], dc = sh[1];
         const int win = stage1_window(t, zt, dc, nullptr);
         if (stage1_smem_bytes(t, zt, dc, win, esz) > 200 * 1024) continue;
-        const int LW = (g.N + 31) / 32, RG = std::max(1, 8 / LW);
-        if ((zt + RG - 1) / RG > 16) continue;
+        if (stage1_layout(g.N, zt, true).per > 16) continue;
         if ((st = plan_stage1(h, t, zt, dc)) != RCA_OK) break;
         const float ms = time_it([&] { launch_stage1(h, t, iq, iq_t, F, slices); });
         if (ms < best) {

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256, 4) k_demod(const void* __restrict__ rf, c
     demod_body<RT>(blockIdx.x, blockIdx.y, blockIdx.z, xs, rf, scale, mean, mix, fir, nt, E, ns, iq, iq_t);
 }
 
-template <typename TS, int MAXR>
+template <typename TS, int MAXR, bool PAIR>
 __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __restrict__ iq,
                                                 const unsigned char* __restrict__ rtab, int rblk,
                                                 const int* __restrict__ dmax, const int4* __restrict__ chunks, int zt,
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bars[2];
-    stage1_body<TS, MAXR, true>(blockIdx.x, blockIdx.y, blockIdx.z, smraw, bars, g, iq, rtab, rblk, dmax, chunks, zt,
+    stage1_body<TS, MAXR, true, PAIR>(blockIdx.x, blockIdx.y, blockIdx.z, smraw, bars, g, iq, rtab, rblk, dmax, chunks, zt,
                                 dc, n_tiles, nch, win, slices, status);
 }
 
@@ -191,23 +191,14 @@ rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca
     return cuda_check(h, cudaGetLastError(), "ingest kernels");
 }
 
-// Lateral pixels across the lanes of LW warps, rows across RG warp groups:
-// 32 * LW * RG <= 256 threads, each thread owning ceil(zt / RG) rows.
-static void warp_layout(int N, int zt, int* LW, int* RG, int* per)
-{
-    *LW = (N + 31) / 32;
-    *RG = std::max(1, 8 / *LW);
-    *per = (zt + *RG - 1) / *RG;
-}
-
-template <typename TS, int MAXR>
+template <typename TS, int MAXR, bool PAIR>
 static rca_status stage1_launch(rca_handle* h, const rca_tables* t, const void* iq, int F, float2* slices,
                                 int threads)
 {
     const GeomDev& g = t->gd;
     const Stage1Plan& p = t->s1;
     const size_t smem = stage1_smem_bytes(t, p.zt, p.dc, p.win, sizeof(TS));
-    auto kern = k_stage1<TS, MAXR>;
+    auto kern = k_stage1<TS, MAXR, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage1 smem attribute");
     dim3 grid(p.n_tiles, 2 * g.K, F);
@@ -221,19 +212,26 @@ template <typename TS>
 static rca_status stage1_dispatch(rca_handle* h, const rca_tables* t, const void* iq, int F, float2* slices)
 {
     const GeomDev& g = t->gd;
-    int LW, RG, per;
-    warp_layout(g.N, t->s1.zt, &LW, &RG, &per);
-    if (LW > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256 is not supported");
-    const int threads = 32 * LW * RG;
+    const S1Layout L = stage1_layout(g.N, t->s1.zt, true);
+    if (L.LW > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256 is not supported");
+    const int threads = 32 * L.LW * L.RG;
     // the kernel's row loop is exact: every thread owns exactly MAXR rows
     // (or one row, with some warps idle, when the tile has fewer rows than warps)
-    if (!(per == 1 || per * RG == t->s1.zt))
-        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 row tile %d is not a multiple of %d row groups", t->s1.zt, RG);
-    if (per == 1) return stage1_launch<TS, 1>(h, t, iq, F, slices, threads);
-    if (per == 2) return stage1_launch<TS, 2>(h, t, iq, F, slices, threads);
-    if (per == 4) return stage1_launch<TS, 4>(h, t, iq, F, slices, threads);
-    if (per == 8) return stage1_launch<TS, 8>(h, t, iq, F, slices, threads);
-    if (per == 16) return stage1_launch<TS, 16>(h, t, iq, F, slices, threads);
+    if (!(L.per == 1 || L.per * L.RG == t->s1.zt))
+        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 row tile %d is not a multiple of %d row groups", t->s1.zt,
+                         L.RG);
+    if (L.pair) {
+        if (L.per == 1) return stage1_launch<TS, 1, true>(h, t, iq, F, slices, threads);
+        if (L.per == 2) return stage1_launch<TS, 2, true>(h, t, iq, F, slices, threads);
+        if (L.per == 4) return stage1_launch<TS, 4, true>(h, t, iq, F, slices, threads);
+        if (L.per == 8) return stage1_launch<TS, 8, true>(h, t, iq, F, slices, threads);
+    } else {
+        if (L.per == 1) return stage1_launch<TS, 1, false>(h, t, iq, F, slices, threads);
+        if (L.per == 2) return stage1_launch<TS, 2, false>(h, t, iq, F, slices, threads);
+        if (L.per == 4) return stage1_launch<TS, 4, false>(h, t, iq, F, slices, threads);
+        if (L.per == 8) return stage1_launch<TS, 8, false>(h, t, iq, F, slices, threads);
+        if (L.per == 16) return stage1_launch<TS, 16, false>(h, t, iq, F, slices, threads);
+    }
     return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 row tile too tall");
 }
 
@@ -296,10 +294,10 @@ rca_status launch_direct(rca_handle* h, const rca_tables* t, const void* iq, rca
     const GeomDev& g = t->gd;
     if (!complex_dtype(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
     if (32 % g.P != 0) return set_error(h, RCA_ERR_UNSUPPORTED, "direct mode needs P dividing 32");
-    int LW, RG, per;
-    warp_layout(g.N, t->direct_zt, &LW, &RG, &per);
-    if (LW > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256 is not supported");
-    const int threads = 32 * LW * RG;
+    const S1Layout L = stage1_layout(g.N, t->direct_zt, false);
+    if (L.LW > 8) return set_error(h, RCA_ERR_UNSUPPORTED, "n_el > 256 is not supported");
+    const int threads = 32 * L.LW * L.RG;
+    const int per = L.per;
     if (per <= 2) return direct_launch<2>(h, t, iq, iq_t, F, planes, pt, threads);
     if (per <= 4) return direct_launch<4>(h, t, iq, iq_t, F, planes, pt, threads);
     if (per <= 8) return direct_launch<8>(h, t, iq, iq_t, F, planes, pt, threads);

@@ -308,15 +308,82 @@ __device__ __forceinline__ void s1_mfma(float& a1x, float& a1y, float& a2x, floa
 
 enum { S1_NONE = 0, S1_FULL = 1, S1_PRED = 2 };
 
+// One pixel's update for one (row, d) record: A = {A1.x, A1.y, A2.x, A2.y}
+// += the folded term of the mirror elements at window offsets ox (l - d) and
+// oy (l + d), sample rows at `row` and row + RS.  Modes XM / YM and the
+// per-lane predicates hx / hy say which of the two elements exist.
+// HALF: r0 / r1 = {Re a, Re b} / {Im a, Im b} half pairs; else r0..r3 =
+// Re a, Re b, Im a, Im b as floats.
+template <typename TS, int XM, int YM>
+__device__ __forceinline__ void s1_pixel(float (&A)[4], unsigned row, unsigned ox, unsigned oy, int RS, bool hx,
+                                         bool hy, unsigned r0, unsigned r1, unsigned r2, unsigned r3)
+{
+    if constexpr (S1Rec<TS>::HALF) {
+        unsigned x0 = 0u, x1 = 0u, y0 = 0u, y1 = 0u;
+        if (XM != S1_NONE && hx) {
+            x0 = lds_u32(row + ox);
+            x1 = lds_u32(row + ox + RS);
+        }
+        if (YM != S1_NONE && hy) {
+            y0 = lds_u32(row + oy);
+            y1 = lds_u32(row + oy + RS);
+        }
+        unsigned s0, s1;
+        if constexpr (XM == S1_NONE) {
+            s0 = y0;
+            s1 = y1;
+        } else if constexpr (YM == S1_NONE) {
+            s0 = x0;
+            s1 = x1;
+        } else {
+            s0 = h2_add(x0, y0);
+            s1 = h2_add(x1, y1);
+        }
+        s1_mfma(A[0], A[1], A[2], A[3], r0, r1, s0, s1);
+    } else {
+        uint64_t x0 = 0ull, x1 = 0ull, y0 = 0ull, y1 = 0ull;
+        if (XM != S1_NONE && hx) {
+            x0 = s1_ld<TS>(row + ox);
+            x1 = s1_ld<TS>(row + ox + RS);
+        }
+        if (YM != S1_NONE && hy) {
+            y0 = s1_ld<TS>(row + oy);
+            y1 = s1_ld<TS>(row + oy + RS);
+        }
+        uint64_t s0, s1;
+        if constexpr (XM == S1_NONE) {
+            s0 = y0;
+            s1 = y1;
+        } else if constexpr (YM == S1_NONE) {
+            s0 = x0;
+            s1 = x1;
+        } else {
+            s0 = f2_add(x0, y0);
+            s1 = f2_add(x1, y1);
+        }
+        const float2 u = f2_unpack(s0), v = f2_unpack(s1);
+        const float fax = __uint_as_float(r0), fbx = __uint_as_float(r1);
+        const float fay = __uint_as_float(r2), fby = __uint_as_float(r3);
+        A[0] = fmaf(fax, u.x, fmaf(fbx, v.x, A[0]));
+        A[1] = fmaf(fax, u.y, fmaf(fbx, v.y, A[1]));
+        A[2] = fmaf(fay, u.x, fmaf(fby, v.x, A[2]));
+        A[3] = fmaf(fay, u.y, fmaf(fby, v.y, A[3]));
+    }
+}
+
 // One range [d0, d1) of lateral distances with fixed modes for the two mirror
 // elements: S1_FULL (every lane has the element), S1_PRED (some do: the others
 // load zeros), S1_NONE (no lane does: skipped).  nrow: rows of this thread
 // (MAXR when EXACT).  H[j] = {A1.x, A1.y, A2.x, A2.y}: sums of the
-// Re-weight and Im-weight products of row j.
-template <typename TS, int MAXR, bool EXACT, int XM, int YM>
-__device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
-                                             int d1, int cz, int zt, int l, int Lx, int Ly, int row0, int nrow,
-                                             unsigned rbase, unsigned obase, unsigned wbase, int RS)
+// Re-weight and Im-weight products of row j for pixel l.
+// PAIR: the thread also owns the mirror pixel m = N - 1 - l, whose elements
+// m - d and m + d exist exactly when l + d and l - d do, so it runs in the
+// same range with the modes swapped and accumulates into G; each record read
+// then serves both pixels.
+template <typename TS, int MAXR, bool EXACT, bool PAIR, int XM, int YM>
+__device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], float (&G)[MAXR][4], int d0, int d1, int cz, int zt,
+                                             int l, int m, int Lx, int Ly, int row0, int nrow, unsigned rbase,
+                                             unsigned obase, unsigned wbase, int RS)
 {
     constexpr bool HALF = S1Rec<TS>::HALF;
     constexpr int RB = S1Rec<TS>::BYTES, ESZ = (int)sizeof(TS);
@@ -326,40 +393,19 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
         const bool hy = YM == S1_FULL || (YM == S1_PRED && d <= Ly);
         // window offsets of the two mirror elements (records hold the row offset)
         const unsigned ox = wbase + (unsigned)((l - d) * ESZ), oy = wbase + (unsigned)((l + d) * ESZ);
-        const unsigned ox1 = ox + RS, oy1 = oy + RS;
+        const unsigned mx = wbase + (unsigned)((m - d) * ESZ), my = wbase + (unsigned)((m + d) * ESZ);
         const int base = (d - cz) * zt + row0;    // record index of the thread's first row
         const unsigned rp = rbase + base * RB, op = obase + base * 4;
         unsigned rowq[4];
 #pragma unroll
         for (int j = 0; j < MAXR; ++j) {
             if (EXACT || j < nrow) {
+                unsigned r0, r1, r2, r3, row;
                 if constexpr (HALF) {
-                    unsigned wr, wi, row, pad;
-                    lds_u32x4(rp + j * RB, wr, wi, row, pad);
-                    unsigned x0 = 0u, x1 = 0u, y0 = 0u, y1 = 0u;
-                    if (XM != S1_NONE && hx) {
-                        x0 = lds_u32(row + ox);
-                        x1 = lds_u32(row + ox1);
-                    }
-                    if (YM != S1_NONE && hy) {
-                        y0 = lds_u32(row + oy);
-                        y1 = lds_u32(row + oy1);
-                    }
-                    unsigned s0, s1;
-                    if constexpr (XM == S1_NONE) {
-                        s0 = y0;
-                        s1 = y1;
-                    } else if constexpr (YM == S1_NONE) {
-                        s0 = x0;
-                        s1 = x1;
-                    } else {
-                        s0 = h2_add(x0, y0);
-                        s1 = h2_add(x1, y1);
-                    }
-                    s1_mfma(H[j][0], H[j][1], H[j][2], H[j][3], wr, wi, s0, s1);
+                    lds_u32x4(rp + j * RB, r0, r1, row, r3);
+                    r2 = 0u;
                 } else {
-                    unsigned ax, bx, ay, by;
-                    lds_u32x4(rp + j * RB, ax, bx, ay, by);
+                    lds_u32x4(rp + j * RB, r0, r1, r2, r3);
                     // row addresses of four consecutive rows in one load (16-byte
                     // aligned: the thread's first row and zt are multiples of 4)
                     constexpr bool QUAD = EXACT && MAXR >= 4;
@@ -370,35 +416,10 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
                             rowq[0] = lds_u32(op + j * 4);
                     }
                     // FP32-weight records hold offsets for 8-byte samples: halve for 4-byte ones
-                    const unsigned row = rowq[QUAD ? (j & 3) : 0] >> (ESZ == 4 ? 1 : 0);
-                    uint64_t x0 = 0ull, x1 = 0ull, y0 = 0ull, y1 = 0ull;
-                    if (XM != S1_NONE && hx) {
-                        x0 = s1_ld<TS>(row + ox);
-                        x1 = s1_ld<TS>(row + ox1);
-                    }
-                    if (YM != S1_NONE && hy) {
-                        y0 = s1_ld<TS>(row + oy);
-                        y1 = s1_ld<TS>(row + oy1);
-                    }
-                    uint64_t s0, s1;
-                    if constexpr (XM == S1_NONE) {
-                        s0 = y0;
-                        s1 = y1;
-                    } else if constexpr (YM == S1_NONE) {
-                        s0 = x0;
-                        s1 = x1;
-                    } else {
-                        s0 = f2_add(x0, y0);
-                        s1 = f2_add(x1, y1);
-                    }
-                    const float2 u = f2_unpack(s0), v = f2_unpack(s1);
-                    const float fax = __uint_as_float(ax), fbx = __uint_as_float(bx);
-                    const float fay = __uint_as_float(ay), fby = __uint_as_float(by);
-                    H[j][0] = fmaf(fax, u.x, fmaf(fbx, v.x, H[j][0]));
-                    H[j][1] = fmaf(fax, u.y, fmaf(fbx, v.y, H[j][1]));
-                    H[j][2] = fmaf(fay, u.x, fmaf(fby, v.x, H[j][2]));
-                    H[j][3] = fmaf(fay, u.y, fmaf(fby, v.y, H[j][3]));
+                    row = rowq[QUAD ? (j & 3) : 0] >> (ESZ == 4 ? 1 : 0);
                 }
+                s1_pixel<TS, XM, YM>(H[j], row, ox, oy, RS, hx, hy, r0, r1, r2, r3);
+                if constexpr (PAIR) s1_pixel<TS, YM, XM>(G[j], row, mx, my, RS, hy, hx, r0, r1, r2, r3);
             }
         }
     }
@@ -406,10 +427,11 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], int d0,
 
 // Returns false if a bounded wait ran out (the CTA must stop).  The thread
 // owns rows [rg * per, rg * per + per) of the tile, per = ceil(zt / RG)
-// (per <= MAXR; EXACT: per == MAXR and zt == RG * MAXR, or MAXR == 1).
+// (per <= MAXR; EXACT: per == MAXR and zt == RG * MAXR, or MAXR == 1), and
+// pixel l (plus N - 1 - l when PAIR).
 // rtab: the plan's record table for this arithmetic (FP16 weights for FP16
 // samples, FP32 weights otherwise), one block of rblk bytes per chunk.
-template <typename TS, int MAXR, bool EXACT>
+template <typename TS, int MAXR, bool EXACT, bool PAIR = false>
 __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned char* __restrict__ smraw,
                                             uint64_t* bars, const GeomDev& g, const void* __restrict__ iq,
                                             const unsigned char* __restrict__ rtab, int rblk,
@@ -424,11 +446,12 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
     unsigned char* recs = bufs + 2 * (size_t)win * RS;        // [2][rblk]
     const int nt = 2 * g.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int LW = (N + 31) >> 5;
+    const int LW = PAIR ? N >> 6 : (N + 31) >> 5;
     const int RG = (blockDim.x >> 5) / LW;
     const int lw = warp % LW, rg = warp / LW;
     const int lb = lw * 32;
     const int l = lb + lane;
+    const int m = N - 1 - l;                                   // mirror pixel (PAIR)
     const int per = (zt + RG - 1) / RG;
     const int row0 = rg * per;                                 // first tile row of this thread
     const int nrow = max(0, min(per, zt - row0));
@@ -470,11 +493,16 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
         }
     };
 
-    // H[j] = {A1.x, A1.y, A2.x, A2.y}; slice value = (A1.x - A2.y, A1.y + A2.x)
-    float H[MAXR][4];
+    // H[j] = {A1.x, A1.y, A2.x, A2.y} of pixel l (G[j]: of pixel m);
+    // slice value = (A1.x - A2.y, A1.y + A2.x)
+    float H[MAXR][4], G[MAXR][4];
 #pragma unroll
-    for (int j = 0; j < MAXR; ++j) H[j][0] = H[j][1] = H[j][2] = H[j][3] = 0.f;
+    for (int j = 0; j < MAXR; ++j) {
+        H[j][0] = H[j][1] = H[j][2] = H[j][3] = 0.f;
+        G[j][0] = G[j][1] = G[j][2] = G[j][3] = 0.f;
+    }
     // per-lane reach of the mirror elements: l - d needs d <= Lx, l + d needs d <= Ly
+    // (for the mirror pixel m the two swap: m - d needs d <= Ly, m + d needs d <= Lx)
     const int Lx = l < N ? l : -1;
     const int Ly = N - 1 - l;
     // warp-uniform range limits: x (e = l - d) for every lane up to xf, for some up to xe;
@@ -506,7 +534,8 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
             if (yf + 1 > d) nx = min(nx, yf + 1);
             if (ye + 1 > d) nx = min(nx, ye + 1);
 #define RCA_S1_RANGE(XM, YM)                                                                                     \
-    stage1_range<TS, MAXR, EXACT, XM, YM>(H, d, nx, cc.z, zt, l, Lx, Ly, row0, nrow, rbase, obase, wbase, RS)
+    stage1_range<TS, MAXR, EXACT, PAIR, XM, YM>(H, G, d, nx, cc.z, zt, l, m, Lx, Ly, row0, nrow, rbase, obase, wbase, \
+                                                RS)
             switch (xm * 3 + ym) {
             case S1_FULL * 3 + S1_FULL: RCA_S1_RANGE(S1_FULL, S1_FULL); break;
             case S1_FULL * 3 + S1_PRED: RCA_S1_RANGE(S1_FULL, S1_PRED); break;
@@ -522,11 +551,14 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
             d = nx;
         }
     }
+    float2* out = slices + ((size_t)f * nt + k) * g.nzs * N;
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) {
         const int r = r0 + row0 + j;
-        if ((EXACT || j < nrow) && r < rend && l < N)
-            slices[(((size_t)f * nt + k) * g.nzs + r) * N + l] = make_float2(H[j][0] - H[j][3], H[j][1] + H[j][2]);
+        if ((EXACT || j < nrow) && r < rend && l < N) {
+            out[(size_t)r * N + l] = make_float2(H[j][0] - H[j][3], H[j][1] + H[j][2]);
+            if (PAIR) out[(size_t)r * N + m] = make_float2(G[j][0] - G[j][3], G[j][1] + G[j][2]);
+        }
     }
     return true;
 }

@@ -138,6 +138,33 @@ struct rca_tables {
 };
 
 // Stage-2 CTA geometry (shared by the planner and the kernels)
+// Thread layout of a Stage-1 CTA (256 threads): LW warps across the lateral
+// pixels times RG row groups of `per` rows each.  Paired (N a multiple of 64,
+// at most 8 rows per thread): a lane owns pixel l < N / 2 and its mirror
+// N - 1 - l, so LW = N / 64; otherwise one pixel per lane, LW = ceil(N / 32).
+struct S1Layout {
+    int LW, RG, per;
+    bool pair;
+};
+__host__ __device__ inline S1Layout stage1_layout(int N, int zt, bool allow_pair)
+{
+    S1Layout s;
+    s.pair = false;
+    if (allow_pair && N % 64 == 0 && N <= 512) {
+        s.LW = N / 64;
+        s.RG = s.LW >= 8 ? 1 : 8 / s.LW;
+        s.per = (zt + s.RG - 1) / s.RG;
+        if (s.per <= 8) {
+            s.pair = true;
+            return s;
+        }
+    }
+    s.LW = (N + 31) / 32;
+    s.RG = s.LW >= 8 ? 1 : 8 / s.LW;
+    s.per = (zt + s.RG - 1) / s.RG;
+    return s;
+}
+
 #define S2_ZP 16       // plane rows per CTA (at most)
 #define S2_THREADS 256
 
