@@ -656,7 +656,7 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.dc = t->s1.dc;
         E.n_tiles = t->s1.n_tiles;
         E.nch = t->s1.nch;
-        E.win = t->s1.win;
+        E.ring = t->s1.ring;
         E.mix = t->mix;
         E.sfl = t->s2_sfl;
         E.sfr = t->s2_sfr;
@@ -698,7 +698,7 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         maxr = std::max(maxr, (E.zt + RG - 1) / RG);
         tmax = std::max(tmax, t->T);
         tmin_all = std::min(tmin_all, t->T);
-        smem = std::max(smem, stage1_smem_bytes(t, E.zt, E.dc, E.win, esz));
+        smem = std::max(smem, stage1_smem_bytes(t, E.zt, E.dc, E.ring, esz));
         smem = std::max(smem, stage2_smem_bytes(t, E.zp));
         if (prm) {
             b->A.push_back((float*)alloc((size_t)F * 2 * g.S * g.nz * g.N * 4));
@@ -924,8 +924,8 @@ extern "C" rca_status rca_autotune(rca_handle* h, rca_tables* t, const void* iq,
     int bz = t->s1.zt, bd = t->s1.dc;
     for (auto& sh : shapes) {
         const int zt = sh[0], dc = sh[1];
-        const int win = stage1_window(t, zt, dc, nullptr);
-        if (stage1_smem_bytes(t, zt, dc, win, esz) > 200 * 1024) continue;
+        const int ring = stage1_ring(t, zt, dc, nullptr, nullptr);
+        if (stage1_smem_bytes(t, zt, dc, ring, esz) > 200 * 1024) continue;
         if (stage1_layout(g.N, zt, true).per > 16) continue;
         if ((st = plan_stage1(h, t, zt, dc)) != RCA_OK) break;
         const float ms = time_it([&] { launch_stage1(h, t, iq, iq_t, F, slices); });

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
                 demod_body<RCA_I16>(a0, a1, a2, xs, E.rf, E.scale, E.mean, E.mix, fir, nt, g.N, g.ns, E.iq, iq_t);
         } else if (stage == BS_STAGE1) {
             ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.rtab, E.rblk, E.dmax, E.chunks,
-                                              E.zt, E.dc, E.n_tiles, E.nch, E.win, E.slices, status);
+                                              E.zt, E.dc, E.n_tiles, E.nch, E.ring, E.slices, status);
         } else {
             ok = stage2_body<TM>(a0, a1 >> 1, a1 & 1, a2, smraw, &bars[0], g, E.slices, E.sfl, E.sfr, E.psi, E.ec,
                                  E.coef, E.c2, E.tmin, E.T, E.iA, E.iB, E.zp, E.rows, E.smin0, E.smin1, E.planes, pt,

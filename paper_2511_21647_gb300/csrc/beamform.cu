@@ -26,13 +26,13 @@ template <typename TS, int MAXR, bool PAIR>
 __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __restrict__ iq,
                                                 const unsigned char* __restrict__ rtab, int rblk,
                                                 const int* __restrict__ dmax, const int4* __restrict__ chunks, int zt,
-                                                int dc, int n_tiles, int nch, int win, float2* __restrict__ slices,
+                                                int dc, int n_tiles, int nch, int ring, float2* __restrict__ slices,
                                                 unsigned* __restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bars[2];
     stage1_body<TS, MAXR, true, PAIR>(blockIdx.x, blockIdx.y, blockIdx.z, smraw, bars, g, iq, rtab, rblk, dmax, chunks, zt,
-                                dc, n_tiles, nch, win, slices, status);
+                                dc, n_tiles, nch, ring, slices, status);
 }
 
 template <int TM>
@@ -197,14 +197,14 @@ static rca_status stage1_launch(rca_handle* h, const rca_tables* t, const void* 
 {
     const GeomDev& g = t->gd;
     const Stage1Plan& p = t->s1;
-    const size_t smem = stage1_smem_bytes(t, p.zt, p.dc, p.win, sizeof(TS));
+    const size_t smem = stage1_smem_bytes(t, p.zt, p.dc, p.ring, sizeof(TS));
     auto kern = k_stage1<TS, MAXR, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage1 smem attribute");
     dim3 grid(p.n_tiles, 2 * g.K, F);
     const unsigned char* rtab = std::is_same<TS, __half2>::value ? p.d_rec16 : p.d_rec32;
     kern<<<grid, threads, smem, h->stream>>>(g, iq, rtab, p.rblk, t->dmax, p.d_chunks, p.zt, p.dc, p.n_tiles, p.nch,
-                                             p.win, slices, h->d_status);
+                                             p.ring, slices, h->d_status);
     return cuda_check(h, cudaGetLastError(), "stage1 kernel");
 }
 

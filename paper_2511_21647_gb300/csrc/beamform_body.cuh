@@ -436,14 +436,14 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
                                             uint64_t* bars, const GeomDev& g, const void* __restrict__ iq,
                                             const unsigned char* __restrict__ rtab, int rblk,
                                             const int* __restrict__ dmax, const int4* __restrict__ chunks, int zt,
-                                            int dc, int n_tiles, int nch, int win, float2* __restrict__ slices,
+                                            int dc, int n_tiles, int nch, int ring, float2* __restrict__ slices,
                                             unsigned* __restrict__ status)
 {
     constexpr int ESZ = (int)sizeof(TS);
     const int E = g.N, N = g.N;
-    const int RS = E * ESZ;                                   // window row (bytes)
-    unsigned char* bufs = smraw;                              // [2][win][RS]
-    unsigned char* recs = bufs + 2 * (size_t)win * RS;        // [2][rblk]
+    const int RS = E * ESZ;                                   // sample row (bytes)
+    unsigned char* rng = smraw;                               // [ring + 1][RS]
+    unsigned char* recs = rng + (size_t)(ring + 1) * RS;      // [2][rblk]
     const int nt = 2 * g.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int LW = PAIR ? N >> 6 : (N + 31) >> 5;
@@ -472,23 +472,41 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
     }
     __syncthreads();
 
-    // zero the window rows outside the record, then (thread 0) bulk-copy the
-    // rest and the chunk's record block on one barrier
+    // fetch the rows of chunk c that are not resident: [a, a + cnt) into ring
+    // slots sa.. (wrapping to slot 0 after c1 rows); rows outside [0, ns) are
+    // zeroed by all threads, the rest bulk-copied by thread 0 with the
+    // chunk's record block on one barrier.  The row in slot 0 is also
+    // written to slot `ring`.
     auto issue = [&](int c, int b) {
         const int4 cc = ch[c];
-        unsigned char* dst = bufs + (size_t)b * win * RS;
-        const int lo = max(cc.x, 0), hi = max(lo, min(cc.x + cc.y, g.ns));
-        const int z0 = min(lo - cc.x, cc.y), z1 = hi - cc.x;
+        const int a = cc.x, cnt = cc.y & 0xffff, sa = cc.y >> 16;
+        const int c1 = min(cnt, ring - sa);
         const int v16 = RS / 16;
-        for (int idx = threadIdx.x; idx < z0 * v16; idx += blockDim.x)
-            reinterpret_cast<uint4*>(dst)[idx] = make_uint4(0u, 0u, 0u, 0u);
-        for (int idx = threadIdx.x; idx < (cc.y - z1) * v16; idx += blockDim.x)
-            reinterpret_cast<uint4*>(dst + (size_t)z1 * RS)[idx] = make_uint4(0u, 0u, 0u, 0u);
+        if (a < 0 || a + cnt > g.ns) {
+            for (int idx = threadIdx.x; idx < cnt * v16; idx += blockDim.x) {
+                const int q = idx / v16, u = idx - q * v16, n = a + q;
+                if (n >= 0 && n < g.ns) continue;
+                const int sl = q < c1 ? sa + q : q - c1;
+                reinterpret_cast<uint4*>(rng + (size_t)sl * RS)[u] = make_uint4(0u, 0u, 0u, 0u);
+                if (sl == 0) reinterpret_cast<uint4*>(rng + (size_t)ring * RS)[u] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
         if (threadIdx.x == 0) {
             fence_proxy_async();
-            const unsigned bytes = (unsigned)((hi - lo) * RS);
+            // in-sample parts of the two runs, and the row that lands in slot 0
+            const int lo1 = max(a, 0), hi1 = max(lo1, min(a + c1, g.ns));
+            const int lo2 = max(a + c1, 0), hi2 = max(lo2, min(a + cnt, g.ns));
+            const int n0 = c1 < cnt ? a + c1 : (sa == 0 && cnt > 0 ? a : -1);
+            const bool dup = n0 >= 0 && n0 < g.ns;
+            const unsigned bytes = (unsigned)((hi1 - lo1) + (hi2 - lo2) + (dup ? 1 : 0)) * (unsigned)RS;
             mbar_arrive_expect_tx(&bars[b], bytes + (unsigned)rblk);
-            if (bytes) bulk_g2s(dst + (size_t)(lo - cc.x) * RS, blk + (size_t)lo * RS, bytes, &bars[b]);
+            if (hi1 > lo1)
+                bulk_g2s(rng + (size_t)(sa + lo1 - a) * RS, blk + (size_t)lo1 * RS, (unsigned)((hi1 - lo1) * RS),
+                         &bars[b]);
+            if (hi2 > lo2)
+                bulk_g2s(rng + (size_t)(lo2 - (a + c1)) * RS, blk + (size_t)lo2 * RS, (unsigned)((hi2 - lo2) * RS),
+                         &bars[b]);
+            if (dup) bulk_g2s(rng + (size_t)ring * RS, blk + (size_t)n0 * RS, (unsigned)RS, &bars[b]);
             bulk_g2s(recs + (size_t)b * rblk, rsrc + (size_t)c * rblk, (unsigned)rblk, &bars[b]);
         }
     };
@@ -517,8 +535,8 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
         if (!cta_wait_copies(&bars[b], (phase >> b) & 1u, status)) return false;
         phase ^= 1u << b;
         if (c + 1 < nch) issue(c + 1, b ^ 1);
-        if (cc.y == 0 || nrow == 0) continue;
-        const unsigned wbase = smem_u32(bufs + (size_t)b * win * RS);
+        if (cc.w <= cc.z || nrow == 0) continue;
+        const unsigned wbase = smem_u32(rng);
         const unsigned rbase = smem_u32(recs + (size_t)b * rblk);
         const unsigned obase = rbase + (unsigned)(zt * dc * 16);
         // the thread's rows advance together: each d step updates its rows'

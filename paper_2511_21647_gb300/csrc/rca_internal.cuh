@@ -80,10 +80,13 @@ struct Stage1Plan {
     int dc = 0;               // lateral distances per chunk
     int n_tiles = 0;
     int nch = 0;              // chunks per tile
-    int win = 0;              // max nrows over all chunks
-    int4* d_chunks = nullptr; // [2K][n_tiles][nch] {nlo, nrows, d0, d1}
+    int ring = 0;             // sample rows of the shared-memory ring (plus one duplicate row)
+    // [2K][n_tiles][nch] {first new sample row n, new row count | ring slot of n << 16, d0, d1}:
+    // the rows a chunk needs that earlier chunks of its tile did not load; d1 == d0 for a
+    // chunk without work
+    int4* d_chunks = nullptr;
     // per-(d, row) weight records of every chunk, one block of rblk bytes per
-    // (k, tile, chunk): [dc][zt] 16-byte records, then [dc][zt] window byte
+    // (k, tile, chunk): [dc][zt] 16-byte records, then [dc][zt] ring byte
     // offsets.  rec32: FP32 weights, offsets for 8-byte samples (4-byte
     // samples use half of them); rec16: FP16 weights, offsets for 4-byte samples.
     int rblk = 0;
@@ -193,8 +196,8 @@ inline __host__ __device__ size_t s2_smem_bytes(int K, int S, int N, int P, int 
 
 
 // launch-shape planning (tables.cu)
-int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* chunks);
-size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t esz);
+int stage1_ring(const rca_tables* t, int zt, int dc, std::vector<int4>* chunks, std::vector<int>* bases);
+size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int ring, size_t esz);
 rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc);
 size_t stage2_smem_bytes(const rca_tables* t, int zp);
 void plan_stage2(rca_tables* t, int zp);
@@ -458,7 +461,7 @@ struct BatchEns {
     const int4* chunks;
     const unsigned char* rtab;  // Stage-1 record table for the batch's IQ dtype
     int rblk;
-    int zt, dc, n_tiles, nch, win;
+    int zt, dc, n_tiles, nch, ring;
     const float2* mix;
     const int* sfl;
     const float* sfr;

@@ -347,7 +347,7 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     for (auto& sh : shapes) {
         zt = sh[0];
         dc = sh[1];
-        if (stage1_smem_bytes(t, zt, dc, stage1_window(t, zt, dc, nullptr), sizeof(float2)) <= budget) break;
+        if (stage1_smem_bytes(t, zt, dc, stage1_ring(t, zt, dc, nullptr, nullptr), sizeof(float2)) <= budget) break;
     }
     if ((st = plan_stage1(h, t, zt, dc)) != RCA_OK) return st;
     // Stage 2: the tallest plane-row tile that fits the same budget
@@ -387,17 +387,27 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
 // launch-shape planning from the host copies of the tables
 // ---------------------------------------------------------------------------
 // Stage-1 chunks: row tiles of zt slice rows, lateral distances in chunks of
-// dc; each chunk's sample window is contiguous in the [ns][E] IQ block.
-// Returns the largest window (rows); fills chunks {nlo, nrows, d0, d1}.
-int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* out)
+// dc.  A chunk needs the contiguous sample rows [lo, hi] of the [ns][E] IQ
+// block (its delays' integer parts plus the interpolation neighbour); lo and
+// hi only grow from one chunk of a tile to the next.  The CTA keeps the rows
+// in a ring of R rows: sample row n sits in slot (n - base) mod R (base: the
+// tile's first row), and while chunk c runs, the rows of chunk c + 1 that
+// are not resident yet are fetched into slots that chunk c does not read.
+// That holds when R >= hi(c + 1) - lo(c) + 1 for consecutive chunks with
+// work; R is the largest such span over all tiles.  Slot R repeats slot 0,
+// so that a row and its successor are always R-adjacent.
+// Returns R; fills the chunk table and the per-(k, tile) base rows.
+int stage1_ring(const rca_tables* t, int zt, int dc, std::vector<int4>* out, std::vector<int>* bases)
 {
     const GeomDev& g = t->gd;
     const int nt = 2 * g.K;
     const int tiles = (g.nzs + zt - 1) / zt, nch = (g.N + dc - 1) / dc;
-    int win = 0;
-    if (out) out->assign((size_t)nt * tiles * nch, make_int4(0, 0, 0, 0));
+    std::vector<long> lo_v((size_t)nt * tiles * nch), hi_v((size_t)nt * tiles * nch);
+    int R = 1;
     for (int k = 0; k < nt; ++k)
-        for (int tt = 0; tt < tiles; ++tt)
+        for (int tt = 0; tt < tiles; ++tt) {
+            long plo = 0;
+            bool prev = false;
             for (int c = 0; c < nch; ++c) {
                 const int d0 = c * dc, d1 = std::min(g.N, d0 + dc);
                 long lo = 1L << 40, hi = -(1L << 40);
@@ -405,23 +415,57 @@ int stage1_window(const rca_tables* t, int zt, int dc, std::vector<int4>* out)
                     if (t->h_dm[r] < d0) continue;
                     const long tq = t->h_txq[(size_t)k * g.nzs + r];
                     lo = std::min(lo, (tq + t->h_rxq[(size_t)r * g.N + d0]) >> 16);
-                    hi = std::max(hi, (tq + t->h_rxq[(size_t)r * g.N + std::min(d1 - 1, t->h_dm[r])]) >> 16);
+                    hi = std::max(hi, ((tq + t->h_rxq[(size_t)r * g.N + std::min(d1 - 1, t->h_dm[r])]) >> 16) + 1);
                 }
-                const int nrows = hi >= lo ? (int)(hi - lo + 2) : 0;
-                win = std::max(win, nrows);
-                if (out) (*out)[((size_t)k * tiles + tt) * nch + c] = make_int4((int)lo, nrows, d0, d1);
+                const size_t i = ((size_t)k * tiles + tt) * nch + c;
+                lo_v[i] = lo;
+                hi_v[i] = hi;
+                if (hi < lo) continue;
+                R = std::max(R, (int)(hi - lo + 1));
+                if (prev) R = std::max(R, (int)(hi - plo + 1));
+                plo = lo;
+                prev = true;
             }
-    return win;
+        }
+    if (out) out->assign((size_t)nt * tiles * nch, make_int4(0, 0, 0, 0));
+    if (bases) bases->assign((size_t)nt * tiles, 0);
+    if (!out) return R;
+    for (int k = 0; k < nt; ++k)
+        for (int tt = 0; tt < tiles; ++tt) {
+            bool first = true;
+            long base = 0, top = 0;           // top: last resident row
+            for (int c = 0; c < nch; ++c) {
+                const size_t i = ((size_t)k * tiles + tt) * nch + c;
+                const int d0 = c * dc, d1 = std::min(g.N, d0 + dc);
+                const long lo = lo_v[i], hi = hi_v[i];
+                if (hi < lo) {
+                    (*out)[i] = make_int4(0, 0, d0, d0);
+                    continue;
+                }
+                if (first) {
+                    base = lo;
+                    top = lo - 1;
+                    first = false;
+                }
+                const long a = std::max(lo, top + 1);
+                const int cnt = (int)std::max(0L, hi - a + 1);
+                const int slot = (int)((a - base) % R);
+                (*out)[i] = make_int4((int)a, cnt | (slot << 16), d0, d1);
+                top = std::max(top, hi);
+            }
+            if (bases) (*bases)[(size_t)k * tiles + tt] = (int)base;
+        }
+    return R;
 }
 
 // bytes of one chunk's record block: [dc][zt] 16-byte records + [dc][zt]
-// 4-byte window offsets, rounded up to 16 (a TMA bulk copy unit)
+// 4-byte ring offsets, rounded up to 16 (a TMA bulk copy unit)
 static int stage1_rblk(int zt, int dc) { return ((zt * dc * 20) + 15) / 16 * 16; }
 
 // double-buffered sample windows and record blocks
-size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t esz)
+size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int ring, size_t esz)
 {
-    return 2 * (size_t)win * t->gd.N * esz + 2 * (size_t)stage1_rblk(zt, dc);
+    return (size_t)(ring + 1) * t->gd.N * esz + 2 * (size_t)stage1_rblk(zt, dc);
 }
 
 // Stage-1 records of every (k, tile, chunk): one thread per (d, row) slot.
@@ -429,13 +473,13 @@ size_t stage1_smem_bytes(const rca_tables* t, int zt, int dc, int win, size_t es
 // 4-byte samples; otherwise FP32 {Re a, Re b, Im a, Im b} with the offsets
 // (for 8-byte samples) in the block's second array.  a = w (1 - fr),
 // b = w fr, halved at d = 0 (the two mirror elements coincide there); zero
-// where the distance is outside the row's aperture or the delay leaves the
-// record.
+// (and offset 0, a slot the tile's first chunk fills) where the distance is
+// outside the row's aperture or the delay leaves the record.
 template <bool HALF>
 __global__ void k_s1_records(GeomDev g, const int* __restrict__ tx_q16, const int* __restrict__ rx_q16,
                              const float2* __restrict__ W, const int* __restrict__ dmax,
-                             const int4* __restrict__ chunks, int zt, int dc, int n_tiles, int nch, int rblk,
-                             unsigned char* __restrict__ out)
+                             const int4* __restrict__ chunks, const int* __restrict__ bases, int ring, int zt,
+                             int dc, int n_tiles, int nch, int rblk, unsigned char* __restrict__ out)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int per_blk = zt * dc;
@@ -461,7 +505,7 @@ __global__ void k_s1_records(GeomDev g, const int* __restrict__ tx_q16, const in
             bx = h * w.x * fr;
             ay = h * w.y * (1.0f - fr);
             by = h * w.y * fr;
-            off = ((q >> 16) - cc.x) * RS;
+            off = (((q >> 16) - bases[cb / nch]) % ring) * RS;
         }
     }
     unsigned char* blk = out + cb * rblk;
@@ -480,19 +524,24 @@ __global__ void k_s1_records(GeomDev g, const int* __restrict__ tx_q16, const in
 rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
 {
     std::vector<int4> chunks;
-    const int win = stage1_window(t, zt, dc, &chunks);
-    if (stage1_smem_bytes(t, zt, dc, win, sizeof(float2)) > 200 * 1024)
-        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 sample window of %d samples x %d elements exceeds shared memory",
-                         win, t->gd.N);
-    int4* d = nullptr;
+    std::vector<int> bases;
+    const int ring = stage1_ring(t, zt, dc, &chunks, &bases);
+    if (stage1_smem_bytes(t, zt, dc, ring, sizeof(float2)) > 200 * 1024)
+        return set_error(h, RCA_ERR_UNSUPPORTED, "Stage-1 sample ring of %d samples x %d elements exceeds shared memory",
+                         ring, t->gd.N);
     rca_status st = RCA_OK;
-    d = dalloc<int4>(h, chunks.size(), &st);
-    if (st != RCA_OK) return st;
-    st = cuda_check(h, cudaMemcpyAsync(d, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream),
-                    "chunk upload");
+    int4* d = dalloc<int4>(h, chunks.size(), &st);
+    int* db = st == RCA_OK ? dalloc<int>(h, bases.size(), &st) : nullptr;
+    if (st == RCA_OK)
+        st = cuda_check(h, cudaMemcpyAsync(d, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                           h->stream), "chunk upload");
+    if (st == RCA_OK)
+        st = cuda_check(h, cudaMemcpyAsync(db, bases.data(), bases.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                           h->stream), "ring base upload");
     if (st == RCA_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "chunk upload sync");
     if (st != RCA_OK) {
-        cudaFree(d);
+        if (d) cudaFree(d);
+        if (db) cudaFree(db);
         return st;
     }
     const int n_tiles = (t->gd.nzs + zt - 1) / zt, nch = (t->gd.N + dc - 1) / dc;
@@ -502,17 +551,19 @@ rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
     unsigned char* r16 = st == RCA_OK ? dalloc<unsigned char>(h, nblk * rblk, &st) : nullptr;
     if (st != RCA_OK) {
         cudaFree(d);
+        cudaFree(db);
         if (r32) cudaFree(r32);
         return st;
     }
     const long long slots = (long long)nblk * zt * dc;
     const unsigned grid = (unsigned)((slots + 255) / 256);
-    k_s1_records<false><<<grid, 256, 0, h->stream>>>(t->gd, t->tx_q16, t->rx_q16, t->W, t->dmax, d, zt, dc, n_tiles,
-                                                      nch, rblk, r32);
-    k_s1_records<true><<<grid, 256, 0, h->stream>>>(t->gd, t->tx_q16, t->rx_q16, t->W, t->dmax, d, zt, dc, n_tiles,
-                                                     nch, rblk, r16);
+    k_s1_records<false><<<grid, 256, 0, h->stream>>>(t->gd, t->tx_q16, t->rx_q16, t->W, t->dmax, d, db, ring, zt, dc,
+                                                      n_tiles, nch, rblk, r32);
+    k_s1_records<true><<<grid, 256, 0, h->stream>>>(t->gd, t->tx_q16, t->rx_q16, t->W, t->dmax, d, db, ring, zt, dc,
+                                                     n_tiles, nch, rblk, r16);
     st = cuda_check(h, cudaGetLastError(), "Stage-1 record kernels");
     if (st == RCA_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "Stage-1 record build");
+    cudaFree(db);
     if (st != RCA_OK) {
         cudaFree(d);
         cudaFree(r32);
@@ -528,7 +579,7 @@ rca_status plan_stage1(rca_handle* h, rca_tables* t, int zt, int dc)
     t->s1.rblk = rblk;
     t->s1.zt = zt;
     t->s1.dc = dc;
-    t->s1.win = win;
+    t->s1.ring = ring;
     t->s1.n_tiles = n_tiles;
     t->s1.nch = nch;
     return RCA_OK;

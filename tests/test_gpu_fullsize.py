@@ -113,7 +113,33 @@ def test_paired_beamform_end_to_end(paired):
     ratio = e / np.maximum(n, 1e-2 * n.max())
     q = int(np.argmax(ratio))
     print(f"\nn_el {g.n_el}: worst plane error {ratio[q]:.2e} (plane norm {n[q] / n.max():.1e} of the largest)")
+    _plane_report(n, e)
     assert ratio.max() < TOL_FP32
+
+
+def _plane_report(n, e):
+    """per-plane absolute error against the largest plane norm, by plane size"""
+    o = np.argsort(n)
+    ea = e / n.max()
+    for lab, sel in (("smallest", o[:8]), ("largest", o[-8:])):
+        print(f"  {lab:8s} planes: norm/max {np.array2string(n[sel] / n.max(), precision=1)}")
+        print(f"  {'':8s}   err/max {np.array2string(ea[sel], precision=1)}")
+    print(f"  err/max over all planes: median {np.median(ea):.1e}, max {ea.max():.1e} (plane {int(np.argmax(ea))})")
+
+
+def test_paired_stage2_on_oracle_slices(paired):
+    """Stage 2 + projection alone at 64 / 128 elements, on the oracle's slices
+    rounded to complex64, against the oracle's projection of the same slices."""
+    g, s, _, _, sl_o, _ = paired
+    sl32 = sl_o.astype(np.complex64)
+    ref = np.stack([O.stage2_project(g, sl32[f].astype(np.complex128)) for f in range(sl32.shape[0])])
+    pl = as_c128(s.stage2(c_tensor(sl32)))
+    assert s.sync_status() == 0
+    assert rel(pl, ref) < 1e-5
+    n = np.linalg.norm(ref.reshape(-1, ref.shape[-2] * ref.shape[-1]), axis=1)
+    e = np.linalg.norm((pl - ref).reshape(n.size, -1), axis=1)
+    print(f"\nStage 2 alone, n_el {g.n_el}:")
+    _plane_report(n, e)
 
 
 # --- paper scale, sampled frames ---------------------------------------------------------
