@@ -698,6 +698,7 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         maxr = std::max(maxr, (E.zt + RG - 1) / RG);
         tmax = std::max(tmax, t->T);
         tmin_all = std::min(tmin_all, t->T);
+        if (g.us != 2) b->us2 = false;
         smem = std::max(smem, stage1_smem_bytes(t, E.zt, E.dc, E.ring, esz));
         smem = std::max(smem, stage2_smem_bytes(t, E.zp));
         if (prm) {

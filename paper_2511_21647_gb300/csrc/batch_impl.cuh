@@ -24,7 +24,7 @@ __device__ __forceinline__ int ld_acquire(const int* p)
 }
 
 
-template <typename TS, int MAXR, int TM>
+template <typename TS, int MAXR, int TM, int US>
 __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
                                                  int nseg, int total, int* __restrict__ cnt, int n_counters,
                                                  long long wait_limit, Fir fir, int rf_t, int iq_t, int pt,
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
             ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.rtab, E.rblk, E.dmax, E.chunks,
                                               E.zt, E.dc, E.n_tiles, E.nch, E.ring, E.slices, status);
         } else {
-            ok = stage2_body<TM>(a0, a1 >> 1, a1 & 1, a2, smraw, &bars[0], g, E.slices, E.sfl, E.sfr, E.psi, E.ec,
+            ok = stage2_body<TM, US>(a0, a1 >> 1, a1 & 1, a2, smraw, &bars[0], g, E.slices, E.sfl, E.sfr, E.psi, E.ec,
                                  E.coef, E.c2, E.tmin, E.T, E.iA, E.iB, E.zp, E.rows, E.smin0, E.smin1, E.planes, pt,
                                  status);
         }
@@ -166,10 +166,10 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
 // ---------------------------------------------------------------------------
 // batched launch
 // ---------------------------------------------------------------------------
-template <typename TS, int MAXR, int TM>
+template <typename TS, int MAXR, int TM, int US>
 static rca_status batch_launch(rca_handle* h, rca_batch* b)
 {
-    auto kern = k_batch<TS, MAXR, TM>;
+    auto kern = k_batch<TS, MAXR, TM, US>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     if (e != cudaSuccess) return cuda_check(h, e, "batch smem attribute");
     if (b->grid == 0) {
@@ -191,9 +191,10 @@ static rca_status batch_launch(rca_handle* h, rca_batch* b)
 template <typename TS, int MAXR>
 static rca_status batch_tm(rca_handle* h, rca_batch* b)
 {
-    // one tap count shared by every ensemble: exact, else the generic loop
-    if (b->tmax == 3 && b->tmin_all == 3) return batch_launch<TS, MAXR, 3>(h, b);
-    return batch_launch<TS, MAXR, 0>(h, b);
+    // one tap count and two slice rows per plane row in every ensemble: exact,
+    // else the generic loop
+    if (b->tmax == 3 && b->tmin_all == 3 && b->us2) return batch_launch<TS, MAXR, 3, 2>(h, b);
+    return batch_launch<TS, MAXR, 0, 0>(h, b);
 }
 
 template <typename TS>

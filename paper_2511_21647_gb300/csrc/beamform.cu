@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
                                 dc, n_tiles, nch, ring, slices, status);
 }
 
-template <int TM>
-__global__ void __launch_bounds__(S2_THREADS, 3) k_stage2(GeomDev g, const float2* __restrict__ slices,
+template <int TM, int US>
+__global__ void __launch_bounds__(S2_THREADS, 2) k_stage2(GeomDev g, const float2* __restrict__ slices,
                                                        const int* __restrict__ sfl, const float* __restrict__ sfr,
                                                        const float2* __restrict__ psi, const float2* __restrict__ ec,
                                                        const float2* __restrict__ coef, const float2* __restrict__ c2,
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(S2_THREADS, 3) k_stage2(GeomDev g, const float
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bar;
-    stage2_body<TM>(blockIdx.x, blockIdx.y, blockIdx.z & 1, blockIdx.z >> 1, smraw, &bar, g, slices, sfl, sfr, psi, ec,
+    stage2_body<TM, US>(blockIdx.x, blockIdx.y, blockIdx.z & 1, blockIdx.z >> 1, smraw, &bar, g, slices, sfl, sfr, psi, ec,
                     coef, c2, tmin, T, iA, iB, zp, rows, smin0, smin1, planes, pt, status);
 }
 
@@ -243,7 +243,7 @@ rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca
     return set_error(h, RCA_ERR_UNSUPPORTED, "iq dtype must be C32, C16F or C16BF");
 }
 
-template <int TM>
+template <int TM, int US>
 static rca_status stage2_launch(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes,
                                 rca_dtype pt)
 {
@@ -252,7 +252,7 @@ static rca_status stage2_launch(rca_handle* h, const rca_tables* t, const float2
     if (GW == 0) return set_error(h, RCA_ERR_UNSUPPORTED, "Stage 2 needs an even multiple of P (%d) up to 32", g.P);
     if (2 * (long long)F > 65535) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 32767 frames in one call");
     const size_t smem = stage2_smem_bytes(t, t->s2.zp);
-    auto kern = k_stage2<TM>;
+    auto kern = k_stage2<TM, US>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage2 smem attribute");
     dim3 grid(t->s2.n_tiles, (g.N + GW - 1) / GW, 2 * F);
@@ -265,11 +265,14 @@ static rca_status stage2_launch(rca_handle* h, const rca_tables* t, const float2
 rca_status launch_stage2(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes, rca_dtype pt)
 {
     if (!complex_dtype(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
-    // exact tap counts of the usual steering ranges; any other count runs the generic loop
-    if (t->T == 2) return stage2_launch<2>(h, t, slices, F, planes, pt);
-    if (t->T == 3) return stage2_launch<3>(h, t, slices, F, planes, pt);
-    if (t->T == 4) return stage2_launch<4>(h, t, slices, F, planes, pt);
-    return stage2_launch<0>(h, t, slices, F, planes, pt);
+    // exact tap counts of the usual steering ranges with two slice rows per
+    // plane row; any other combination runs the generic loop
+    if (t->gd.us == 2) {
+        if (t->T == 2) return stage2_launch<2, 2>(h, t, slices, F, planes, pt);
+        if (t->T == 3) return stage2_launch<3, 2>(h, t, slices, F, planes, pt);
+        if (t->T == 4) return stage2_launch<4, 2>(h, t, slices, F, planes, pt);
+    }
+    return stage2_launch<0, 0>(h, t, slices, F, planes, pt);
 }
 
 template <int MAXR>

