@@ -301,7 +301,7 @@ def main():
                 "unit": "TFLOP/s", "frac": round(ach / fp32_peak_tflops, 4), "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)",
                 "limiter": "shared-memory data path: each term reads two complex FP32 samples (16 B); "
-                           "84 % of L1/shared throughput in profiles/kernels_paper_40frames_full.md"}
+                           "83 % of L1/shared throughput in profiles/kernels_paper_40frames_full.md"}
     else:
         ach = bytes_alg[dominant] / (stage_ms[dominant] / 1e3) / 1e9
         roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
