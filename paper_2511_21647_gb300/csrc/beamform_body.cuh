@@ -144,32 +144,37 @@ __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __res
     const bool quads = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(rf) & 15) == 0 &&
                        (reinterpret_cast<uintptr_t>(mean) & 15) == 0;
     if (quads) {
-        // whole aligned quads n0-16+4q .. n0-13+4q (q < 40): each inside or outside [0, ns)
-        for (int el = warp; el < DM_NE; el += nwarp) {
-            const int e = e0 + el;
-            const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
-            for (int q = lane; q < (DM_NT + 32) / 4; q += 32) {
-                const int nb = n0 - 16 + 4 * q;
-                float x[4] = {0.f, 0.f, 0.f, 0.f};
-                float4 m01 = make_float4(0.f, 0.f, 0.f, 0.f), m23 = m01;
-                if (nb >= 0 && nb < ns && e < E) {
-                    const float4 r = rf_quad<RT>(rf, (chan0 + e) * ns + nb);
-                    x[0] = r.x * sc;
-                    x[1] = r.y * sc;
-                    x[2] = r.z * sc;
-                    x[3] = r.w * sc;
-                    if (mean) {
-                        const float4 mu = __ldg(reinterpret_cast<const float4*>(mean + ((size_t)k * E + e) * ns + nb));
-                        x[0] -= mu.x;
-                        x[1] -= mu.y;
-                        x[2] -= mu.z;
-                        x[3] -= mu.w;
-                    }
-                    m01 = __ldg(reinterpret_cast<const float4*>(mix + nb));
-                    m23 = __ldg(reinterpret_cast<const float4*>(mix + nb + 2));
+        // whole aligned quads n0-16+4q .. n0-13+4q (q < NQ): each inside or outside [0, ns).
+        // Items (element, quad) in element-major order, two per thread in flight:
+        // both items' loads are issued before either is converted and stored.
+        constexpr int NQ = (DM_NT + 32) / 4;
+        constexpr int ITEMS = DM_NE * NQ;
+        for (int i0 = threadIdx.x; i0 < ITEMS; i0 += 2 * blockDim.x) {
+            float4 r[2], mu[2], ma[2], mb[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = i0 + u * blockDim.x;
+                const int el = idx / NQ, q = idx - el * NQ;
+                const int e = e0 + el, nb = n0 - 16 + 4 * q;
+                r[u] = mu[u] = ma[u] = mb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (idx < ITEMS && nb >= 0 && nb < ns && e < E) {
+                    r[u] = rf_quad<RT>(rf, (chan0 + e) * ns + nb);
+                    if (mean) mu[u] = __ldg(reinterpret_cast<const float4*>(mean + ((size_t)k * E + e) * ns + nb));
+                    ma[u] = __ldg(reinterpret_cast<const float4*>(mix + nb));
+                    mb[u] = __ldg(reinterpret_cast<const float4*>(mix + nb + 2));
                 }
-                const float2 v[4] = {make_float2(x[0] * m01.x, x[0] * m01.y), make_float2(x[1] * m01.z, x[1] * m01.w),
-                                     make_float2(x[2] * m23.x, x[2] * m23.y), make_float2(x[3] * m23.z, x[3] * m23.w)};
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = i0 + u * blockDim.x;
+                if (idx >= ITEMS) continue;
+                const int el = idx / NQ, q = idx - el * NQ;
+                const int e = e0 + el;
+                const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
+                const float x0 = r[u].x * sc - mu[u].x, x1 = r[u].y * sc - mu[u].y;
+                const float x2 = r[u].z * sc - mu[u].z, x3 = r[u].w * sc - mu[u].w;
+                const float2 v[4] = {make_float2(x0 * ma[u].x, x0 * ma[u].y), make_float2(x1 * ma[u].z, x1 * ma[u].w),
+                                     make_float2(x2 * mb[u].x, x2 * mb[u].y), make_float2(x3 * mb[u].z, x3 * mb[u].w)};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int sidx = 4 * q - 1 + j;
