@@ -66,6 +66,15 @@ _D = C.c_double
 _I = C.c_int
 
 
+class TrackParams(C.Structure):
+    _fields_ = [("len", C.c_int), ("substeps", C.c_int), ("max_step", C.c_double), ("cos_max_turn", C.c_double),
+                ("max_speed_change", C.c_double), ("voxel", C.c_double)]
+
+
+TRACK = np.dtype([("first", "<i4"), ("frame0", "<i4"), ("accepted", "<i4"), ("a", "<f8", (3, 3)),
+                  ("mean_speed", "<f8"), ("cos_turn", "<f8"), ("speed_range", "<f8")], align=True)
+
+
 def lib():
     global _lib
     with _lock:
@@ -95,6 +104,10 @@ def lib():
                 "or_peaks_plane": (_I, [_I, _I, _P, _P, _D, _D, _D, _I, _P]),
                 "or_localize2d": (_I, [_I, _I, _I, _I, _P, _P, _I, _D, _D, _D, _D, _I, _P]),
                 "or_pair3d": (_I, [_I, _P, _I, _I, _P]),
+                "or_track_link": (None, [_P, _I, _P, _P, _P, _P, _D, _P]),
+                "or_track_build": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
+                "or_track_grid": (None, [_P, _D, _P]),
+                "or_track_accumulate": (None, [_P, _I, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -315,3 +328,58 @@ def localize(planes, d, sig_z, sig_l, alpha, ncc_min, P):
     L2 = localize2d(A, M, d, sig_z, sig_l, alpha, ncc_min)
     L3 = pair3d(L2, P)
     return A, M, L2, L3
+
+
+# --- tracking (Sec. II-A6) ----------------------------------------------------------
+
+def track_params(length=10, substeps=10, max_step=150e-6, max_turn_deg=45.0, max_speed_change=0.5,
+                 voxel=50e-6) -> TrackParams:
+    import math
+    return TrackParams(length, substeps, max_step, math.cos(math.radians(max_turn_deg)), max_speed_change, voxel)
+
+
+def _list_columns(list3d):
+    L = np.ascontiguousarray(list3d)
+    return (np.ascontiguousarray(L["frame"], dtype=np.int32), np.ascontiguousarray(L["x"], dtype=np.float64),
+            np.ascontiguousarray(L["y"], dtype=np.float64), np.ascontiguousarray(L["z"], dtype=np.float64))
+
+
+def track_link(g, list3d, max_step: float) -> np.ndarray:
+    """successor of each 3D localisation in the next frame (-1: none); the list is frame-major"""
+    fr, x, y, z = _list_columns(list3d)
+    succ = np.full(len(fr), -1, dtype=np.int32)
+    lib().or_track_link(_byref(geom(g)), len(fr), _ptr(fr), _ptr(x), _ptr(y), _ptr(z), max_step, _ptr(succ))
+    return succ
+
+
+def track_build(g, list3d, succ, prm: TrackParams, cap: int = 1 << 20) -> np.ndarray:
+    fr, x, y, z = _list_columns(list3d)
+    succ = np.ascontiguousarray(succ, dtype=np.int32)
+    out = np.zeros(cap, dtype=TRACK)
+    n = lib().or_track_build(_byref(geom(g)), len(fr), _ptr(fr), _ptr(x), _ptr(y), _ptr(z), _ptr(succ),
+                             _byref(prm), cap, _ptr(out))
+    if n > cap:
+        raise RuntimeError(f"oracle track capacity {cap} < {n}")
+    return out[:n]
+
+
+def track_grid(g, voxel: float) -> tuple:
+    dims = np.zeros(3, dtype=np.int32)
+    lib().or_track_grid(_byref(geom(g)), voxel, _ptr(dims))
+    return int(dims[0]), int(dims[1]), int(dims[2])
+
+
+def track_accumulate(g, tracks, prm: TrackParams) -> np.ndarray:
+    """density counts [nz_v][ny_v][nx_v] (uint32)"""
+    nx, ny, nz = track_grid(g, prm.voxel)
+    grid = np.zeros((nz, ny, nx), dtype=np.uint32)
+    tr = np.ascontiguousarray(tracks, dtype=TRACK)
+    lib().or_track_accumulate(_byref(geom(g)), len(tr), _ptr(tr) if len(tr) else None, _byref(prm), _ptr(grid))
+    return grid
+
+
+def track(g, list3d, prm: TrackParams):
+    """list3d -> (successors, tracks, density counts)"""
+    succ = track_link(g, list3d, prm.max_step)
+    tr = track_build(g, list3d, succ, prm)
+    return succ, tr, track_accumulate(g, tr, prm)

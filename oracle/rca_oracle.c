@@ -630,3 +630,183 @@ int or_pair3d(int n2d, const or_loc2d* L, int P, int cap, or_loc3d* out)
     free(best_xz);
     return n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Fixed-length tracking, smoothing, rejection and accumulation (Sec. II-A6, */
+/* Fig. 1f)                                                                  */
+/* ------------------------------------------------------------------------ */
+/* Readings (the paper names a bipartite pairing [41] and the rules, not the
+ * formulas):
+ *  - positions in metres: x, y lateral pixel -> (p - (N-1)/2) pitch, depth
+ *    pixel -> z0 + p dz;
+ *  - pairing between frames t and t+1: mutual nearest neighbours (Euclidean,
+ *    within max_step; ties to the lower list index) -- a one-to-one partial
+ *    matching of the bipartite graph of the two frames' localisations;
+ *  - every localisation of every frame starts a search; it becomes a track
+ *    when its successor chain reaches len points;
+ *  - smoothing: least-squares quadratic per axis over tau = 0 .. len-1, in the
+ *    orthogonal basis 1, phi1 = tau - m, phi2 = (tau - m)^2 - q, m = (len-1)/2,
+ *    q = (len^2 - 1)/12;
+ *  - rejection: the direction change is the angle between the first and the
+ *    last smoothed segment (kept when its cosine >= cos_max_turn); the speed
+ *    change is max - min of the smoothed segment lengths (kept when <=
+ *    max_speed_change x their mean); a track with zero mean speed is dropped;
+ *  - accumulation: the smoothed track sampled at tau = s / substeps,
+ *    s = 0 .. (len-1) substeps, adds one count per sample to the voxel that
+ *    holds it; the grid starts half a pixel before the first lateral pixel and
+ *    the first depth row. */
+
+static void or_track_pos(const or_geom* g, double xp, double yp, double zp, double p[3])
+{
+    p[0] = (xp - 0.5 * (g->n_el - 1)) * g->pitch;
+    p[1] = (yp - 0.5 * (g->n_el - 1)) * g->pitch;
+    p[2] = g->z0 + zp * g->dz;
+}
+
+static double or_d2(const double a[3], const double b[3])
+{
+    const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+/* succ[i] = the localisation of frame[i] + 1 paired with i, or -1 */
+void or_track_link(const or_geom* g, int n, const int* frame, const double* x, const double* y, const double* z,
+                   double max_step, int* succ)
+{
+    int* nxt = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int* prv = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    const double r2 = max_step * max_step;
+    for (int i = 0; i < n; ++i) {
+        double pi[3], pj[3], best = 0.0;
+        or_track_pos(g, x[i], y[i], z[i], pi);
+        nxt[i] = -1;
+        prv[i] = -1;
+        for (int j = 0; j < n; ++j) {
+            if (frame[j] != frame[i] + 1) continue;
+            or_track_pos(g, x[j], y[j], z[j], pj);
+            const double d2 = or_d2(pi, pj);
+            if (d2 <= r2 && (nxt[i] < 0 || d2 < best)) {
+                nxt[i] = j;
+                best = d2;
+            }
+        }
+        best = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (frame[j] != frame[i] - 1) continue;
+            or_track_pos(g, x[j], y[j], z[j], pj);
+            const double d2 = or_d2(pi, pj);
+            if (d2 <= r2 && (prv[i] < 0 || d2 < best)) {
+                prv[i] = j;
+                best = d2;
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) succ[i] = (nxt[i] >= 0 && prv[nxt[i]] == i) ? nxt[i] : -1;
+    free(nxt);
+    free(prv);
+}
+
+/* Tracks in list order of their first point; returns the count (entries
+ * beyond cap are counted, not written). */
+int or_track_build(const or_geom* g, int n, const int* frame, const double* x, const double* y, const double* z,
+                   const int* succ, const or_track_params* prm, int cap, or_track* out)
+{
+    const int L = prm->len;
+    const double m = 0.5 * (double)(L - 1), q = ((double)L * (double)L - 1.0) / 12.0;
+    /* sums of phi1^2 and phi2^2 over tau = 0 .. L-1 */
+    double n1 = 0.0, n2 = 0.0;
+    for (int t = 0; t < L; ++t) {
+        const double f1 = (double)t - m, f2 = f1 * f1 - q;
+        n1 += f1 * f1;
+        n2 += f2 * f2;
+    }
+    int* idx = (int*)malloc(sizeof(int) * (L > 0 ? L : 1));
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        idx[0] = i;
+        int ok = 1;
+        for (int s = 1; s < L && ok; ++s) {
+            idx[s] = succ[idx[s - 1]];
+            ok = idx[s] >= 0;
+        }
+        if (!ok) continue;
+        or_track tr;
+        tr.first = i;
+        tr.frame0 = frame[i];
+        for (int ax = 0; ax < 3; ++ax) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int t = 0; t < L; ++t) {
+                double p[3];
+                or_track_pos(g, x[idx[t]], y[idx[t]], z[idx[t]], p);
+                const double f1 = (double)t - m, f2 = f1 * f1 - q;
+                s0 += p[ax];
+                s1 += p[ax] * f1;
+                s2 += p[ax] * f2;
+            }
+            tr.a[ax][0] = s0 / (double)L;
+            tr.a[ax][1] = s1 / n1;
+            tr.a[ax][2] = s2 / n2;
+        }
+        /* smoothed segment s -> s+1: a1 + a2 (phi2(s+1) - phi2(s)) = a1 + a2 (2 (s - m) + 1) */
+        double vfirst[3] = {0.0, 0.0, 0.0}, vlast[3] = {0.0, 0.0, 0.0}, sum = 0.0, vmax = 0.0, vmin = 0.0;
+        for (int s = 0; s + 1 < L; ++s) {
+            double v[3];
+            const double dphi2 = 2.0 * ((double)s - m) + 1.0;
+            for (int ax = 0; ax < 3; ++ax) v[ax] = tr.a[ax][1] + tr.a[ax][2] * dphi2;
+            const double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            sum += sp;
+            if (s == 0 || sp > vmax) vmax = sp;
+            if (s == 0 || sp < vmin) vmin = sp;
+            if (s == 0)
+                for (int ax = 0; ax < 3; ++ax) vfirst[ax] = v[ax];
+            if (s + 2 == L)
+                for (int ax = 0; ax < 3; ++ax) vlast[ax] = v[ax];
+        }
+        tr.mean_speed = sum / (double)(L - 1);
+        tr.speed_range = vmax - vmin;
+        const double nf = sqrt(vfirst[0] * vfirst[0] + vfirst[1] * vfirst[1] + vfirst[2] * vfirst[2]);
+        const double nl = sqrt(vlast[0] * vlast[0] + vlast[1] * vlast[1] + vlast[2] * vlast[2]);
+        const double dot = vfirst[0] * vlast[0] + vfirst[1] * vlast[1] + vfirst[2] * vlast[2];
+        tr.cos_turn = (nf > 0.0 && nl > 0.0) ? dot / (nf * nl) : -2.0;
+        tr.accepted = tr.mean_speed > 0.0 && tr.cos_turn >= prm->cos_max_turn &&
+                      tr.speed_range <= prm->max_speed_change * tr.mean_speed;
+        if (cnt < cap) out[cnt] = tr;
+        ++cnt;
+    }
+    free(idx);
+    return cnt;
+}
+
+/* density grid [nz_v][ny_v][nx_v] covering the lateral pixels and the depth rows */
+void or_track_grid(const or_geom* g, double voxel, int dims[3])
+{
+    dims[0] = (int)ceil((double)g->n_el * g->pitch / voxel);
+    dims[1] = dims[0];
+    dims[2] = (int)ceil((double)g->nz * g->dz / voxel);
+}
+
+void or_track_accumulate(const or_geom* g, int ntr, const or_track* tr, const or_track_params* prm,
+                         unsigned* grid)
+{
+    int dims[3];
+    or_track_grid(g, prm->voxel, dims);
+    const int L = prm->len;
+    const double m = 0.5 * (double)(L - 1), q = ((double)L * (double)L - 1.0) / 12.0;
+    const double lo[3] = {-0.5 * (double)g->n_el * g->pitch, -0.5 * (double)g->n_el * g->pitch,
+                          g->z0 - 0.5 * g->dz};
+    for (int k = 0; k < ntr; ++k) {
+        if (!tr[k].accepted) continue;
+        for (int s = 0; s <= (L - 1) * prm->substeps; ++s) {
+            const double tau = (double)s / (double)prm->substeps;
+            const double f1 = tau - m, f2 = f1 * f1 - q;
+            int iv[3], inside = 1;
+            for (int ax = 0; ax < 3; ++ax) {
+                const double p = tr[k].a[ax][0] + tr[k].a[ax][1] * f1 + tr[k].a[ax][2] * f2;
+                const double c = floor((p - lo[ax]) / prm->voxel);
+                inside = inside && c >= 0.0 && c < (double)dims[ax];
+                iv[ax] = inside ? (int)c : 0;
+            }
+            if (inside) grid[((size_t)iv[2] * dims[1] + iv[1]) * dims[0] + iv[0]] += 1u;
+        }
+    }
+}

@@ -100,6 +100,34 @@ int or_localize2d(int F, int S, int nz, int N, const double* A, const double* M,
                   int cap, or_loc2d* out);
 int or_pair3d(int n2d, const or_loc2d* list, int P, int cap, or_loc3d* out);
 
+/* fixed-length tracking and accumulation (Sec. II-A6, Fig. 1f) */
+typedef struct {
+    int len;                  /* points per track (the paper: ten consecutive volumes) */
+    int substeps;             /* accumulation samples per frame interval */
+    double max_step;          /* link radius between consecutive frames (m) */
+    double cos_max_turn;      /* cosine of the largest direction change kept (45 deg) */
+    double max_speed_change;  /* largest (max - min) segment speed kept, fraction of the mean (0.5) */
+    double voxel;             /* density grid spacing (m) */
+} or_track_params;
+
+typedef struct {
+    int first;                /* track id: list index of the first point */
+    int frame0;               /* its frame */
+    int accepted;             /* 1 if the turn and speed tests pass */
+    double a[3][3];           /* per axis x, y, z: coefficients of 1, phi1(tau), phi2(tau) (m) */
+    double mean_speed;        /* mean smoothed segment length (m per frame) */
+    double cos_turn;          /* cosine of the angle between the first and last segment */
+    double speed_range;       /* max - min smoothed segment length (m per frame) */
+} or_track;
+
+void or_track_link(const or_geom* g, int n, const int* frame, const double* x, const double* y, const double* z,
+                   double max_step, int* succ);
+int or_track_build(const or_geom* g, int n, const int* frame, const double* x, const double* y, const double* z,
+                   const int* succ, const or_track_params* prm, int cap, or_track* out);
+void or_track_grid(const or_geom* g, double voxel, int dims[3]);
+void or_track_accumulate(const or_geom* g, int ntr, const or_track* tr, const or_track_params* prm,
+                         unsigned* grid);
+
 #ifdef __cplusplus
 }
 #endif

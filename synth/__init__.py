@@ -18,3 +18,4 @@ from .rca_sim import (  # noqa: F401
     quantize_int16,
     tx_angles,
 )
+from .track_scene import TrackScene, track_scene  # noqa: F401,E402
