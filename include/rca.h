@@ -332,6 +332,66 @@ rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, 
                         ulm_loc3d* out3d, int cap3d, int* n3d_dev);
 
 /* ---------------------------------------------------------------------- */
+/* Fixed-length tracking and accumulation (Sec. II-A6, Fig. 1f)            */
+/* ---------------------------------------------------------------------- */
+
+/* Tracking parameters.  The paper keeps MBs tracked across ten consecutive
+ * volumes, smooths each track by a least-squares quadratic and drops tracks
+ * whose direction changes by more than 45 degrees or whose speed changes by
+ * more than half their mean speed (Sec. II-A6). */
+typedef struct {
+    int32_t len;               /* points per track (10); 2 .. ULM_TRACK_MAX_LEN */
+    int32_t substeps;          /* density samples per frame interval (>= 1) */
+    double max_step_m;         /* link radius between consecutive frames (metres, > 0) */
+    double cos_max_turn;       /* cosine of the largest direction change kept (cos 45 deg) */
+    double max_speed_change;   /* largest (max - min) smoothed segment speed kept, as a fraction of the mean (0.5) */
+    double voxel_m;            /* density grid spacing (metres, > 0) */
+} ulm_track_params;
+#define ULM_TRACK_MAX_LEN 64
+
+/* One fixed-length track. */
+typedef struct {
+    int32_t first;             /* track id: 3D-list index of its first point */
+    int32_t frame0;            /* frame of the first point */
+    int32_t accepted;          /* 1: kept by the turn and speed tests */
+    int32_t reserved;
+    double a[3][3];            /* per axis x, y, z (metres): least-squares quadratic in the basis
+                                  1, tau - m, (tau - m)^2 - (len^2 - 1)/12, tau = 0 .. len-1, m = (len-1)/2 */
+    double mean_speed;         /* mean smoothed segment length (metres per frame) */
+    double cos_turn;           /* cosine of the angle between the first and last smoothed segment (-2: undefined) */
+    double speed_range;        /* max - min smoothed segment length (metres per frame) */
+} ulm_track_rec;               /* 112 bytes */
+
+/* Density grid of a geometry: dims = {nx, ny, nz} voxels of voxel_m covering
+ * the N lateral pixels (x, y from -N pitch / 2) and the nz depth rows (from
+ * z0 - dz / 2); the grid is [nz][ny][nx] uint32. */
+rca_status ulm_density_shape(const rca_tables* t, double voxel_m, int32_t dims[3]);
+
+/* Fixed-length tracking of a 3D localisation list (Sec. II-A6).  Positions
+ * in metres: x, y -> (p - (N-1)/2) pitch, z -> z0 + p dz.
+ *  1. Pairing of consecutive frames: i (frame t) and j (frame t + 1) are
+ *     linked when each is the other's nearest neighbour within max_step_m
+ *     (ties to the lower index) -- a one-to-one matching of the two frames.
+ *  2. Every localisation starts a search; it becomes a track when its chain
+ *     of links reaches len points (tracks may overlap in time).
+ *  3. Least-squares quadratic per axis; rejection as in ulm_track_params;
+ *     a track with zero mean speed is rejected.
+ *  4. If density is non-NULL, every accepted track written to out, sampled
+ *     at tau = s / substeps (s = 0 .. (len-1) substeps), adds 1 to the voxel
+ *     holding each sample (accumulated INTO density: zero it first, or sum
+ *     ensembles).
+ * All decisions and coefficients in double precision.
+ *   list3d: frame-major (as ulm_pair3d writes it); *n3d_dev: its length
+ *   (entries beyond cap3d ignored).  out: capacity cap_tracks, tracks in
+ *   order of their first point; *n_tracks_dev (device int) receives the true
+ *   count (beyond cap_tracks: status word CAPACITY).  density: device
+ *   [nz][ny][nx] uint32 as from ulm_density_shape.
+ * Host-side errors: invalid parameters or sizes (INVALID_ARG) before any launch. */
+rca_status ulm_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* list3d, const int* n3d_dev, int cap3d,
+                     int n_frames, const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks_dev,
+                     uint32_t* density);
+
+/* ---------------------------------------------------------------------- */
 /* Learned localiser (the paper's future-work form, Sec. IV)               */
 /* ---------------------------------------------------------------------- */
 

@@ -64,6 +64,16 @@ class ulm_cnn_desc(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_ulonglong)]
 
 
+class ulm_track_params(C.Structure):
+    _fields_ = [("len", C.c_int32), ("substeps", C.c_int32), ("max_step_m", C.c_double), ("cos_max_turn", C.c_double),
+                ("max_speed_change", C.c_double), ("voxel_m", C.c_double)]
+
+
+ULM_TRACK_MAX_LEN = 64
+TRACK = np.dtype([("first", "<i4"), ("frame0", "<i4"), ("accepted", "<i4"), ("reserved", "<i4"),
+                  ("a", "<f8", (3, 3)), ("mean_speed", "<f8"), ("cos_turn", "<f8"), ("speed_range", "<f8")])
+assert TRACK.itemsize == 112
+
 LOC2D = np.dtype([("frame", "<i4"), ("axis", "<i4"), ("slab", "<i4"), ("iz", "<i4"), ("ilat", "<i4"),
                   ("z", "<f4"), ("lat", "<f4"), ("ncc", "<f4"), ("amp", "<f4"), ("reserved", "<i4")])
 LOC3D = np.dtype([("frame", "<i4"), ("i_xz", "<i4"), ("i_yz", "<i4"), ("reserved", "<i4"),
@@ -102,6 +112,8 @@ SIGNATURES = {
     "ulm_pair3d": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
     "ulm_pair3d_noalloc": (_S, [_P, _P, _P, _P, _I, _I, _P, _I, _P]),
     "ulm_localize": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _I, _P]),
+    "ulm_density_shape": (_S, [_P, C.c_double, _P]),
+    "ulm_track": (_S, [_P, _P, _P, _P, _I, _I, C.POINTER(ulm_track_params), _P, _I, _P, _P]),
     "ulm_cnn_create": (_S, [_P, C.POINTER(ulm_cnn_desc), C.POINTER(_P)]),
     "ulm_cnn_destroy": (_S, [_P]),
     "ulm_cnn_param_count": (_S, [_P, C.POINTER(_SZ)]),

@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librca.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# translation units and their extra flags (the FP64 table kernel keeps every
-# rounding as written: no fused multiply-add contraction)
+# translation units and their extra flags (the FP64 table and tracking
+# kernels keep every rounding as written: no fused multiply-add contraction)
 UNITS = {
     "api.cu": [],
     "tables.cu": ["-fmad=false"],
@@ -28,6 +28,7 @@ UNITS = {
     "batch_c16bf.cu": [],
     "localize.cu": [],
     "cnn.cu": [],
+    "track.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
 }
 
 

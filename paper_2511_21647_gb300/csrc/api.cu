@@ -512,6 +512,42 @@ extern "C" rca_status ulm_pair3d_noalloc(rca_handle* h, const rca_tables* t, con
     return launch_pair3d_noalloc(h, t, L, n2d, cap2d, F, out, cap3d, n3d);
 }
 
+extern "C" rca_status ulm_density_shape(const rca_tables* t, double voxel_m, int32_t dims[3])
+{
+    if (!t || !dims || !(voxel_m > 0.0)) return RCA_ERR_INVALID_ARG;
+    int d[3];
+    density_shape(t->gd, voxel_m, d);
+    for (int k = 0; k < 3; ++k) dims[k] = d[k];
+    return RCA_OK;
+}
+
+extern "C" rca_status ulm_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d,
+                                int F, const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks,
+                                uint32_t* density)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!prm) return set_error(h, RCA_ERR_INVALID_ARG, "null tracking parameters");
+    if (prm->len < 2 || prm->len > ULM_TRACK_MAX_LEN)
+        return set_error(h, RCA_ERR_INVALID_ARG, "track length %d outside [2, %d]", prm->len, ULM_TRACK_MAX_LEN);
+    if (prm->substeps < 1 || prm->substeps > 1024)
+        return set_error(h, RCA_ERR_INVALID_ARG, "substeps %d outside [1, 1024]", prm->substeps);
+    if (!(prm->max_step_m > 0.0) || !(prm->voxel_m > 0.0) || !(prm->max_speed_change >= 0.0) ||
+        !(prm->cos_max_turn >= -1.0 && prm->cos_max_turn <= 1.0))
+        return set_error(h, RCA_ERR_INVALID_ARG, "tracking radius, voxel, speed change or turn cosine out of range");
+    if (!n3d || !n_tracks || cap3d < 0 || cap_tracks < 0 || (cap3d > 0 && !L) || (cap_tracks > 0 && !out))
+        return set_error(h, RCA_ERR_INVALID_ARG, "null list or count");
+    if (density) {
+        int d[3];
+        density_shape(t->gd, prm->voxel_m, d);
+        if (d[0] <= 0 || d[2] <= 0 || (double)d[0] * d[1] * d[2] > 4.0e9)
+            return set_error(h, RCA_ERR_INVALID_ARG, "density grid of %d x %d x %d voxels", d[0], d[1], d[2]);
+    }
+    DeviceGuard dg(h->device);
+    return launch_track(h, t, L, n3d, cap3d, F, prm, out, cap_tracks, n_tracks, density);
+}
+
 extern "C" rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
                                    const ulm_params* prm, ulm_loc2d* out2d, int cap2d, int* n2d, ulm_loc3d* out3d,
                                    int cap3d, int* n3d)

@@ -186,6 +186,26 @@ def ulm_pair3d(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
     _check(L.load().ulm_pair3d(h, t, _ptr(list2d), _ptr(n2d), cap2d, n_frames, _ptr(out3d), cap3d, _ptr(n3d)), h)
 
 
+def make_track_params(length=10, substeps=10, max_step_m=150e-6, max_turn_deg=45.0, max_speed_change=0.5,
+                      voxel_m=50e-6) -> L.ulm_track_params:
+    import math
+    p = L.ulm_track_params()
+    p.len, p.substeps, p.max_step_m = length, substeps, max_step_m
+    p.cos_max_turn, p.max_speed_change, p.voxel_m = math.cos(math.radians(max_turn_deg)), max_speed_change, voxel_m
+    return p
+
+
+def ulm_density_shape(t, voxel_m):
+    dims = (C.c_int32 * 3)()
+    _check(L.load().ulm_density_shape(t, voxel_m, C.cast(dims, C.c_void_p)), None)
+    return int(dims[0]), int(dims[1]), int(dims[2])
+
+
+def ulm_track(h, t, list3d, n3d, cap3d, n_frames, prm, out, cap_tracks, n_tracks, density=None):
+    _check(L.load().ulm_track(h, t, _ptr(list3d), _ptr(n3d), cap3d, n_frames, C.byref(prm), _ptr(out), cap_tracks,
+                              _ptr(n_tracks), _ptr(density)), h)
+
+
 def ulm_pair3d_noalloc(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
     """ulm_pair3d on the library's fixed per-device scratch (no allocation)."""
     _check(L.load().ulm_pair3d_noalloc(h, t, _ptr(list2d), _ptr(n2d), cap2d, n_frames, _ptr(out3d), cap3d, _ptr(n3d)), h)
