@@ -410,6 +410,7 @@ def main():
         forms["reduced"] = reduced_form(R, L, sess, rf, F, prm, max(3, args.warmup), K, stream)
         forms["batched"] = batched_form(R, L, dev, stream, K)
         forms["learned"] = learned_form(R, L, sess, planes, F, g, dev, stream, peaks)
+    track = tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K) if rank == 0 and not args.no_forms else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
@@ -441,6 +442,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "forms": forms,
+            "tracking": track,
             "gpu_launches": K * sum(launches.values()),
             "clocks": clk.summary(),
             "localisations": {"n2d": n2d_v, "n3d": n3d_v},
@@ -452,6 +454,40 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K):
+    """Fixed-length tracking (Sec. II-A6) of the last step's 3D list: ten-point
+    tracks, 150 um link radius, 45 degree / half-mean-speed rejection, 50 um
+    density grid; not part of the timed step (the paper's tracking follows the
+    projection path)."""
+    import torch
+    prm = R.make_track_params()
+    nx, ny, nz = R.ulm_density_shape(sess.t, prm.voxel_m)
+    grid = torch.zeros((nz, ny, nx), dtype=torch.int32, device=out3d.device)
+    cap_t = cap3d
+    out = torch.zeros((cap_t, L.TRACK.itemsize // 4), dtype=torch.int32, device=out3d.device)
+    nt = torch.zeros(1, dtype=torch.int32, device=out3d.device)
+
+    def run():
+        R.ulm_track(sess.h, sess.t, out3d, n3d, cap3d, F, prm, out, cap_t, nt, grid)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k = int(nt.item())
+    rec = out[:min(k, cap_t)].cpu().numpy().view(L.TRACK).reshape(-1)
+    return {"ms_per_ensemble": round(e0.elapsed_time(e1) / K, 4), "tracks": k,
+            "accepted": int(rec["accepted"].sum()), "localisations": int(n3d.item()),
+            "params": {"len": prm.len, "max_step_m": prm.max_step_m, "max_turn_deg": 45.0,
+                       "max_speed_change": prm.max_speed_change, "voxel_m": prm.voxel_m, "substeps": prm.substeps},
+            "density_grid": [nz, ny, nx], "kernels": 6, "status": R.rca_sync_status(sess.h)}
 
 
 def reduced_form(R, L, sess, rf, F, prm, W, K, stream):
