@@ -19,3 +19,4 @@ from .rca_sim import (  # noqa: F401
     tx_angles,
 )
 from .track_scene import TrackScene, track_scene  # noqa: F401,E402
+from .slice_scene import moving_slices  # noqa: F401,E402
