@@ -332,6 +332,30 @@ rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, 
                         ulm_loc3d* out3d, int cap3d, int* n3d_dev);
 
 /* ---------------------------------------------------------------------- */
+/* Projection-based rigid motion estimation (Sec. II-A3, Fig. 1d)          */
+/* ---------------------------------------------------------------------- */
+
+/* Rigid displacement of every frame against frame 0 from the Stage-1 slices.
+ * For each transmission k, slice k of frame f and of frame 0 are
+ * zero-padded to Zp x N (Zp: next power of two >= nzs) and correlated by 2D
+ * FFT: R = IFFT2(FFT2(S_f) conj(FFT2(S_0))), R[dz, dx] = sum_p S_f[p + (dz,
+ * dx)] conj(S_0[p]) (circular).  The displacement is the peak of |R| (first
+ * in row-major order on ties; indices at or past half the padded size are
+ * negative), refined per axis by a 3-point parabola through |R| at the peak
+ * and its circular neighbours (clamped to +-1/2, none when not concave).
+ * RC transmissions (k < K) resolve (x, z), CR (k >= K) resolve (y, z); each
+ * family is averaged over its K transmissions and the two combine into
+ * motion[f] = (x_RC pitch, y_CR pitch, (z_RC + z_CR) / 2 dz / us) metres.
+ *   slices: [F][2K][nzs][N] C32 (as rca_stage1 writes them; pass unfiltered
+ *   slices, whose tissue carries the motion).  motion: device [F][3] float.
+ *   shifts (nullable): device [F][2K][3] float (z in slice rows, x in
+ *   lateral pixels, NCC = |R| / (||S_f|| ||S_0||) at the peak).  peaks
+ *   (nullable): device [F][2K][2] int, the integer (dz, dx).
+ * Limits: N a power of two in [32, 256], nzs <= 512 (UNSUPPORTED beyond). */
+rca_status rca_motion_estimate(rca_handle* h, const rca_tables* t, const void* slices, int n_frames, float* motion,
+                               float* shifts, int* peaks);
+
+/* ---------------------------------------------------------------------- */
 /* Fixed-length tracking and accumulation (Sec. II-A6, Fig. 1f)            */
 /* ---------------------------------------------------------------------- */
 

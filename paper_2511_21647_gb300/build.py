@@ -29,6 +29,7 @@ UNITS = {
     "localize.cu": [],
     "cnn.cu": [],
     "track.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
+    "motion.cu": [],
 }
 
 

@@ -512,6 +512,18 @@ extern "C" rca_status ulm_pair3d_noalloc(rca_handle* h, const rca_tables* t, con
     return launch_pair3d_noalloc(h, t, L, n2d, cap2d, F, out, cap3d, n3d);
 }
 
+extern "C" rca_status rca_motion_estimate(rca_handle* h, const rca_tables* t, const void* slices, int F,
+                                          float* motion, float* shifts, int* peaks)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!slices || !motion) return set_error(h, RCA_ERR_INVALID_ARG, "null slices or motion");
+    if (F > 65535) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 65535 frames in one call");
+    DeviceGuard dg(h->device);
+    return launch_motion(h, t, (const float2*)slices, F, motion, shifts, peaks);
+}
+
 extern "C" rca_status ulm_density_shape(const rca_tables* t, double voxel_m, int32_t dims[3])
 {
     if (!t || !dims || !(voxel_m > 0.0)) return RCA_ERR_INVALID_ARG;

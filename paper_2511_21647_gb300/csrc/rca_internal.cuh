@@ -50,6 +50,7 @@ enum WsSlot {
     WS_N2D,        // int [1]
     WS_MISC,       // small scratch
     WS_TRACK,      // tracking: frame offsets, links, flags, positions, per-localisation tracks
+    WS_MOTION,     // motion estimation: twiddles, row spectra, reference spectrum, correlations
     WS_COUNT
 };
 
@@ -232,6 +233,8 @@ rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca
 rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
                          float2* slices);
 void density_shape(const GeomDev& g, double voxel, int dims[3]);
+rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slices, int F, float* motion,
+                         float* shifts, int* peaks);
 rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d, int F,
                         const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks, unsigned* density);
 rca_status launch_stage2(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes,

@@ -195,6 +195,10 @@ def make_track_params(length=10, substeps=10, max_step_m=150e-6, max_turn_deg=45
     return p
 
 
+def rca_motion_estimate(h, t, slices, n_frames, motion, shifts=None, peaks=None):
+    _check(L.load().rca_motion_estimate(h, t, _ptr(slices), n_frames, _ptr(motion), _ptr(shifts), _ptr(peaks)), h)
+
+
 def ulm_density_shape(t, voxel_m):
     dims = (C.c_int32 * 3)()
     _check(L.load().ulm_density_shape(t, voxel_m, C.cast(dims, C.c_void_p)), None)

@@ -22,10 +22,9 @@ def moving_slices(geom, n_frames: int, K: int, displacement, seed: int, n_scat: 
                     rng.uniform(-0.3 * N * geom.pitch, 0.3 * N * geom.pitch, n_scat),
                     geom.z0 + rng.uniform(0.2, 0.8, n_scat) * (nzs - 1) * row_m], axis=1)
     amp = rng.normal(size=(2 * K, n_scat)) + 1j * rng.normal(size=(2 * K, n_scat))
-    zz = np.arange(nzs)[:, None].astype(np.float64)
-    xx = np.arange(N)[None, :].astype(np.float64)
     out = np.zeros((n_frames, 2 * K, nzs, N), dtype=np.complex128)
     disp = np.asarray(displacement, dtype=np.float64)
+    hz, hx = int(np.ceil(5 * sigma_rows)), int(np.ceil(5 * sigma_px))   # blobs cut at 5 sigma
     for f in range(n_frames):
         p = pos + disp[f][None, :]
         for k in range(2 * K):
@@ -34,8 +33,15 @@ def moving_slices(geom, n_frames: int, K: int, displacement, seed: int, n_scat: 
             zr = (p[:, 2] - geom.z0) / row_m
             acc = np.zeros((nzs, N), dtype=np.complex128)
             for s in range(n_scat):
-                acc += amp[k, s] * np.exp(-(zz - zr[s]) ** 2 / (2 * sigma_rows ** 2)
-                                          - (xx - lp[s]) ** 2 / (2 * sigma_px ** 2))
+                z0, x0 = int(np.floor(zr[s])), int(np.floor(lp[s]))
+                za, zb = max(0, z0 - hz), min(nzs, z0 + hz + 2)
+                xa, xb = max(0, x0 - hx), min(N, x0 + hx + 2)
+                if za >= zb or xa >= xb:
+                    continue
+                zz = np.arange(za, zb)[:, None].astype(np.float64)
+                xx = np.arange(xa, xb)[None, :].astype(np.float64)
+                acc[za:zb, xa:xb] += amp[k, s] * np.exp(-(zz - zr[s]) ** 2 / (2 * sigma_rows ** 2)
+                                                        - (xx - lp[s]) ** 2 / (2 * sigma_px ** 2))
             if noise > 0:
                 acc += noise * (rng.normal(size=acc.shape) + 1j * rng.normal(size=acc.shape))
             out[f, k] = acc
