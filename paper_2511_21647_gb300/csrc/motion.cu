@@ -2,7 +2,9 @@
 // domain cross-correlation of every frame's Stage-1 slices with frame 0.
 //
 // The slices are zero-padded to Zp x Xp (Zp the next power of two >= nzs,
-// Xp = N) and transformed by hand-written radix-2 FFTs in shared memory:
+// Xp = N) and transformed by hand-written radix-4 / radix-2 FFTs in shared
+// memory; forward transforms leave the spectra in bit-reversed order, which
+// the pointwise product and the inverse transforms take as they are:
 //   k_mo_twiddles   exp(-2 pi i k / n) tables for both axes (double, rounded)
 //   k_mo_rows       forward FFT of every slice row (one warp per row) and the
 //                   row energies
@@ -22,7 +24,7 @@
 
 namespace {
 
-#define MO_TILE 32        // columns per k_mo_cols CTA
+#define MO_TILE 16        // columns per k_mo_cols CTA (three CTAs per SM at 512 rows)
 #define MO_TP (MO_TILE + 1)  // padded tile row: a warp's column walk spreads over the banks
 
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -41,29 +43,98 @@ __global__ void k_mo_twiddles(int xp, int zp, float2* __restrict__ tw)
     tw[i] = make_float2((float)c, (float)s);
 }
 
-// In-place radix-2 decimation-in-time FFT of n = 2^logn points buf[i * st]
-// by the 32 lanes of one warp; inverse: conjugated twiddles, no scaling.
-__device__ __forceinline__ void warp_fft(float2* buf, int st, int logn, const float2* __restrict__ tw, bool inverse,
-                                         int lane)
+// In-place FFTs of n = 2^logn points buf[i * st] by the 32 lanes of one warp,
+// no scaling.  The forward transform is decimation in frequency (natural
+// order in, bit-reversed order out) and the inverse decimation in time
+// (bit-reversed in, natural out), so a spectrum is only ever multiplied
+// pointwise in bit-reversed order and no reordering pass is needed.  Two
+// radix-2 stages run as one radix-4 butterfly on four points held in
+// registers (one shared-memory pass per two stages); an odd stage count adds
+// one radix-2 stage.  tw[k] = exp(-2 pi i k / n), k < n / 2; the inverse uses
+// the conjugates.
+
+// -i v (forward) or +i v (inverse)
+__device__ __forceinline__ float2 rot_q(float2 v, bool inverse)
+{
+    return inverse ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+}
+
+__device__ __forceinline__ float2 tw_get(const float2* tw, int i, bool inverse)
+{
+    float2 w = tw[i];
+    if (inverse) w.y = -w.y;
+    return w;
+}
+
+// natural -> bit-reversed
+__device__ __forceinline__ void warp_fft_dif(float2* buf, int st, int logn, const float2* tw, bool inverse, int lane)
 {
     const int n = 1 << logn;
-    for (int i = lane; i < n; i += 32) {
-        const int j = (int)(__brev((unsigned)i) >> (32 - logn));
-        if (i < j) {
-            const float2 a = buf[i * st], b = buf[j * st];
-            buf[i * st] = b;
-            buf[j * st] = a;
-        }
-    }
-    __syncwarp();
-    for (int s = 1; s <= logn; ++s) {
+    int s = logn;
+    if (s & 1) {
+        // single radix-2 stage, half = 2^(s-1)
         const int half = 1 << (s - 1), tstep = n >> s;
-        for (int b = lane; b < n / 2; b += 32) {
-            const int grp = b >> (s - 1), pos = b & (half - 1);
-            const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-            float2 w = tw[pos * tstep];
-            if (inverse) w.y = -w.y;
-            const float2 u = buf[i0 * st], v = c_mul(buf[i1 * st], w);
+        for (int bf = lane; bf < n / 2; bf += 32) {
+            const int pos = bf & (half - 1), i0 = (bf >> (s - 1)) * 2 * half + pos, i1 = i0 + half;
+            const float2 u = buf[i0 * st], v = buf[i1 * st];
+            buf[i0 * st] = make_float2(u.x + v.x, u.y + v.y);
+            buf[i1 * st] = c_mul(make_float2(u.x - v.x, u.y - v.y), tw_get(tw, pos * tstep, inverse));
+        }
+        __syncwarp();
+        --s;
+    }
+    for (; s >= 2; s -= 2) {
+        // stages s (half 2h) then s - 1 (half h) on a, b, c, d at i0 + {0, h, 2h, 3h}
+        const int h = 1 << (s - 2);
+        for (int g = lane; g < n / 4; g += 32) {
+            const int pos = g & (h - 1), i0 = (g >> (s - 2)) * 4 * h + pos;
+            const float2 a = buf[i0 * st], b = buf[(i0 + h) * st], c = buf[(i0 + 2 * h) * st],
+                         d = buf[(i0 + 3 * h) * st];
+            const float2 w2 = tw_get(tw, pos * (n >> s), inverse);            // w_{4h}^pos
+            const float2 w1 = tw_get(tw, pos * (n >> (s - 1)), inverse);      // w_{2h}^pos
+            const float2 a1 = make_float2(a.x + c.x, a.y + c.y);
+            const float2 c1 = c_mul(make_float2(a.x - c.x, a.y - c.y), w2);
+            const float2 b1 = make_float2(b.x + d.x, b.y + d.y);
+            const float2 d1 = rot_q(c_mul(make_float2(b.x - d.x, b.y - d.y), w2), inverse);
+            buf[i0 * st] = make_float2(a1.x + b1.x, a1.y + b1.y);
+            buf[(i0 + h) * st] = c_mul(make_float2(a1.x - b1.x, a1.y - b1.y), w1);
+            buf[(i0 + 2 * h) * st] = make_float2(c1.x + d1.x, c1.y + d1.y);
+            buf[(i0 + 3 * h) * st] = c_mul(make_float2(c1.x - d1.x, c1.y - d1.y), w1);
+        }
+        __syncwarp();
+    }
+}
+
+// bit-reversed -> natural
+__device__ __forceinline__ void warp_fft_dit(float2* buf, int st, int logn, const float2* tw, bool inverse, int lane)
+{
+    const int n = 1 << logn;
+    int s = 1;
+    for (; s + 1 <= logn; s += 2) {
+        // stages s (half h) then s + 1 (half 2h) on a, b, c, d at i0 + {0, h, 2h, 3h}
+        const int h = 1 << (s - 1);
+        for (int g = lane; g < n / 4; g += 32) {
+            const int pos = g & (h - 1), i0 = (g >> (s - 1)) * 4 * h + pos;
+            const float2 a = buf[i0 * st], b = buf[(i0 + h) * st], c = buf[(i0 + 2 * h) * st],
+                         d = buf[(i0 + 3 * h) * st];
+            const float2 w1 = tw_get(tw, pos * (n >> s), inverse);            // w_{2h}^pos
+            const float2 w2 = tw_get(tw, pos * (n >> (s + 1)), inverse);      // w_{4h}^pos
+            const float2 tb = c_mul(b, w1), td = c_mul(d, w1);
+            const float2 a1 = make_float2(a.x + tb.x, a.y + tb.y), b1 = make_float2(a.x - tb.x, a.y - tb.y);
+            const float2 c1 = make_float2(c.x + td.x, c.y + td.y), d1 = make_float2(c.x - td.x, c.y - td.y);
+            const float2 tc = c_mul(c1, w2), tdd = rot_q(c_mul(d1, w2), inverse);
+            buf[i0 * st] = make_float2(a1.x + tc.x, a1.y + tc.y);
+            buf[(i0 + 2 * h) * st] = make_float2(a1.x - tc.x, a1.y - tc.y);
+            buf[(i0 + h) * st] = make_float2(b1.x + tdd.x, b1.y + tdd.y);
+            buf[(i0 + 3 * h) * st] = make_float2(b1.x - tdd.x, b1.y - tdd.y);
+        }
+        __syncwarp();
+    }
+    if (s == logn) {
+        const int half = 1 << (s - 1);
+        for (int bf = lane; bf < n / 2; bf += 32) {
+            const int pos = bf & (half - 1), i0 = (bf >> (s - 1)) * 2 * half + pos, i1 = i0 + half;
+            const float2 u = buf[i0 * st], v = c_mul(buf[i1 * st], tw_get(tw, pos * (n >> s), inverse));
             buf[i0 * st] = make_float2(u.x + v.x, u.y + v.y);
             buf[i1 * st] = make_float2(u.x - v.x, u.y - v.y);
         }
@@ -78,7 +149,10 @@ __global__ void __launch_bounds__(256) k_mo_rows(const float2* __restrict__ sl, 
 {
     extern __shared__ float2 smo[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2* buf = smo + (size_t)warp * xp;
+    float2* stw = smo;                                  // twiddles [xp / 2]
+    float2* buf = smo + xp / 2 + (size_t)warp * xp;
+    for (int i = threadIdx.x; i < xp / 2; i += blockDim.x) stw[i] = tw[i];
+    __syncthreads();
     const int z = blockIdx.x * 8 + warp;
     const size_t fk = (size_t)blockIdx.z * nt + blockIdx.y;
     if (z >= nzs) return;
@@ -91,7 +165,7 @@ __global__ void __launch_bounds__(256) k_mo_rows(const float2* __restrict__ sl, 
     }
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
     __syncwarp();
-    warp_fft(buf, 1, logx, tw, false, lane);
+    warp_fft_dif(buf, 1, logx, stw, false, lane);
     float2* dst = B + (fk * nzs + z) * xp;
     for (int x = lane; x < xp; x += 32) dst[x] = buf[x];
     if (lane == 0) E[fk * nzs + z] = e;
@@ -105,31 +179,43 @@ __global__ void __launch_bounds__(256) k_mo_cols(const float2* __restrict__ B, i
                                                  const float2* __restrict__ ref, float2* __restrict__ out)
 {
     extern __shared__ float2 smo[];
-    float2* tile = smo;                                // [zp][MO_TP]
+    float2* stw = smo;                                 // twiddles [zp / 2]
+    float2* tile = smo + zp / 2;                       // [zp][MO_TP]
+    const int nth = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int x0 = blockIdx.x * MO_TILE;
     const int k = blockIdx.y, f = frame_base + blockIdx.z;
     const size_t fk = (size_t)f * nt + k;
-    for (int z = warp; z < zp; z += nwarp)
-        tile[z * MO_TP + lane] = z < nzs ? B[(fk * nzs + z) * xp + x0 + lane] : make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < zp / 2; i += nth) stw[i] = twz[i];
+    // element i of the tile: row i / MO_TILE, column i % MO_TILE (a warp covers two rows)
+    for (int i = threadIdx.x; i < zp * MO_TILE; i += nth) {
+        const int z = i / MO_TILE, c = i - z * MO_TILE;
+        tile[z * MO_TP + c] = z < nzs ? B[(fk * nzs + z) * xp + x0 + c] : make_float2(0.f, 0.f);
+    }
     __syncthreads();
-    for (int c = warp; c < MO_TILE; c += nwarp) warp_fft(tile + c, MO_TP, logz, twz, false, lane);
+    for (int c = warp; c < MO_TILE; c += nwarp) warp_fft_dif(tile + c, MO_TP, logz, stw, false, lane);
     __syncthreads();
     if (!ref) {
         float2* dst = out + (size_t)k * zp * xp;
-        for (int z = warp; z < zp; z += nwarp) dst[(size_t)z * xp + x0 + lane] = tile[z * MO_TP + lane];
+        for (int i = threadIdx.x; i < zp * MO_TILE; i += nth) {
+            const int z = i / MO_TILE, c = i - z * MO_TILE;
+            dst[(size_t)z * xp + x0 + c] = tile[z * MO_TP + c];
+        }
         return;
     }
     const float2* rk = ref + (size_t)k * zp * xp;
-    for (int z = warp; z < zp; z += nwarp) {
-        const float2 a = tile[z * MO_TP + lane], r = rk[(size_t)z * xp + x0 + lane];
-        tile[z * MO_TP + lane] = c_mulc(a, r);
+    for (int i = threadIdx.x; i < zp * MO_TILE; i += nth) {
+        const int z = i / MO_TILE, c = i - z * MO_TILE;
+        tile[z * MO_TP + c] = c_mulc(tile[z * MO_TP + c], rk[(size_t)z * xp + x0 + c]);
     }
     __syncthreads();
-    for (int c = warp; c < MO_TILE; c += nwarp) warp_fft(tile + c, MO_TP, logz, twz, true, lane);
+    for (int c = warp; c < MO_TILE; c += nwarp) warp_fft_dit(tile + c, MO_TP, logz, stw, true, lane);
     __syncthreads();
     float2* dst = out + ((size_t)blockIdx.z * nt + k) * zp * xp;
-    for (int z = warp; z < zp; z += nwarp) dst[(size_t)z * xp + x0 + lane] = tile[z * MO_TP + lane];
+    for (int i = threadIdx.x; i < zp * MO_TILE; i += nth) {
+        const int z = i / MO_TILE, c = i - z * MO_TILE;
+        dst[(size_t)z * xp + x0 + c] = tile[z * MO_TP + c];
+    }
 }
 
 // |R|^2 of one inverse-transformed row into the caller's buffer
@@ -138,7 +224,7 @@ __device__ __forceinline__ void mo_row_mag(const float2* __restrict__ Crow, floa
 {
     for (int x = lane; x < xp; x += 32) buf[x] = Crow[x];
     __syncwarp();
-    warp_fft(buf, 1, logx, twx, true, lane);
+    warp_fft_dit(buf, 1, logx, twx, true, lane);
 }
 
 // one CTA per (frame, transmission): peak, sub-pixel, NCC
@@ -152,13 +238,16 @@ __global__ void __launch_bounds__(256) k_mo_peak(const float2* __restrict__ C, c
     __shared__ float s_nb[4];
     __shared__ float s_e[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    float2* buf = smo + (size_t)warp * xp;
+    float2* stw = smo;                                  // twiddles [xp / 2]
+    float2* buf = smo + xp / 2 + (size_t)warp * xp;
+    for (int i = threadIdx.x; i < xp / 2; i += blockDim.x) stw[i] = twx[i];
+    __syncthreads();
     const int k = blockIdx.x, fl = blockIdx.y, f = frame_base + fl;
     const float2* Cfk = C + ((size_t)fl * nt + k) * zp * xp;
     float best = -1.f;
     int bidx = 0x7fffffff;
     for (int z = warp; z < zp; z += nwarp) {
-        mo_row_mag(Cfk + (size_t)z * xp, buf, xp, logx, twx, lane);
+        mo_row_mag(Cfk + (size_t)z * xp, buf, xp, logx, stw, lane);
         for (int x = lane; x < xp; x += 32) {
             const float2 v = buf[x];
             const float m = v.x * v.x + v.y * v.y;
@@ -211,7 +300,7 @@ __global__ void __launch_bounds__(256) k_mo_peak(const float2* __restrict__ C, c
     // neighbours: rows iz - 1 and iz + 1 at ix, row iz at ix - 1 and ix + 1 (circular)
     const int rows[3] = {(iz + zp - 1) & (zp - 1), iz, (iz + 1) & (zp - 1)};
     for (int r = 0; r < 3; ++r) {
-        mo_row_mag(Cfk + (size_t)rows[r] * xp, buf, xp, logx, twx, lane);
+        mo_row_mag(Cfk + (size_t)rows[r] * xp, buf, xp, logx, stw, lane);
         if (lane == 0) {
             auto mag = [&](int x) {
                 const float2 v = buf[x];
@@ -305,12 +394,12 @@ rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slice
     float* S = reinterpret_cast<float*>((char*)E + up(nE * 4));
     float* shifts = shifts_out ? shifts_out : S;
 
-    const size_t smem_cols = (size_t)zp * MO_TP * sizeof(float2);
+    const size_t smem_cols = ((size_t)zp * MO_TP + zp / 2) * sizeof(float2);
+    const size_t smem_rows = ((size_t)8 * xp + xp / 2) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_mo_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols);
     if (e != cudaSuccess) return cuda_check(h, e, "motion column smem attribute");
     k_mo_twiddles<<<(unsigned)((n_tw + 255) / 256), 256, 0, h->stream>>>(xp, zp, tw);
-    k_mo_rows<<<dim3((nzs + 7) / 8, nt, F), 256, 8 * xp * sizeof(float2), h->stream>>>(slices, nt, nzs, xp, logx, tw,
-                                                                                      B, E);
+    k_mo_rows<<<dim3((nzs + 7) / 8, nt, F), 256, smem_rows, h->stream>>>(slices, nt, nzs, xp, logx, tw, B, E);
     // reference spectrum (frame 0)
     k_mo_cols<<<dim3(xp / MO_TILE, nt, 1), 256, smem_cols, h->stream>>>(B, nt, nzs, xp, zp, logz, tw + xp / 2, 0,
                                                                          nullptr, REF);
@@ -318,8 +407,7 @@ rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slice
         const int nf = std::min(chunk, F - f0);
         k_mo_cols<<<dim3(xp / MO_TILE, nt, nf), 256, smem_cols, h->stream>>>(B, nt, nzs, xp, zp, logz, tw + xp / 2,
                                                                               f0, REF, Cb);
-        k_mo_peak<<<dim3(nt, nf), 256, 8 * xp * sizeof(float2), h->stream>>>(Cb, E, nt, nzs, xp, zp, logx, tw, f0,
-                                                                             shifts, peaks);
+        k_mo_peak<<<dim3(nt, nf), 256, smem_rows, h->stream>>>(Cb, E, nt, nzs, xp, zp, logx, tw, f0, shifts, peaks);
     }
     k_mo_combine<<<(F + 127) / 128, 128, 0, h->stream>>>(shifts, F, g.K, g.pitch, g.dz / g.us, motion);
     return cuda_check(h, cudaGetLastError(), "motion kernels");
