@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--cpu-sample-frames", type=int, default=4)
     ap.add_argument("--frames", type=int, default=0, help="override the ensemble length (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision / batched / learned forms")
+    ap.add_argument("--no-next-rows", action="store_true", help="skip tracking and motion estimation")
     return ap.parse_args()
 
 
@@ -410,9 +411,9 @@ def main():
         forms["reduced"] = reduced_form(R, L, sess, rf, F, prm, max(3, args.warmup), K, stream)
         forms["batched"] = batched_form(R, L, dev, stream, K)
         forms["learned"] = learned_form(R, L, sess, planes, F, g, dev, stream, peaks)
-    track = tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K) if rank == 0 and not args.no_forms else None
-    motion = motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream, K) \
-        if rank == 0 and not args.no_forms else None
+    next_rows = rank == 0 and not args.no_next_rows and not reduced
+    track = tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K) if next_rows else None
+    motion = motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream, K) if next_rows else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
@@ -485,7 +486,7 @@ def motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream,
     m = motion.cpu().numpy()
     t = [f / 400.0 for f in range(F)]
     truth = [w.tissue_motion_amp * math.sin(2 * math.pi * w.tissue_motion_hz * x) for x in t]
-    err = [abs(a - b) for a, b in zip(m[:, 2], truth)]
+    err = [abs(float(a) - b) for a, b in zip(m[:, 2], truth)]
     return {"ms_per_ensemble": round(e0.elapsed_time(e1) / K, 4), "frames": F,
             "axial_rms_error_um": round(1e6 * math.sqrt(sum(e * e for e in err) / F), 3),
             "axial_max_error_um": round(1e6 * max(err), 3),
