@@ -332,6 +332,25 @@ rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, 
                         ulm_loc3d* out3d, int cap3d, int* n3d_dev);
 
 /* ---------------------------------------------------------------------- */
+/* Eigen-based SVD clutter filter on the Stage-1 slices (Sec. II-A2)       */
+/* ---------------------------------------------------------------------- */
+
+/* In place on slices [F][2K][nzs][N] C32 (as rca_stage1 writes them; use
+ * slices of channel data ingested with RCA_CLUTTER_NONE).  For each
+ * transmission k the frames' slices are the columns of the Casorati matrix
+ * X_k (nzs N pixels x F frames); the filter removes the subspace of the
+ * `rank` largest eigenvalues of the frame covariance C_k = X_k^H X_k:
+ * X_k <- X_k - X_k Q Q^H, Q an orthonormal basis of that subspace found by
+ * `iterations` steps of orthogonal iteration Q <- orth(C_k Q) from fixed
+ * start vectors (the projection depends on the subspace only).  The paper
+ * gives no rank or threshold: `rank` is the caller's (0 leaves the slices
+ * unchanged).  FP32 arithmetic throughout.
+ *   Limits: rank in [0, 32] and below F; iterations in [1, 1000]
+ *   (INVALID_ARG); F x (rank + 1) complex values twice must fit the
+ *   eigenspace kernel's shared memory (F (rank + 1) <= 12 800, UNSUPPORTED). */
+rca_status rca_clutter_svd(rca_handle* h, const rca_tables* t, void* slices, int n_frames, int rank, int iterations);
+
+/* ---------------------------------------------------------------------- */
 /* Projection-based rigid motion estimation (Sec. II-A3, Fig. 1d)          */
 /* ---------------------------------------------------------------------- */
 

@@ -114,6 +114,7 @@ SIGNATURES = {
     "ulm_localize": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_params), _P, _I, _P, _P, _I, _P]),
     "ulm_density_shape": (_S, [_P, C.c_double, _P]),
     "rca_motion_estimate": (_S, [_P, _P, _P, _I, _P, _P, _P]),
+    "rca_clutter_svd": (_S, [_P, _P, _P, _I, _I, _I]),
     "ulm_track": (_S, [_P, _P, _P, _P, _I, _I, C.POINTER(ulm_track_params), _P, _I, _P, _P]),
     "ulm_cnn_create": (_S, [_P, C.POINTER(ulm_cnn_desc), C.POINTER(_P)]),
     "ulm_cnn_destroy": (_S, [_P]),

@@ -30,6 +30,7 @@ UNITS = {
     "cnn.cu": [],
     "track.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
     "motion.cu": [],
+    "svd.cu": [],
 }
 
 

@@ -512,6 +512,18 @@ extern "C" rca_status ulm_pair3d_noalloc(rca_handle* h, const rca_tables* t, con
     return launch_pair3d_noalloc(h, t, L, n2d, cap2d, F, out, cap3d, n3d);
 }
 
+extern "C" rca_status rca_clutter_svd(rca_handle* h, const rca_tables* t, void* slices, int F, int rank,
+                                      int iterations)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!slices) return set_error(h, RCA_ERR_INVALID_ARG, "null slices");
+    if (F > 65535) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 65535 frames in one call");
+    DeviceGuard dg(h->device);
+    return launch_clutter_svd(h, t, (float2*)slices, F, rank, iterations);
+}
+
 extern "C" rca_status rca_motion_estimate(rca_handle* h, const rca_tables* t, const void* slices, int F,
                                           float* motion, float* shifts, int* peaks)
 {

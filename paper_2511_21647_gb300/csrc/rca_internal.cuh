@@ -51,6 +51,7 @@ enum WsSlot {
     WS_MISC,       // small scratch
     WS_TRACK,      // tracking: frame offsets, links, flags, positions, per-localisation tracks
     WS_MOTION,     // motion estimation: twiddles, row spectra, reference spectrum, correlations
+    WS_SVD,        // clutter filter: partial covariances, covariances, subspace bases
     WS_COUNT
 };
 
@@ -233,6 +234,7 @@ rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca
 rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
                          float2* slices);
 void density_shape(const GeomDev& g, double voxel, int dims[3]);
+rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices, int F, int nc, int iters);
 rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slices, int F, float* motion,
                          float* shifts, int* peaks);
 rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d, int F,

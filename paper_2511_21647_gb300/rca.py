@@ -195,6 +195,10 @@ def make_track_params(length=10, substeps=10, max_step_m=150e-6, max_turn_deg=45
     return p
 
 
+def rca_clutter_svd(h, t, slices, n_frames, rank, iterations=30):
+    _check(L.load().rca_clutter_svd(h, t, _ptr(slices), n_frames, rank, iterations), h)
+
+
 def rca_motion_estimate(h, t, slices, n_frames, motion, shifts=None, peaks=None):
     _check(L.load().rca_motion_estimate(h, t, _ptr(slices), n_frames, _ptr(motion), _ptr(shifts), _ptr(peaks)), h)
 
