@@ -414,6 +414,7 @@ def main():
     next_rows = rank == 0 and not args.no_next_rows and not reduced
     track = tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K) if next_rows else None
     motion = motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream, K) if next_rows else None
+    svd = svd_step(R, sess, slices, F, stream, K) if next_rows else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
@@ -447,6 +448,7 @@ def main():
             "forms": forms,
             "tracking": track,
             "motion": motion,
+            "clutter_svd": svd,
             "gpu_launches": K * sum(launches.values()),
             "clocks": clk.summary(),
             "localisations": {"n2d": n2d_v, "n3d": n3d_v},
@@ -493,6 +495,29 @@ def motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream,
             "lateral_max_um": round(1e6 * float(abs(m[:, :2]).max()), 3),
             "truth": "tissue displacement 0.2 mm sin(2 pi 1 Hz t), t = frame / 400 Hz, axial",
             "kernels": 5 + 2 * ((F + 63) // 64), "status": R.rca_sync_status(sess.h)}
+
+
+def svd_step(R, sess, slices, F, stream, K, rank=16, iters=30):
+    """Eigen-based SVD clutter filter (Sec. II-A2) on the ensemble's unfiltered
+    Stage-1 slices (as motion_step leaves them), in place; timed beside the
+    step.  Work: the 2K frame covariances (F^2 P / 2 complex products each),
+    the eigenspace iteration, the projection (2 F rank P complex products)."""
+    import torch
+    for _ in range(2):
+        R.rca_clutter_svd(sess.h, sess.t, slices, F, rank, iters)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        R.rca_clutter_svd(sess.h, sess.t, slices, F, rank, iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    nt, P = slices.shape[1], slices.shape[2] * slices.shape[3]
+    flops = nt * (F * F * P * 4.0 + 2 * F * rank * P * 8.0)
+    return {"ms_per_ensemble": round(ms, 4), "rank": rank, "iterations": iters, "frames": F,
+            "gflop": round(flops / 1e9, 1), "tflops": round(flops / (ms / 1e3) / 1e12, 2),
+            "kernels": 4, "status": R.rca_sync_status(sess.h)}
 
 
 def tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K):

@@ -187,16 +187,20 @@ rca_status rca_tables_download(const rca_tables* t, int table_id, void* host_dst
 /* ---------------------------------------------------------------------- */
 
 typedef enum { RCA_MODE_TWO_STAGE = 0, RCA_MODE_DIRECT = 1 } rca_bf_mode;
-typedef enum { RCA_CLUTTER_NONE = 0, RCA_CLUTTER_MEAN = 1 } rca_clutter;
+typedef enum { RCA_CLUTTER_NONE = 0, RCA_CLUTTER_MEAN = 1, RCA_CLUTTER_SVD = 2 } rca_clutter;
 
 typedef struct {
     int mode;      /* rca_bf_mode: TWO_STAGE (the method) or DIRECT (exact slab
                       sums of conventional 3D DAS, no volume; validation and
                       the "what it replaces" baseline) */
     int clutter;   /* rca_clutter: MEAN removes each channel sample's mean over
-                      the ensemble's frames before demodulation */
+                      the ensemble's frames before demodulation; SVD (TWO_STAGE
+                      only) runs rca_clutter_svd on the Stage-1 slices before
+                      Stage 2, as the paper places its filter (Sec. II-A2) */
     int iq_dtype;  /* internal IQ storage: RCA_C32, RCA_C16F or RCA_C16BF */
-    int reserved[5];
+    int svd_rank;        /* SVD: tissue eigenvectors removed (0 .. 32) */
+    int svd_iterations;  /* SVD: orthogonal-iteration steps (0: 30) */
+    int reserved[3];
 } rca_bf_params;
 
 /* Channel data -> IQ: optional mean clutter removal over the F frames, then
@@ -228,8 +232,9 @@ rca_status rca_stage2_project(rca_handle* h, const rca_tables* t, const void* sl
 rca_status rca_direct_project(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_dtype,
                               int n_frames, void* planes, rca_dtype planes_dtype);
 
-/* The whole beamforming path: ingest -> Stage 1 -> Stage 2 + projection (or
- * ingest -> direct) using library workspace for IQ and slices.
+/* The whole beamforming path: ingest -> Stage 1 -> [SVD clutter filter] ->
+ * Stage 2 + projection (or ingest -> direct) using library workspace for IQ
+ * and slices.
  *   rf: [F][2K][E][ns] (F32, F16, or I16 + scale[2K][E]); planes as above.
  * Errors: INVALID_ARG / SHAPE / UNSUPPORTED on the host. */
 rca_status rca_beamform_projections(rca_handle* h, const rca_tables* t, const void* rf,

@@ -29,7 +29,7 @@ RCA_ERR_BOUNDS = 7
 RCA_F32, RCA_I16, RCA_F16, RCA_C32, RCA_C16F, RCA_C16BF = range(6)
 
 RCA_MODE_TWO_STAGE, RCA_MODE_DIRECT = 0, 1
-RCA_CLUTTER_NONE, RCA_CLUTTER_MEAN = 0, 1
+RCA_CLUTTER_NONE, RCA_CLUTTER_MEAN, RCA_CLUTTER_SVD = 0, 1, 2
 ULM_ENH_XDOPPLER, ULM_ENH_COHERENT = 0, 1
 
 (RCA_TAB_TX_F64, RCA_TAB_RX_F64, RCA_TAB_TX_Q16, RCA_TAB_RX_Q16, RCA_TAB_W, RCA_TAB_DMAX,
@@ -45,7 +45,8 @@ class rca_geometry_desc(C.Structure):
 
 
 class rca_bf_params(C.Structure):
-    _fields_ = [("mode", C.c_int), ("clutter", C.c_int), ("iq_dtype", C.c_int), ("reserved", C.c_int * 5)]
+    _fields_ = [("mode", C.c_int), ("clutter", C.c_int), ("iq_dtype", C.c_int), ("svd_rank", C.c_int),
+                ("svd_iterations", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class ulm_params(C.Structure):

@@ -435,17 +435,29 @@ extern "C" rca_status rca_beamform_projections(rca_handle* h, const rca_tables* 
     if (!is_real_rf(rf_t)) return set_error(h, RCA_ERR_UNSUPPORTED, "rf dtype must be F32, F16 or I16");
     if (rf_t == RCA_I16 && !scale) return set_error(h, RCA_ERR_INVALID_ARG, "int16 rf needs a scale array");
     if (!is_complex(prm->iq_dtype) || !is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "complex dtypes required");
-    if (prm->clutter != RCA_CLUTTER_NONE && prm->clutter != RCA_CLUTTER_MEAN) return set_error(h, RCA_ERR_INVALID_ARG, "bad clutter mode");
+    if (prm->clutter != RCA_CLUTTER_NONE && prm->clutter != RCA_CLUTTER_MEAN && prm->clutter != RCA_CLUTTER_SVD)
+        return set_error(h, RCA_ERR_INVALID_ARG, "bad clutter mode");
+    const bool svd = prm->clutter == RCA_CLUTTER_SVD;
+    if (svd && prm->mode != RCA_MODE_TWO_STAGE)
+        return set_error(h, RCA_ERR_INVALID_ARG, "the SVD clutter filter acts on Stage-1 slices (TWO_STAGE only)");
+    if (svd && (prm->svd_rank < 0 || prm->svd_rank > 32 || prm->svd_rank >= F || prm->svd_iterations < 0 ||
+                prm->svd_iterations > 1000))
+        return set_error(h, RCA_ERR_INVALID_ARG, "SVD rank %d / iterations %d out of range", prm->svd_rank,
+                         prm->svd_iterations);
     DeviceGuard dg(h->device);
     const GeomDev& g = t->gd;
     const rca_dtype iq_t = (rca_dtype)prm->iq_dtype;
     void* iq = ws_get(h, WS_IQ, (size_t)F * 2 * g.K * g.N * g.ns * dtype_size(iq_t), &st);
     if (!iq) return st;
-    if ((st = launch_ingest(h, t, rf, rf_t, scale, F, prm->clutter, iq, iq_t)) != RCA_OK) return st;
+    if ((st = launch_ingest(h, t, rf, rf_t, scale, F, svd ? RCA_CLUTTER_NONE : prm->clutter, iq, iq_t)) != RCA_OK)
+        return st;
     if (prm->mode == RCA_MODE_DIRECT) return launch_direct(h, t, iq, iq_t, F, planes, pt);
     float2* slices = (float2*)ws_get(h, WS_SLICES, (size_t)F * 2 * g.K * g.nzs * g.N * sizeof(float2), &st);
     if (!slices) return st;
     if ((st = launch_stage1(h, t, iq, iq_t, F, slices)) != RCA_OK) return st;
+    if (svd && (st = launch_clutter_svd(h, t, slices, F, prm->svd_rank,
+                                        prm->svd_iterations > 0 ? prm->svd_iterations : 30)) != RCA_OK)
+        return st;
     return launch_stage2(h, t, slices, F, planes, pt);
 }
 

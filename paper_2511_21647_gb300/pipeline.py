@@ -82,11 +82,12 @@ class RcaSession:
         return pl
 
     def beamform(self, rf, rf_dtype=L.RCA_F32, scale=None, mode=L.RCA_MODE_TWO_STAGE,
-                 clutter=L.RCA_CLUTTER_MEAN, iq_dtype=L.RCA_C32, planes_dtype=L.RCA_C32, out=None):
+                 clutter=L.RCA_CLUTTER_MEAN, iq_dtype=L.RCA_C32, planes_dtype=L.RCA_C32, out=None, svd_rank=0,
+                 svd_iterations=0):
         F = rf.shape[0]
         pl = out if out is not None else complex_buffer(self.planes_shape(F), planes_dtype, self.device)
-        R.rca_beamform_projections(self.h, self.t, rf, rf_dtype, scale, F, R.bf_params(mode, clutter, iq_dtype),
-                                   pl, planes_dtype)
+        R.rca_beamform_projections(self.h, self.t, rf, rf_dtype, scale, F,
+                                   R.bf_params(mode, clutter, iq_dtype, svd_rank, svd_iterations), pl, planes_dtype)
         return pl
 
     def enhance(self, planes, planes_dtype=L.RCA_C32, enh=L.ULM_ENH_XDOPPLER):

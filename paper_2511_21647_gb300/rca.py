@@ -156,9 +156,11 @@ def rca_direct_project(h, t, iq, iq_dtype, n_frames, planes, planes_dtype):
     _check(L.load().rca_direct_project(h, t, _ptr(iq), iq_dtype, n_frames, _ptr(planes), planes_dtype), h)
 
 
-def bf_params(mode=L.RCA_MODE_TWO_STAGE, clutter=L.RCA_CLUTTER_MEAN, iq_dtype=L.RCA_C32) -> rca_bf_params:
+def bf_params(mode=L.RCA_MODE_TWO_STAGE, clutter=L.RCA_CLUTTER_MEAN, iq_dtype=L.RCA_C32, svd_rank=0,
+              svd_iterations=0) -> rca_bf_params:
     p = rca_bf_params()
     p.mode, p.clutter, p.iq_dtype = mode, clutter, iq_dtype
+    p.svd_rank, p.svd_iterations = svd_rank, svd_iterations
     return p
 
 

@@ -95,3 +95,31 @@ def test_argument_errors(tiny):
             with pytest.raises(rca.RcaError) as e:
                 rca.rca_clutter_svd(s.h, s.t, t, F, rank, iters)
             assert e.value.status == _lib.RCA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("rank", [1])
+def test_beamform_with_svd_clutter_filter_end_to_end(tiny, tiny_rf, rank):
+    """channel data -> IQ without clutter removal -> Stage 1 -> SVD filter ->
+    Stage 2 + projection, through the one-call beamformer, against the oracle
+    chained the same way (its filter on its own FP64 slices).  The tiny
+    ensemble's tissue is static: one eigenvalue, then the blood and noise at
+    1e-6 of it, whose next ratios (0.82, 0.93) are within FP32's resolution of
+    a covariance that size, so only the rank-1 subspace is determined in FP32."""
+    import oracle as O
+    from paper_2511_21647_gb300 import _lib as L
+    from paper_2511_21647_gb300.pipeline import RcaSession, to_complex128
+    g = tiny.geom
+    rf = tiny_rf.rf.numpy()
+    iq = O.demod(g, rf, remove_mean=False)
+    sl = np.stack([O.stage1(g, iq[f]) for f in range(rf.shape[0])])
+    flt = OS.filter_slices(sl, rank)
+    ref = np.stack([O.stage2_project(g, flt[f]) for f in range(rf.shape[0])])
+    with RcaSession(g) as s:
+        pl = to_complex128(s.beamform(tiny_rf.rf.cuda(), clutter=L.RCA_CLUTTER_SVD, svd_rank=rank))
+        assert s.sync_status() == 0
+        with pytest.raises(Exception):
+            s.beamform(tiny_rf.rf.cuda(), mode=L.RCA_MODE_DIRECT, clutter=L.RCA_CLUTTER_SVD, svd_rank=rank)
+    e = np.linalg.norm(pl - ref) / np.linalg.norm(ref)
+    print(f"\nSVD rank {rank} through the beamformer: planes rel-L2 {e:.2e}, top eigenvalue ratios "
+          f"{OS.spectrum(sl, 0)[:rank + 2] / OS.spectrum(sl, 0)[0]}")
+    assert e < 1e-4
