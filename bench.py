@@ -413,6 +413,7 @@ def main():
         forms["learned"] = learned_form(R, L, sess, planes, F, g, dev, stream, peaks)
     next_rows = rank == 0 and not args.no_next_rows and not reduced
     track = tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K) if next_rows else None
+    sep = separation_step(R, L, sess, w, planes, F, prm, cap2d, cap3d, stream, K) if next_rows else None
     motion = motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream, K) if next_rows else None
     svd = svd_step(R, sess, slices, F, stream, K) if next_rows else None
     cpu = None
@@ -447,6 +448,7 @@ def main():
             "e2e": e2e,
             "forms": forms,
             "tracking": track,
+            "separation": sep,
             "motion": motion,
             "clutter_svd": svd,
             "gpu_launches": K * sum(launches.values()),
@@ -518,6 +520,64 @@ def svd_step(R, sess, slices, F, stream, K, rank=16, iters=30):
     return {"ms_per_ensemble": round(ms, 4), "rank": rank, "iterations": iters, "frames": F,
             "gflop": round(flops / 1e9, 1), "tflops": round(flops / (ms / 1e3) / 1e12, 2),
             "kernels": 4, "status": R.rca_sync_status(sess.h)}
+
+
+def separation_step(R, L, sess, w, planes, F, prm, cap2d, cap3d, stream, K, n_bands=3):
+    """Microbubble separation (Sec. II-A5) of the step's FP32 planes into three
+    equal speed bands over (0, 200] Hz x up / down, fused with each subset's
+    XDoppler enhancement (ulm_separate_enhance), then each subset's detection
+    and pairing (the paper's Up3 / Down3 localisation); timed beside the step.
+    Algorithmic bytes: planes read once, six amplitude stacks written; work:
+    one forward and six inverse F-point transforms per plane pixel
+    (5 F log2 F flop each, the conventional FFT count)."""
+    import math
+    import torch
+    g = w.geom
+    sp = R.make_sep_params(w.frame_rate, n_bands)
+    ns = 2 * n_bands
+    A = torch.empty((ns,) + tuple(sess.a_shape(F)), dtype=torch.float32, device=planes.device)
+    M = torch.empty((ns, F), dtype=torch.float32, device=planes.device)
+    bufs = [sess.loc_buffers(cap2d, cap3d) for _ in range(ns)]
+
+    def sep():
+        R.ulm_separate_enhance(sess.h, sess.t, planes, L.RCA_C32, F, sp, L.ULM_ENH_XDOPPLER, A, M)
+
+    def loc():
+        for s in range(ns):
+            out2d, n2d, out3d, n3d = bufs[s]
+            R.ulm_detect2d(sess.h, sess.t, A[s], M[s], F, prm, out2d, cap2d, n2d)
+            R.ulm_pair3d(sess.h, sess.t, out2d, n2d, cap2d, F, out3d, cap3d, n3d)
+
+    for _ in range(2):
+        sep()
+        loc()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_sep = t_loc = 0.0
+    for _ in range(K):
+        ev[0].record(stream)
+        sep()
+        ev[1].record(stream)
+        loc()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t_sep += ev[0].elapsed_time(ev[1])
+        t_loc += ev[1].elapsed_time(ev[2])
+    ms_sep, ms_loc = t_sep / K, t_loc / K
+    npx = planes.numel() // (2 * F)
+    bytes_ = planes.numel() * planes.element_size() + A.numel() * 4
+    flop = 7 * 5.0 * F * math.log2(F) * npx
+    import json as _json
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = _json.load(open(pk)).get("hbm_gbs") if os.path.exists(pk) else None
+    n2d = [int(b[1].item()) for b in bufs]
+    n3d = [int(b[3].item()) for b in bufs]
+    return {"ms_per_ensemble": round(ms_sep, 4), "subsets": ns, "bands_hz": [round(x, 3) for x in sp.edges_hz[:n_bands + 1]],
+            "alg_GBps": round(bytes_ / (ms_sep / 1e3) / 1e9, 1),
+            "hbm_frac": round(bytes_ / (ms_sep / 1e3) / 1e9 / peak, 4) if peak else None,
+            "fft_TFLOPs": round(flop / (ms_sep / 1e3) / 1e12, 2),
+            "localise_subsets_ms": round(ms_loc, 4), "n2d": n2d, "n3d": n3d,
+            "kernels": 1, "status": R.rca_sync_status(sess.h)}
 
 
 def tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K):

@@ -356,6 +356,48 @@ rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, 
 rca_status rca_clutter_svd(rca_handle* h, const rca_tables* t, void* slices, int n_frames, int rank, int iterations);
 
 /* ---------------------------------------------------------------------- */
+/* Microbubble separation on the projection planes (Sec. II-A5, Fig. 1c)   */
+/* ---------------------------------------------------------------------- */
+
+#define ULM_SEP_MAX_BANDS 4
+
+/* Speed bands of the separation.  Bin j of the F-point slow-time DFT has the
+ * signed index k = j (2 j < F) or j - F (2 j > F) and the Doppler frequency
+ * k prf_hz / F; band b holds the bins with
+ *   edges_hz[b] < |k| prf_hz / F <= edges_hz[b + 1]      (b < n_bands),
+ * evaluated in double precision.  k > 0 (flow toward the array, decreasing
+ * depth: the planes' phase grows as the echo delay shrinks) is "up", k < 0
+ * "down"; DC and, for even F, the Nyquist bin belong to no subset.  The
+ * paper separates into three speed ranges and two directions but prints no
+ * band edges: equal bands over (0, prf/2] are edges_hz[i] = i prf / (2 n). */
+typedef struct {
+    double prf_hz;                            /* frame rate (Hz, > 0) */
+    int32_t n_bands;                          /* 1 .. ULM_SEP_MAX_BANDS (paper: 3) */
+    int32_t reserved;
+    double edges_hz[ULM_SEP_MAX_BANDS + 1];   /* n_bands + 1 increasing edges, edges_hz[0] >= 0 */
+} ulm_sep_params;
+
+/* Subsets of the planes: for every plane pixel, the F-frame signal is
+ * transformed, each subset keeps its bins (rectangular mask) and is
+ * transformed back (1/F on the inverse).  Subset index = direction n_bands +
+ * band, direction 0 up, 1 down.
+ *   planes: [F][2][2][S][nz][N] (C32 / C16F / C16BF); subsets: device
+ *   [2 n_bands][F][2][2][S][nz][N] C32.  FP32 transforms.
+ * Limits: F <= 512 with prime factors 2, 3 and 5 only (UNSUPPORTED
+ * otherwise); bad bands or prf: INVALID_ARG. */
+rca_status ulm_separate(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype planes_dtype, int n_frames,
+                        const ulm_sep_params* prm, void* subsets);
+
+/* Separation fused with each subset's enhancement: the subsets are never
+ * stored; for each subset the XDoppler (or coherent) amplitude of
+ * ulm_enhance and its per-frame maxima are written, ready for ulm_detect2d
+ * on A + s F 2 S nz N and M + s F.
+ *   A: device [2 n_bands][F][2][S][nz][N] float; M: device [2 n_bands][F]
+ *   float.  Limits as ulm_separate; enh as ulm_enhance. */
+rca_status ulm_separate_enhance(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype planes_dtype,
+                                int n_frames, const ulm_sep_params* prm, int enh, float* A, float* M);
+
+/* ---------------------------------------------------------------------- */
 /* Projection-based rigid motion estimation (Sec. II-A3, Fig. 1d)          */
 /* ---------------------------------------------------------------------- */
 

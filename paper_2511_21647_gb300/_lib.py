@@ -71,6 +71,12 @@ class ulm_track_params(C.Structure):
 
 
 ULM_TRACK_MAX_LEN = 64
+ULM_SEP_MAX_BANDS = 4
+
+
+class ulm_sep_params(C.Structure):
+    _fields_ = [("prf_hz", C.c_double), ("n_bands", C.c_int32), ("reserved", C.c_int32),
+                ("edges_hz", C.c_double * (ULM_SEP_MAX_BANDS + 1))]
 TRACK = np.dtype([("first", "<i4"), ("frame0", "<i4"), ("accepted", "<i4"), ("reserved", "<i4"),
                   ("a", "<f8", (3, 3)), ("mean_speed", "<f8"), ("cos_turn", "<f8"), ("speed_range", "<f8")])
 assert TRACK.itemsize == 112
@@ -116,6 +122,8 @@ SIGNATURES = {
     "ulm_density_shape": (_S, [_P, C.c_double, _P]),
     "rca_motion_estimate": (_S, [_P, _P, _P, _I, _P, _P, _P]),
     "rca_clutter_svd": (_S, [_P, _P, _P, _I, _I, _I]),
+    "ulm_separate": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_sep_params), _P]),
+    "ulm_separate_enhance": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_sep_params), _I, _P, _P]),
     "ulm_track": (_S, [_P, _P, _P, _P, _I, _I, C.POINTER(ulm_track_params), _P, _I, _P, _P]),
     "ulm_cnn_create": (_S, [_P, C.POINTER(ulm_cnn_desc), C.POINTER(_P)]),
     "ulm_cnn_destroy": (_S, [_P]),

@@ -31,6 +31,7 @@ UNITS = {
     "track.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
     "motion.cu": [],
     "svd.cu": [],
+    "separate.cu": [],
 }
 
 

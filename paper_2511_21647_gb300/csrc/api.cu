@@ -548,6 +548,30 @@ extern "C" rca_status rca_motion_estimate(rca_handle* h, const rca_tables* t, co
     return launch_motion(h, t, (const float2*)slices, F, motion, shifts, peaks);
 }
 
+extern "C" rca_status ulm_separate(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
+                                   const ulm_sep_params* prm, void* subsets)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!planes || !prm || !subsets) return set_error(h, RCA_ERR_INVALID_ARG, "null planes, parameters or subsets");
+    if (!is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
+    DeviceGuard dg(h->device);
+    return launch_separate(h, t, planes, pt, F, prm, ULM_ENH_XDOPPLER, (float2*)subsets, nullptr, nullptr);
+}
+
+extern "C" rca_status ulm_separate_enhance(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
+                                           const ulm_sep_params* prm, int enh, float* A, float* M)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!planes || !prm || !A || !M) return set_error(h, RCA_ERR_INVALID_ARG, "null planes, parameters, A or M");
+    if (!is_complex(pt)) return set_error(h, RCA_ERR_UNSUPPORTED, "planes dtype must be C32, C16F or C16BF");
+    DeviceGuard dg(h->device);
+    return launch_separate(h, t, planes, pt, F, prm, enh, nullptr, A, M);
+}
+
 extern "C" rca_status ulm_density_shape(const rca_tables* t, double voxel_m, int32_t dims[3])
 {
     if (!t || !dims || !(voxel_m > 0.0)) return RCA_ERR_INVALID_ARG;

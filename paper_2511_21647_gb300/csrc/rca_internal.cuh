@@ -235,6 +235,8 @@ rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca
                          float2* slices);
 void density_shape(const GeomDev& g, double voxel, int dims[3]);
 rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices, int F, int nc, int iters);
+rca_status launch_separate(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
+                           const ulm_sep_params* prm, int enh, float2* sub, float* A, float* M);
 rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slices, int F, float* motion,
                          float* shifts, int* peaks);
 rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d, int F,

@@ -97,6 +97,23 @@ class RcaSession:
         R.ulm_enhance(self.h, self.t, planes, planes_dtype, F, enh, A, M)
         return A, M
 
+    def separate(self, planes, prm, planes_dtype=L.RCA_C32):
+        """complex subsets [2 nb][F][2][2][S][nz][N] (Sec. II-A5)"""
+        F = planes.shape[0]
+        out = torch.empty((2 * prm.n_bands,) + tuple(self.planes_shape(F)) + (2,), dtype=torch.float32,
+                          device=self.device)
+        R.ulm_separate(self.h, self.t, planes, planes_dtype, F, prm, out)
+        return out
+
+    def separate_enhance(self, planes, prm, planes_dtype=L.RCA_C32, enh=L.ULM_ENH_XDOPPLER):
+        """per-subset amplitude A [2 nb][F][2][S][nz][N] and maxima M [2 nb][F]"""
+        F = planes.shape[0]
+        ns = 2 * prm.n_bands
+        A = torch.empty((ns,) + tuple(self.a_shape(F)), dtype=torch.float32, device=self.device)
+        M = torch.empty((ns, F), dtype=torch.float32, device=self.device)
+        R.ulm_separate_enhance(self.h, self.t, planes, planes_dtype, F, prm, enh, A, M)
+        return A, M
+
     def detect2d(self, A, M, prm, cap2d=1 << 16, want_ncc=False):
         F = A.shape[0]
         out = torch.zeros((max(cap2d, 1), 10), dtype=torch.int32, device=self.device)

@@ -197,6 +197,29 @@ def make_track_params(length=10, substeps=10, max_step_m=150e-6, max_turn_deg=45
     return p
 
 
+def make_sep_params(prf_hz, n_bands=3, edges_hz=None) -> L.ulm_sep_params:
+    """Speed bands of the separation; equal bands over (0, prf / 2] unless
+    edges_hz (n_bands + 1 increasing values) is given."""
+    if edges_hz is None:
+        edges_hz = [i * prf_hz / (2.0 * n_bands) for i in range(n_bands + 1)]
+    if len(edges_hz) != n_bands + 1:
+        raise ValueError("edges_hz needs n_bands + 1 values")
+    p = L.ulm_sep_params()
+    p.prf_hz, p.n_bands = prf_hz, n_bands
+    for i, e in enumerate(edges_hz):
+        p.edges_hz[i] = e
+    return p
+
+
+def ulm_separate(h, t, planes, planes_dtype, n_frames, prm, subsets):
+    _check(L.load().ulm_separate(h, t, _ptr(planes), planes_dtype, n_frames, C.byref(prm), _ptr(subsets)), h)
+
+
+def ulm_separate_enhance(h, t, planes, planes_dtype, n_frames, prm, enh, A, M):
+    _check(L.load().ulm_separate_enhance(h, t, _ptr(planes), planes_dtype, n_frames, C.byref(prm), enh, _ptr(A),
+                                         _ptr(M)), h)
+
+
 def rca_clutter_svd(h, t, slices, n_frames, rank, iterations=30):
     _check(L.load().rca_clutter_svd(h, t, _ptr(slices), n_frames, rank, iterations), h)
 
