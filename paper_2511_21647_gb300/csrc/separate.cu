@@ -11,8 +11,9 @@
 //   forward transform, spectrum kept in registers (MX values per thread);
 //   per subset: the masked spectrum, scaled by 1/F, is written back and
 //   transformed inversely; then either the complex subset is stored
-//   (SP_OUT_COMPLEX) or its XDoppler / coherent amplitude and per-frame maxima
-//   (SP_OUT_ENHANCE), which is what a subset's localisation reads.
+//   (SP_OUT_COMPLEX) or its XDoppler (SP_OUT_XDOPPLER) or coherent
+//   (SP_OUT_COHERENT) amplitude and per-frame maxima, which is what a
+//   subset's localisation reads.
 // Shared-memory traffic per subset and group: one write of the masked
 // spectrum, two accesses per element per pass, one read for the output.
 #include <algorithm>
@@ -29,44 +30,54 @@ namespace {
 #define SP_THREADS 256
 #define SP_MAXP 10              // passes
 #define SP_MAXF 512
+#define SP_WR 87                // W_R^m tables of the composite radices 6, 8, 10, 12, 15, 16, 20
 #define SP_OUT_COMPLEX 0
-#define SP_OUT_ENHANCE 1
+#define SP_OUT_XDOPPLER 1
+#define SP_OUT_COHERENT 2
 
 struct SepConst {
     int F, npass, nsub, enh;
     int radix[SP_MAXP];
+    int twoff[SP_MAXP];             // pass p's twiddle table in shared memory (float2 offset)
+    int ntw;                        // entries of all pass tables
     float s3, c51, c52, s51, s52;   // sin(2pi/3); cos, sin of 2pi/5 and 4pi/5
+    float2 wr[SP_WR];               // exp(-2 pi i m / R) of each composite radix R, m < R
     signed char bin[SP_MAXF];       // subset of DFT bin j, -1 none
 };
 
-struct Codelet {
-    float s3, c51, c52, s51, s52;
-};
+// offset of radix R's table in SepConst::wr
+__host__ __device__ constexpr int wr_off(int R)
+{
+    return R == 6 ? 0 : R == 8 ? 6 : R == 10 ? 14 : R == 12 ? 24 : R == 15 ? 36 : R == 16 ? 51 : R == 20 ? 67 : -1;
+}
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 f2scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 f2fma(float2 a, float s, float2 b) { return make_float2(fmaf(a.x, s, b.x), fmaf(a.y, s, b.y)); }
-__device__ __forceinline__ float2 f2mul(float2 a, float2 b)
+// a w (forward) or a conj(w) (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 twmul(float2 a, float2 w)
 {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+    return INV ? make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y))
+               : make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+// sqrt.approx (relative error about 2^-23; 0 -> 0)
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 // -i v (forward) / +i v (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 rot(float2 v) { return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x); }
-// twiddle exp(-+ 2 pi i m / F) from the forward table
-template <bool INV>
-__device__ __forceinline__ float2 twid(const float2* tw, int m)
-{
-    const float2 w = tw[m];
-    return INV ? make_float2(w.x, -w.y) : w;
-}
 
 // R-point DFT in registers, y_k = sum_n x_n exp(-+2 pi i n k / R)
 template <int R, bool INV> struct Dft;
 
 template <bool INV> struct Dft<2, INV> {
-    static __device__ __forceinline__ void run(float2 (&v)[2], const Codelet&, const float2*, int)
+    static __device__ __forceinline__ void run(float2 (&v)[2], const SepConst&)
     {
         const float2 a = v[0];
         v[0] = f2add(a, v[1]);
@@ -75,7 +86,7 @@ template <bool INV> struct Dft<2, INV> {
 };
 
 template <bool INV> struct Dft<3, INV> {
-    static __device__ __forceinline__ void run(float2 (&v)[3], const Codelet& c, const float2*, int)
+    static __device__ __forceinline__ void run(float2 (&v)[3], const SepConst& c)
     {
         const float2 t = f2add(v[1], v[2]);
         const float2 m = f2fma(t, -0.5f, v[0]);
@@ -87,7 +98,7 @@ template <bool INV> struct Dft<3, INV> {
 };
 
 template <bool INV> struct Dft<4, INV> {
-    static __device__ __forceinline__ void run(float2 (&v)[4], const Codelet&, const float2*, int)
+    static __device__ __forceinline__ void run(float2 (&v)[4], const SepConst&)
     {
         const float2 t0 = f2add(v[0], v[2]), t1 = f2sub(v[0], v[2]);
         const float2 t2 = f2add(v[1], v[3]), t3 = rot<INV>(f2sub(v[1], v[3]));
@@ -99,7 +110,7 @@ template <bool INV> struct Dft<4, INV> {
 };
 
 template <bool INV> struct Dft<5, INV> {
-    static __device__ __forceinline__ void run(float2 (&v)[5], const Codelet& c, const float2*, int)
+    static __device__ __forceinline__ void run(float2 (&v)[5], const SepConst& c)
     {
         const float2 a1 = f2add(v[1], v[4]), b1 = f2sub(v[1], v[4]);
         const float2 a2 = f2add(v[2], v[3]), b2 = f2sub(v[2], v[3]);
@@ -116,19 +127,21 @@ template <bool INV> struct Dft<5, INV> {
 };
 
 // R = R1 R2 by one Cooley-Tukey split in registers: n = R2 n1 + n2,
-// k = k1 + R1 k2; inner twiddles W_R^(n2 k1) = tw[n2 k1 F / R] (twr = F / R).
+// k = k1 + R1 k2; the inner twiddles W_R^(n2 k1) are kernel-parameter
+// constants at compile-time offsets.
 template <int R1, int R2, bool INV> struct DftC {
-    static __device__ __forceinline__ void run(float2 (&v)[R1 * R2], const Codelet& c, const float2* tw, int twr)
+    static __device__ __forceinline__ void run(float2 (&v)[R1 * R2], const SepConst& c)
     {
+        constexpr int W0 = wr_off(R1 * R2);
 #pragma unroll
         for (int n2 = 0; n2 < R2; ++n2) {
             float2 a[R1];
 #pragma unroll
             for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[R2 * n1 + n2];
-            Dft<R1, INV>::run(a, c, tw, twr);
+            Dft<R1, INV>::run(a, c);
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1)
-                v[R2 * k1 + n2] = (n2 * k1 == 0) ? a[k1] : f2mul(a[k1], twid<INV>(tw, n2 * k1 * twr));
+                v[R2 * k1 + n2] = (n2 * k1 == 0) ? a[k1] : twmul<INV>(a[k1], c.wr[W0 + n2 * k1]);
         }
         float2 o[R1 * R2];
 #pragma unroll
@@ -136,7 +149,7 @@ template <int R1, int R2, bool INV> struct DftC {
             float2 b[R2];
 #pragma unroll
             for (int n2 = 0; n2 < R2; ++n2) b[n2] = v[R2 * k1 + n2];
-            Dft<R2, INV>::run(b, c, tw, twr);
+            Dft<R2, INV>::run(b, c);
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = b[k2];
         }
@@ -154,84 +167,120 @@ template <bool INV> struct Radix<15, INV> { using T = DftC<3, 5, INV>; };
 template <bool INV> struct Radix<16, INV> { using T = DftC<4, 4, INV>; };
 template <bool INV> struct Radix<20, INV> { using T = DftC<4, 5, INV>; };
 
+// twiddle-table row pitch of a radix-R pass (R - 1 entries, even for 16-byte pairs)
+__host__ __device__ constexpr int tw_pitch(int R) { return (R - 1 + 1) & ~1; }
+
 // One Stockham pass of radix R over the SP_G signals: after the passes with
 // radices before this one (product Ns), butterfly idx (k = idx mod Ns) takes
-// in[idx + r F / R], twiddles them by W_F^(k r F / (Ns R)), transforms and
-// stores output u at (idx - k) R + k + u Ns.
-template <int R, bool INV>
-__device__ __noinline__ void sp_pass(const float2* __restrict__ in, float2* __restrict__ out, int F, int Ns,
-                                     const float2* __restrict__ tw, Codelet c)
+// in[idx + r F / R], twiddles them by W_F^(k r F / (Ns R)) = T[k pitch + r - 1],
+// transforms and stores output u at (idx - k) R + k + u Ns.  FT / NS: the
+// frame count and Ns at compile time (0: the run-time values).
+template <int R, bool INV, int FT, int NS>
+__device__ __forceinline__ void sp_pass(const float2* __restrict__ in, float2* __restrict__ out, int Frt, int Nsrt,
+                                        const float2* __restrict__ T, const SepConst& c)
 {
-    const int nb = F / R, step = F / (Ns * R), twr = F / R;
+    const int F = FT ? FT : Frt, Ns = NS ? NS : Nsrt;
+    constexpr int P = tw_pitch(R);
+    const int nb = F / R;
     for (int it = threadIdx.x; it < nb * SP_G; it += SP_THREADS) {
         const int g = it & (SP_G - 1), idx = it / SP_G;
-        const int k = idx % Ns;
+        const int k = NS == 1 ? 0 : idx % Ns;
+        const float2* src = in + idx * SP_G + g;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[(idx + r * nb) * SP_G + g];
-        if (k != 0) {
+        for (int r = 0; r < R; ++r) v[r] = src[r * nb * SP_G];
+        if (NS != 1 && k != 0) {
+            const float4* t4 = reinterpret_cast<const float4*>(T + k * P);
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = f2mul(v[r], twid<INV>(tw, k * r * step));
+            for (int r = 1; r < R; r += 2) {
+                const float4 w = t4[(r - 1) / 2];
+                v[r] = twmul<INV>(v[r], make_float2(w.x, w.y));
+                if (r + 1 < R) v[r + 1] = twmul<INV>(v[r + 1], make_float2(w.z, w.w));
+            }
         }
-        Radix<R, INV>::T::run(v, c, tw, twr);
-        const int o = (idx - k) * R + k;
+        Radix<R, INV>::T::run(v, c);
+        float2* dst = out + ((idx - k) * R + k) * SP_G + g;
 #pragma unroll
-        for (int u = 0; u < R; ++u) out[(o + u * Ns) * SP_G + g] = v[u];
+        for (int u = 0; u < R; ++u) dst[u * Ns * SP_G] = v[u];
     }
 }
 
-// all passes; returns the buffer that holds the result
-template <bool INV>
-__device__ float2* sp_fft(float2* a, float2* b, const SepConst& sc, const float2* tw, Codelet c)
+// all passes; returns the buffer that holds the result.  FT = 300: the plan
+// 20 x 15 at compile time; FT = 0: the run-time plan.
+template <bool INV, int FT>
+__device__ float2* sp_fft(float2* a, float2* b, const SepConst& sc, const float2* tws)
 {
-    int Ns = 1;
-    for (int p = 0; p < sc.npass; ++p) {
-        const int R = sc.radix[p], F = sc.F;
-        switch (R) {
-            case 2: sp_pass<2, INV>(a, b, F, Ns, tw, c); break;
-            case 3: sp_pass<3, INV>(a, b, F, Ns, tw, c); break;
-            case 4: sp_pass<4, INV>(a, b, F, Ns, tw, c); break;
-            case 5: sp_pass<5, INV>(a, b, F, Ns, tw, c); break;
-            case 6: sp_pass<6, INV>(a, b, F, Ns, tw, c); break;
-            case 8: sp_pass<8, INV>(a, b, F, Ns, tw, c); break;
-            case 10: sp_pass<10, INV>(a, b, F, Ns, tw, c); break;
-            case 12: sp_pass<12, INV>(a, b, F, Ns, tw, c); break;
-            case 15: sp_pass<15, INV>(a, b, F, Ns, tw, c); break;
-            case 16: sp_pass<16, INV>(a, b, F, Ns, tw, c); break;
-            default: sp_pass<20, INV>(a, b, F, Ns, tw, c); break;
-        }
+    if constexpr (FT == 300) {
+        sp_pass<20, INV, 300, 1>(a, b, 0, 0, nullptr, sc);
         __syncthreads();
-        float2* t = a;
-        a = b;
-        b = t;
-        Ns *= R;
+        sp_pass<15, INV, 300, 20>(b, a, 0, 0, tws + sc.twoff[1], sc);
+        __syncthreads();
+        return a;
+    } else {
+        int Ns = 1;
+        const int F = sc.F;
+        for (int p = 0; p < sc.npass; ++p) {
+            const int R = sc.radix[p];
+            const float2* T = tws + sc.twoff[p];
+            switch (R) {
+                case 2: sp_pass<2, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 3: sp_pass<3, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 4: sp_pass<4, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 5: sp_pass<5, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 6: sp_pass<6, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 8: sp_pass<8, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 10: sp_pass<10, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 12: sp_pass<12, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 15: sp_pass<15, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                case 16: sp_pass<16, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+                default: sp_pass<20, INV, 0, 0>(a, b, F, Ns, T, sc); break;
+            }
+            __syncthreads();
+            float2* t = a;
+            a = b;
+            b = t;
+            Ns *= R;
+        }
+        return a;
     }
-    return a;
 }
 
 // planes [F][2][2][S][nz][N] -> OUT_COMPLEX: sub [nsub][F][2][2][S][nz][N] C32;
-// OUT_ENHANCE: A [nsub][F][2][S][nz][N], M [nsub][F] (float bits, >= 0)
-template <int MX, int OUT>
-__global__ void __launch_bounds__(SP_THREADS, MX <= 20 ? 2 : 1)
+// OUT_XDOPPLER / OUT_COHERENT: A [nsub][F][2][S][nz][N], M [nsub][F] (float bits, >= 0)
+template <int MX, int OUT, int FT>
+__global__ void __launch_bounds__(SP_THREADS, MX <= 19 ? 2 : 1)
     k_separate(const void* __restrict__ planes, int pt, const __grid_constant__ SepConst sc, int S, int nz, int N,
                float2* __restrict__ sub, float* __restrict__ A, unsigned* __restrict__ M)
 {
     extern __shared__ __align__(16) float2 smem[];
-    const int F = sc.F, nsub = sc.nsub;
+    const int F = FT ? FT : sc.F, nsub = sc.nsub;
     float2* B0 = smem;
     float2* B1 = B0 + (size_t)F * SP_G;
-    float2* tw = B1 + (size_t)F * SP_G;
-    unsigned* mx = reinterpret_cast<unsigned*>(tw + F);                       // [nsub][F] (OUT_ENHANCE)
-    signed char* sbin = reinterpret_cast<signed char*>(mx + (OUT == SP_OUT_ENHANCE ? nsub * F : 0));
-    const Codelet c{sc.s3, sc.c51, sc.c52, sc.s51, sc.s52};
+    float2* tws = B1 + (size_t)F * SP_G;                                      // pass twiddle tables
+    unsigned* mx = reinterpret_cast<unsigned*>(tws + sc.ntw);                 // [nsub][F] frame maxima (amplitude outputs)
+    signed char* sbin = reinterpret_cast<signed char*>(mx + (OUT != SP_OUT_COMPLEX ? nsub * F : 0));
 
-    for (int m = threadIdx.x; m < F; m += SP_THREADS) {
-        double s, co;
-        sincospi(-2.0 * (double)m / (double)F, &s, &co);
-        tw[m] = make_float2((float)co, (float)s);
-        sbin[m] = sc.bin[m];
+    // pass p (Ns > 1): T_p[k pitch + r - 1] = exp(-2 pi i k r / (Ns R)), double then rounded
+    {
+        int Ns = 1;
+        for (int p = 0; p < sc.npass; ++p) {
+            const int R = sc.radix[p], P = tw_pitch(R);
+            if (Ns > 1)
+                for (int e = threadIdx.x; e < Ns * P; e += SP_THREADS) {
+                    const int k = e / P, r = e % P + 1;
+                    float2 w = make_float2(0.f, 0.f);
+                    if (r < R) {
+                        double sn, cs;
+                        sincospi(-2.0 * (double)(k * r) / (double)(Ns * R), &sn, &cs);
+                        w = make_float2((float)cs, (float)sn);
+                    }
+                    tws[sc.twoff[p] + e] = w;
+                }
+            Ns *= R;
+        }
     }
-    if (OUT == SP_OUT_ENHANCE)
+    for (int m = threadIdx.x; m < F; m += SP_THREADS) sbin[m] = sc.bin[m];
+    if (OUT != SP_OUT_COMPLEX)
         for (int i = threadIdx.x; i < nsub * F; i += SP_THREADS) mx[i] = 0u;
     __syncthreads();
 
@@ -248,17 +297,24 @@ __global__ void __launch_bounds__(SP_THREADS, MX <= 20 ? 2 : 1)
         const int lat0 = lg * SP_TL;
         const size_t rest0 = (size_t)(row % (long long)rows_axis) * N + lat0;
 
-        // slow-time signals of the group: element t * SP_G + 2 l + fam
-#pragma unroll 4
-        for (int i = threadIdx.x; i < n_el; i += SP_THREADS) {
+        // slow-time signals of the group: element t * SP_G + 2 l + fam; all of a
+        // thread's loads are issued before its shared-memory stores
+        float2 xr[MX];
+#pragma unroll
+        for (int m = 0; m < MX; ++m) {
+            const int i = threadIdx.x + m * SP_THREADS;
             const int t = i / SP_G, gg = i & (SP_G - 1), l = gg >> 1, fam = gg & 1;
-            float2 v = make_float2(0.f, 0.f);
-            if (lat0 + l < N) v = load_c(planes, (((size_t)t * 2 + axis) * 2 + fam) * per_axis + rest0 + l, pt);
-            B0[i] = v;
+            xr[m] = make_float2(0.f, 0.f);
+            if (i < n_el && lat0 + l < N)
+                xr[m] = load_c(planes, (((size_t)t * 2 + axis) * 2 + fam) * per_axis + rest0 + l, pt);
+        }
+#pragma unroll
+        for (int m = 0; m < MX; ++m) {
+            const int i = threadIdx.x + m * SP_THREADS;
+            if (i < n_el) B0[i] = xr[m];
         }
         __syncthreads();
-        const float2* X = sp_fft<false>(B0, B1, sc, tw, c);
-        float2 xr[MX];
+        const float2* X = sp_fft<false, FT>(B0, B1, sc, tws);
 #pragma unroll
         for (int m = 0; m < MX; ++m) {
             const int e = threadIdx.x + m * SP_THREADS;
@@ -273,7 +329,7 @@ __global__ void __launch_bounds__(SP_THREADS, MX <= 20 ? 2 : 1)
                 if (e < n_el) B0[e] = sbin[e / SP_G] == s ? f2scale(xr[m], invF) : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            const float2* Y = sp_fft<true>(B0, B1, sc, tw, c);
+            const float2* Y = sp_fft<true, FT>(B0, B1, sc, tws);
             if (OUT == SP_OUT_COMPLEX) {
                 float2* dst = sub + (size_t)s * F * 4 * per_axis;
                 for (int i = threadIdx.x; i < n_el; i += SP_THREADS) {
@@ -281,50 +337,67 @@ __global__ void __launch_bounds__(SP_THREADS, MX <= 20 ? 2 : 1)
                     if (lat0 + l < N) dst[(((size_t)t * 2 + axis) * 2 + fam) * per_axis + rest0 + l] = Y[i];
                 }
             } else {
-                // one lateral pixel per lane, a run of `per` frames per group of 8 lanes;
-                // (RC, CR) of a pixel are adjacent: one 16-byte load
-                const int l = threadIdx.x & (SP_TL - 1), ch = threadIdx.x / SP_TL;
-                const int per = (F + SP_THREADS / SP_TL - 1) / (SP_THREADS / SP_TL), tb = ch * per;
+                // thread = (frame chunk ch, lateral pair lp): frames [ch per, ch per + per)
+                // of lateral pixels la = lp + 4 (ch & 1) and lb = lp + 4 (1 - (ch & 1))
+                // (the two chunks of a quarter-warp read opposite halves of their rows);
+                // the three-frame window slides along the chunk.  Y4[t SP_TL + l] =
+                // (RC, CR) of pixel l at frame t.
+                constexpr int NLP = SP_TL / 2, NCH = SP_THREADS / NLP;
                 const float4* Y4 = reinterpret_cast<const float4*>(Y);
-                auto q = [&](int t) -> float2 {
-                    if (t < 0 || t >= F) return make_float2(0.f, 0.f);
-                    const float4 v = Y4[t * SP_TL + l];   // (RC re, RC im, CR re, CR im)
-                    return make_float2(v.x * v.z + v.y * v.w, v.y * v.z - v.x * v.w);
-                };
                 float* dstA = A + (size_t)s * F * 2 * per_axis;
-                const bool lat_ok = lat0 + l < N;
-                float2 qm = make_float2(0.f, 0.f), q0 = make_float2(0.f, 0.f);
-                if (sc.enh == ULM_ENH_XDOPPLER) {
-                    qm = q(tb - 1);
-                    q0 = q(tb);
-                }
+                const int lp = threadIdx.x & (NLP - 1), ch = threadIdx.x / NLP;
+                const int la = lp + NLP * (ch & 1), lb = lp + NLP * (1 - (ch & 1));
+                const bool oka = lat0 + la < N, okb = lat0 + lb < N;
+                const int per = (F + NCH - 1) / NCH, t0 = ch * per;
+                auto ld = [&](int t, int l) -> float4 {
+                    return (t >= 0 && t < F) ? Y4[t * SP_TL + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+                };
+                auto qf = [](float4 v) { return make_float2(v.x * v.z + v.y * v.w, v.y * v.z - v.x * v.w); };
+                float2 qma = qf(ld(t0 - 1, la)), qmb = qf(ld(t0 - 1, lb));
+                float2 q0a = qf(ld(t0, la)), q0b = qf(ld(t0, lb));
+                float4 ya = ld(t0, la), yb = ld(t0, lb);
+#pragma unroll
                 for (int i = 0; i < per; ++i) {
-                    const int t = tb + i;
-                    float a = 0.f;
-                    if (sc.enh == ULM_ENH_XDOPPLER) {
-                        const float2 qp = q(t + 1);
-                        const float re = qm.x + q0.x + qp.x, im = qm.y + q0.y + qp.y;
-                        a = sqrtf(sqrtf(re * re + im * im));
-                        qm = q0;
-                        q0 = qp;
-                    } else if (t < F) {
-                        const float4 v = Y4[t * SP_TL + l];
-                        const float re = v.x + v.z, im = v.y + v.w;
-                        a = sqrtf(re * re + im * im);
+                    const int t = t0 + i;
+                    float aa, ab;
+                    if (OUT == SP_OUT_XDOPPLER) {
+                        const float2 qpa = qf(ld(t + 1, la)), qpb = qf(ld(t + 1, lb));
+                        const float ra = qma.x + q0a.x + qpa.x, ia = qma.y + q0a.y + qpa.y;
+                        const float rb = qmb.x + q0b.x + qpb.x, ib = qmb.y + q0b.y + qpb.y;
+                        aa = sqrt_approx(sqrt_approx(ra * ra + ia * ia));
+                        ab = sqrt_approx(sqrt_approx(rb * rb + ib * ib));
+                        qma = q0a;
+                        q0a = qpa;
+                        qmb = q0b;
+                        q0b = qpb;
+                    } else {
+                        const float ra = ya.x + ya.z, ia = ya.y + ya.w, rb = yb.x + yb.z, ib = yb.y + yb.w;
+                        aa = sqrt_approx(ra * ra + ia * ia);
+                        ab = sqrt_approx(rb * rb + ib * ib);
+                        ya = ld(t + 1, la);
+                        yb = ld(t + 1, lb);
                     }
-                    const bool ok = t < F && lat_ok;
-                    if (ok) __stcs(dstA + ((size_t)t * 2 + axis) * per_axis + rest0 + l, a);
-                    float mm = ok ? a : 0.f;
+                    float mm = 0.f;
+                    if (t < F) {
+                        float* d = dstA + ((size_t)t * 2 + axis) * per_axis + rest0;
+                        if (oka) {
+                            __stcs(d + la, aa);
+                            mm = aa;
+                        }
+                        if (okb) {
+                            __stcs(d + lb, ab);
+                            mm = fmaxf(mm, ab);
+                        }
+                    }
                     mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, 1));
                     mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, 2));
-                    mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, 4));
-                    if (l == 0 && t < F) atomicMax(mx + s * F + t, __float_as_uint(mm));
+                    if (lp == 0 && t < F) atomicMax(mx + s * F + t, __float_as_uint(mm));
                 }
             }
             __syncthreads();
         }
     }
-    if (OUT == SP_OUT_ENHANCE)
+    if (OUT != SP_OUT_COMPLEX)
         for (int i = threadIdx.x; i < nsub * F; i += SP_THREADS)
             if (mx[i]) atomicMax(M + i, mx[i]);
 }
@@ -349,11 +422,11 @@ bool plan_radices(int F, int* radix, int* npass)
     return true;
 }
 
-template <int MX, int OUT>
+template <int MX, int OUT, int FT>
 rca_status launch_mx(rca_handle* h, const void* planes, int pt, const SepConst& sc, int S, int nz, int N,
                      float2* sub, float* A, unsigned* M, size_t smem, long long ngroups)
 {
-    auto kern = k_separate<MX, OUT>;
+    auto kern = k_separate<MX, OUT, FT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "separation smem attribute");
     int dev = 0, sms = 0, per_sm = 0;
@@ -396,6 +469,19 @@ rca_status launch_separate(rca_handle* h, const rca_tables* t, const void* plane
     sc.c52 = (float)std::cos(4.0 * pi / 5.0);
     sc.s51 = (float)std::sin(2.0 * pi / 5.0);
     sc.s52 = (float)std::sin(4.0 * pi / 5.0);
+    for (int R : {6, 8, 10, 12, 15, 16, 20})
+        for (int m = 0; m < R; ++m)
+            sc.wr[wr_off(R) + m] = make_float2((float)std::cos(2.0 * pi * m / R), (float)-std::sin(2.0 * pi * m / R));
+    // pass twiddle tables: rows of tw_pitch(R) entries per k < Ns (passes with Ns > 1)
+    {
+        int Ns = 1, off = 0;
+        for (int p = 0; p < sc.npass; ++p) {
+            sc.twoff[p] = off;
+            if (Ns > 1) off += Ns * tw_pitch(sc.radix[p]);
+            Ns *= sc.radix[p];
+        }
+        sc.ntw = off;
+    }
     // bin -> subset: signed index k, |k| prf / F against the edges (upper edge
     // inclusive), k > 0 up (subsets 0 .. nb-1), k < 0 down (nb .. 2 nb - 1);
     // DC and the Nyquist bin in none
@@ -410,25 +496,25 @@ rca_status launch_separate(rca_handle* h, const rca_tables* t, const void* plane
                 break;
             }
     }
-    const int out = A ? SP_OUT_ENHANCE : SP_OUT_COMPLEX;
-    const size_t smem = (size_t)2 * F * SP_G * sizeof(float2) + (size_t)F * sizeof(float2) +
-                        (out == SP_OUT_ENHANCE ? (size_t)sc.nsub * F * sizeof(unsigned) : 0) + (size_t)F;
+    const int out = !A ? SP_OUT_COMPLEX : enh == ULM_ENH_XDOPPLER ? SP_OUT_XDOPPLER : SP_OUT_COHERENT;
+    const size_t smem = (size_t)2 * F * SP_G * sizeof(float2) + (size_t)sc.ntw * sizeof(float2) +
+                        (out != SP_OUT_COMPLEX ? (size_t)sc.nsub * F * sizeof(unsigned) : 0) + (size_t)F;
     const long long ngroups = 2LL * g.S * g.nz * ((g.N + SP_TL - 1) / SP_TL);
     unsigned* Mu = reinterpret_cast<unsigned*>(M);
-    if (out == SP_OUT_ENHANCE) {
+    if (out != SP_OUT_COMPLEX) {
         cudaError_t e = cudaMemsetAsync(M, 0, sizeof(float) * (size_t)sc.nsub * F, h->stream);
         if (e != cudaSuccess) return cuda_check(h, e, "separation maxima");
     }
     const int mx = (F * SP_G + SP_THREADS - 1) / SP_THREADS;
-#define SP_LAUNCH(MXV)                                                                                        \
-    return out == SP_OUT_ENHANCE                                                                              \
-               ? launch_mx<MXV, SP_OUT_ENHANCE>(h, planes, (int)pt, sc, g.S, g.nz, g.N, sub, A, Mu, smem, ngroups) \
-               : launch_mx<MXV, SP_OUT_COMPLEX>(h, planes, (int)pt, sc, g.S, g.nz, g.N, sub, A, Mu, smem, ngroups)
-    if (mx <= 4) SP_LAUNCH(4);
-    if (mx <= 8) SP_LAUNCH(8);
-    if (mx <= 12) SP_LAUNCH(12);
-    if (mx <= 16) SP_LAUNCH(16);
-    if (mx <= 20) SP_LAUNCH(20);
-    SP_LAUNCH(32);
+#define SP_LAUNCH(MXV, FTV)                                                                                     \
+    return out == SP_OUT_XDOPPLER                                                                               \
+               ? launch_mx<MXV, SP_OUT_XDOPPLER, FTV>(h, planes, (int)pt, sc, g.S, g.nz, g.N, sub, A, Mu, smem, ngroups) \
+           : out == SP_OUT_COHERENT                                                                              \
+               ? launch_mx<MXV, SP_OUT_COHERENT, FTV>(h, planes, (int)pt, sc, g.S, g.nz, g.N, sub, A, Mu, smem, ngroups) \
+               : launch_mx<MXV, SP_OUT_COMPLEX, FTV>(h, planes, (int)pt, sc, g.S, g.nz, g.N, sub, A, Mu, smem, ngroups)
+    if (F == 300) SP_LAUNCH(19, 300);   // the paper's ensemble: plan 20 x 15 at compile time
+    if (mx <= 8) SP_LAUNCH(8, 0);
+    if (mx <= 19) SP_LAUNCH(19, 0);
+    SP_LAUNCH(32, 0);
 #undef SP_LAUNCH
 }

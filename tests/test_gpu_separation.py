@@ -120,12 +120,13 @@ def test_fused_enhancement_matches_oracle(S, tiny, tiny_planes, enh):
             M_o = A_o.reshape(A_o.shape[0], -1).max(axis=1)
         assert rel(A[s], A_o) < 2e-5, (s, rel(A[s], A_o))
         assert np.allclose(M[s], M_o, rtol=2e-5, atol=0), s
-    # the same as separating, then enhancing each subset with ulm_enhance
+    # the same as separating, then enhancing each subset with ulm_enhance (the
+    # fused kernel's square roots are the approximate ones, 2^-23 relative)
     sub_dev = S.separate(c64(tiny_planes), prm)
     for s in range(6):
         A2, M2 = S.enhance(sub_dev[s].contiguous(), enh=enh)
-        assert rel(A[s], A2.cpu().numpy()) < 1e-6
-        assert np.allclose(M[s], M2.cpu().numpy(), rtol=1e-6, atol=0)
+        assert rel(A[s], A2.cpu().numpy()) < 2e-6
+        assert np.allclose(M[s], M2.cpu().numpy(), rtol=2e-6, atol=0)
 
 
 def test_subset_localisation_runs_on_fused_output(S, tiny, tiny_planes):
