@@ -315,21 +315,68 @@ __global__ void __launch_bounds__(SP_THREADS, MX <= 19 ? 2 : 1)
         }
         __syncthreads();
         const float2* X = sp_fft<false, FT>(B0, B1, sc, tws);
+        // FT = 300: each of the first 240 threads keeps the 20 spectrum values
+        // that its butterfly of the first inverse pass (radix 20, Ns = 1, no
+        // twiddles) reads, with their subsets (4-bit codes, subset + 1), so the
+        // masking and that pass run from registers; otherwise the thread keeps
+        // elements threadIdx.x + m SP_THREADS and the masked spectrum is
+        // written back for the inverse transform
+        constexpr int R0 = 20, NB0 = 15;
+        const int g0 = threadIdx.x & (SP_G - 1), idx0 = threadIdx.x / SP_G;
+        const bool bf0 = threadIdx.x < NB0 * SP_G;
+        float2 xs[FT == 300 ? R0 : 1];
+        unsigned long long code_lo = 0ull;
+        unsigned code_hi = 0u;
+        if constexpr (FT == 300) {
+            if (bf0) {
 #pragma unroll
-        for (int m = 0; m < MX; ++m) {
-            const int e = threadIdx.x + m * SP_THREADS;
-            xr[m] = e < n_el ? X[e] : make_float2(0.f, 0.f);
+                for (int r = 0; r < R0; ++r) {
+                    const int j = idx0 + NB0 * r;
+                    xs[r] = X[j * SP_G + g0];
+                    const unsigned cj = (unsigned)(sbin[j] + 1);
+                    if (r < 16)
+                        code_lo |= (unsigned long long)cj << (4 * r);
+                    else
+                        code_hi |= cj << (4 * (r - 16));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MX; ++m) {
+                const int e = threadIdx.x + m * SP_THREADS;
+                xr[m] = e < n_el ? X[e] : make_float2(0.f, 0.f);
+            }
         }
         __syncthreads();
 
         for (int s = 0; s < nsub; ++s) {
+            const float2* Y;
+            if constexpr (FT == 300) {
+                if (bf0) {
+                    float2 v[R0];
 #pragma unroll
-            for (int m = 0; m < MX; ++m) {
-                const int e = threadIdx.x + m * SP_THREADS;
-                if (e < n_el) B0[e] = sbin[e / SP_G] == s ? f2scale(xr[m], invF) : make_float2(0.f, 0.f);
+                    for (int r = 0; r < R0; ++r) {
+                        const unsigned cj = r < 16 ? (unsigned)(code_lo >> (4 * r)) & 15u : (code_hi >> (4 * (r - 16))) & 15u;
+                        v[r] = cj == (unsigned)(s + 1) ? f2scale(xs[r], invF) : make_float2(0.f, 0.f);
+                    }
+                    Radix<R0, true>::T::run(v, sc);
+                    float2* dst = B1 + idx0 * R0 * SP_G + g0;
+#pragma unroll
+                    for (int u = 0; u < R0; ++u) dst[u * SP_G] = v[u];
+                }
+                __syncthreads();
+                sp_pass<15, true, 300, 20>(B1, B0, 0, 0, tws + sc.twoff[1], sc);
+                __syncthreads();
+                Y = B0;
+            } else {
+#pragma unroll
+                for (int m = 0; m < MX; ++m) {
+                    const int e = threadIdx.x + m * SP_THREADS;
+                    if (e < n_el) B0[e] = sbin[e / SP_G] == s ? f2scale(xr[m], invF) : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+                Y = sp_fft<true, FT>(B0, B1, sc, tws);
             }
-            __syncthreads();
-            const float2* Y = sp_fft<true, FT>(B0, B1, sc, tws);
             if (OUT == SP_OUT_COMPLEX) {
                 float2* dst = sub + (size_t)s * F * 4 * per_axis;
                 for (int i = threadIdx.x; i < n_el; i += SP_THREADS) {
