@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--cpu-sample-frames", type=int, default=4)
     ap.add_argument("--frames", type=int, default=0, help="override the ensemble length (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision / batched / learned forms")
-    ap.add_argument("--no-next-rows", action="store_true", help="skip tracking and motion estimation")
+    ap.add_argument("--no-next-rows", action="store_true", help="skip tracking, separation, motion estimation and the SVD filter")
     return ap.parse_args()
 
 
