@@ -513,6 +513,11 @@ rca_status ulm_cnn_get_grads(const ulm_cnn* c, float* host, size_t n);
 rca_status ulm_cnn_forward(ulm_cnn* c, const float* A, const float* M, int planes_per_frame, int B, int H, int W,
                            float* heat);
 
+/* Inference: the same computation as ulm_cnn_forward (the name of the
+ * learned form's inference step). */
+rca_status ulm_cnn_infer(ulm_cnn* c, const float* A, const float* M, int planes_per_frame, int B, int H, int W,
+                         float* heat);
+
 /* One training step on a batch: forward, MSE against target [B][4H][4W],
  * backward (gradients kept for ulm_cnn_get_grads) and, if apply_update, an
  * Adam update.  loss_dev: device float receiving the mean squared error. */
@@ -577,6 +582,14 @@ rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_item* items, r
  * the first call runs the batch once, then captures it into a CUDA graph
  * (on a private stream); every call launches that graph. */
 rca_status rca_batch_run(rca_batch* b, int use_graph);
+
+/* One-shot form of the batch plan: rca_batch_create, one rca_batch_run
+ * without a graph, a synchronisation of the handle's stream and
+ * rca_batch_destroy.  Same items and errors as rca_batch_create; the IQ is
+ * kept as RCA_C32.  Synchronises (the plan's workspace is freed); for
+ * repeated batches build the plan once and run it (optionally as a graph). */
+rca_status rca_beamform_projections_batched(rca_handle* h, int n, const rca_batch_item* items, rca_dtype rf_dtype,
+                                            rca_dtype planes_dtype, const ulm_params* prm);
 
 /* Bound of every dependency wait in the persistent launch, in SM clock
  * cycles (default ~4e9).  block_ensemble >= 0 makes that ensemble's Stage-1

@@ -132,12 +132,14 @@ SIGNATURES = {
     "ulm_cnn_get_params": (_S, [_P, _P, _SZ]),
     "ulm_cnn_get_grads": (_S, [_P, _P, _SZ]),
     "ulm_cnn_forward": (_S, [_P, _P, _P, _I, _I, _I, _I, _P]),
+    "ulm_cnn_infer": (_S, [_P, _P, _P, _I, _I, _I, _I, _P]),
     "ulm_cnn_train_step": (_S, [_P, _P, _P, _I, _I, _I, _I, _P, _P, _I]),
     "ulm_cnn_target": (_S, [_P, _P, _I, _I, _I, _I, C.c_float, _P]),
     "ulm_cnn_save": (_S, [_P, C.c_char_p]),
     "ulm_cnn_load": (_S, [_P, C.c_char_p]),
     "ulm_detect_map": (_S, [_P, _P, _P, _I, _P, _P, _I, C.c_float, C.c_float, _P, _I, _P]),
     "rca_batch_create": (_S, [_P, _I, C.POINTER(rca_batch_item), _I, _I, _I, C.POINTER(ulm_params), C.POINTER(_P)]),
+    "rca_beamform_projections_batched": (_S, [_P, _I, C.POINTER(rca_batch_item), _I, _I, C.POINTER(ulm_params)]),
     "rca_batch_run": (_S, [_P, _I]),
     "rca_batch_set_wait_limit": (_S, [_P, C.c_longlong, _I]),
     "rca_batch_destroy": (_S, [_P]),

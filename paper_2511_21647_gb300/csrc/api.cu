@@ -1056,3 +1056,19 @@ extern "C" rca_status rca_autotune(rca_handle* h, rca_tables* t, const void* iq,
     if (zp_out) *zp_out = bzp;
     return st;
 }
+
+extern "C" rca_status rca_beamform_projections_batched(rca_handle* h, int n, const rca_batch_item* items,
+                                                       rca_dtype rf_t, rca_dtype pl_t, const ulm_params* prm)
+{
+    CHECK_HANDLE(h);
+    rca_batch* b = nullptr;
+    rca_status st = rca_batch_create(h, n, items, rf_t, RCA_C32, pl_t, prm, &b);
+    if (st != RCA_OK) return st;
+    st = rca_batch_run(b, 0);
+    DeviceGuard dg(h->device);
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    const rca_status sd = rca_batch_destroy(b);
+    if (st != RCA_OK) return st;
+    if (e != cudaSuccess) return cuda_check(h, e, "batched beamforming");
+    return sd;
+}

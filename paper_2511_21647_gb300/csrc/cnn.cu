@@ -812,6 +812,12 @@ extern "C" rca_status ulm_cnn_forward(ulm_cnn* c, const float* A, const float* M
                       "heatmap copy");
 }
 
+extern "C" rca_status ulm_cnn_infer(ulm_cnn* c, const float* A, const float* M, int ppf, int B, int H, int W,
+                                    float* heat)
+{
+    return ulm_cnn_forward(c, A, M, ppf, B, H, W, heat);
+}
+
 extern "C" rca_status ulm_cnn_train_step(ulm_cnn* c, const float* A, const float* M, int ppf, int B, int H, int W,
                                          const float* target, float* loss_dev, int apply_update)
 {

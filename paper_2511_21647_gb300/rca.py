@@ -249,11 +249,8 @@ def ulm_localize(h, t, planes, planes_dtype, n_frames, prm: ulm_params, out2d, c
                                  _ptr(n2d), _ptr(out3d), cap3d, _ptr(n3d)), h)
 
 
-def rca_batch_create(h, items, rf_dtype, iq_dtype, planes_dtype, prm=None):
-    """items: sequence of dicts with keys tables, rf, scale, n_frames, planes and
-    (with prm) out2d, cap2d, n2d, out3d, cap3d, n3d (tensors or pointers)."""
+def _batch_items(items):
     arr = (rca_batch_item * len(items))()
-    keep = []
     for q, it in enumerate(items):
         a = arr[q]
         a.tables = it["tables"]
@@ -267,11 +264,24 @@ def rca_batch_create(h, items, rf_dtype, iq_dtype, planes_dtype, prm=None):
         a.out3d = _ptr(it.get("out3d"))
         a.cap3d = it.get("cap3d", 0)
         a.n3d_dev = _ptr(it.get("n3d"))
-        keep.append(it)
+    return arr
+
+
+def rca_batch_create(h, items, rf_dtype, iq_dtype, planes_dtype, prm=None):
+    """items: sequence of dicts with keys tables, rf, scale, n_frames, planes and
+    (with prm) out2d, cap2d, n2d, out3d, cap3d, n3d (tensors or pointers)."""
+    arr = _batch_items(items)
     b = C.c_void_p()
     _check(L.load().rca_batch_create(h, len(items), arr, rf_dtype, iq_dtype, planes_dtype,
                                      C.byref(prm) if prm is not None else None, C.byref(b)), h)
     return b
+
+
+def rca_beamform_projections_batched(h, items, rf_dtype, planes_dtype, prm=None):
+    """one-shot batch (plan, one run, synchronise, free); items as rca_batch_create"""
+    arr = _batch_items(items)
+    _check(L.load().rca_beamform_projections_batched(h, len(items), arr, rf_dtype, planes_dtype,
+                                                     C.byref(prm) if prm is not None else None), h)
 
 
 def rca_batch_run(b, use_graph=False, h=None):
@@ -329,6 +339,10 @@ def ulm_cnn_get_grads(c) -> np.ndarray:
 
 def ulm_cnn_forward(c, A, M, planes_per_frame, B, H, W, heat):
     _check(L.load().ulm_cnn_forward(c, _ptr(A), _ptr(M), planes_per_frame, B, H, W, _ptr(heat)), None, "ulm_cnn_forward")
+
+
+def ulm_cnn_infer(c, A, M, planes_per_frame, B, H, W, heat):
+    _check(L.load().ulm_cnn_infer(c, _ptr(A), _ptr(M), planes_per_frame, B, H, W, _ptr(heat)), None, "ulm_cnn_infer")
 
 
 def ulm_cnn_train_step(c, A, M, planes_per_frame, B, H, W, target, loss_dev, apply_update=True):

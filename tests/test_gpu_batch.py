@@ -91,6 +91,33 @@ def test_persistent_batch_matches_oracle_and_single_calls(handle, ensembles):
         free(keep)
 
 
+def test_one_shot_batched_call_equals_the_plan(handle, ensembles):
+    """rca_beamform_projections_batched (plan, run, synchronise, free) gives
+    the plan's planes and lists bit for bit"""
+    from paper_2511_21647_gb300 import _lib as L
+    from paper_2511_21647_gb300 import rca
+    items, keep = make_items(handle, ensembles, with_loc=True)
+    prm = rca.make_ulm_params(d=5, sig_z=0.807, sig_lat=1.4495, alpha=0.1, ncc_min=0.5)
+    try:
+        rca.rca_beamform_projections_batched(handle, items, L.RCA_F32, L.RCA_C32, prm)
+        first = [(it["planes"].clone(), int(it["n2d"].item()), int(it["n3d"].item())) for it in items]
+        b = rca.rca_batch_create(handle, items, L.RCA_F32, L.RCA_C32, L.RCA_C32, prm)
+        try:
+            for it in items:
+                it["planes"].zero_()
+                it["n2d"].zero_()
+                it["n3d"].zero_()
+            rca.rca_batch_run(b, use_graph=False, h=handle)
+            assert rca.rca_sync_status(handle) == L.RCA_OK
+            for (pl, n2, n3), it in zip(first, items):
+                assert torch.equal(pl, it["planes"])
+                assert (n2, n3) == (int(it["n2d"].item()), int(it["n3d"].item()))
+        finally:
+            rca.rca_batch_destroy(b)
+    finally:
+        free(keep)
+
+
 def test_batch_graph_replay_and_localisation(handle, ensembles):
     from paper_2511_21647_gb300 import _lib as L
     from paper_2511_21647_gb300 import rca

@@ -58,6 +58,9 @@ def test_forward_matches_oracle(net, case):
     rca.ulm_cnn_forward(net, A, None, 1, 2, 20, 24, heat)
     got = heat.cpu().numpy()
     assert rel(got, ref) < 1e-2
+    heat2 = torch.empty_like(heat)
+    rca.ulm_cnn_infer(net, A, None, 1, 2, 20, 24, heat2)
+    assert torch.equal(heat, heat2)
 
 
 def test_gradients_match_oracle(net, case):
