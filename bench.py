@@ -421,6 +421,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, G.rf, args.cpu_sample_frames)
+        if next_rows:
+            cpu["next_rows"] = cpu_next_rows(w, L, out3d, n3d, planes, slices, F)
 
     if rank == 0:
         line = {
@@ -924,6 +926,57 @@ def cpu_baseline(w, rf_tensor, n_frames):
     nf = len(frames) + 2
     return {"value": round(nf / dt, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": f"{nf} of {w.n_frames} frames of the same ensemble (mean over all {w.n_frames}), {dt:.1f} s"}
+
+
+def cpu_next_rows(w, L, out3d, n3d, planes, slices, F):
+    """The FP64 oracle of each row outside the step, timed as it stands on the
+    host cores on a bounded sample and scaled to one 300-frame ensemble:
+    tracking of the step's whole 3D list, separation of 4096 sampled pixels'
+    slow-time signals, the SVD filter of one transmission, motion estimation of
+    three frames against frame 0.  Inputs are the ensemble's own data."""
+    import numpy as np
+    import oracle as O
+    from oracle import motion as OM
+    from oracle import separation as OSep
+    from oracle import svd_filter as OS
+    g = w.geom
+    out = {}
+    n = int(n3d.item())
+    rec = out3d[:n].cpu().numpy().view(L.LOC3D).reshape(-1)
+    lst = np.zeros(n, dtype=O.LOC3D)
+    lst["frame"] = rec["frame"]
+    for f in ("x", "y", "z"):
+        lst[f] = rec[f].astype(np.float64)
+    t0 = time.time()
+    O.track(g, lst, O.track_params())
+    dt = time.time() - t0
+    out["tracking"] = {"ms_per_ensemble": round(1e3 * dt, 1), "sample": f"the whole 3D list ({n} localisations)"}
+    rng = np.random.default_rng(0)
+    npx = planes.numel() // (2 * F)
+    sel = rng.choice(npx, 4096, replace=False)
+    a = planes.reshape(F, npx, 2)[:, sel].cpu().numpy().astype(np.float64)
+    xs = a[..., 0] + 1j * a[..., 1]
+    t0 = time.time()
+    OSep.separate(xs, w.frame_rate, OSep.default_edges(w.frame_rate, 3))
+    dt = time.time() - t0
+    out["separation"] = {"ms_per_ensemble": round(1e3 * dt * npx / 4096, 1),
+                         "sample": f"4096 of {npx} plane pixels, {1e3 * dt:.0f} ms"}
+    b = slices[:, 0:1].cpu().numpy().astype(np.float64)
+    sl = b[..., 0] + 1j * b[..., 1]
+    t0 = time.time()
+    OS.filter_slices(sl, 16)
+    dt = time.time() - t0
+    nt = slices.shape[1]
+    out["clutter_svd"] = {"ms_per_ensemble": round(1e3 * dt * nt, 1),
+                          "sample": f"1 of {nt} transmissions (rank 16, eigendecomposition), {1e3 * dt:.0f} ms"}
+    c = slices[:4].cpu().numpy().astype(np.float64)
+    sm = c[..., 0] + 1j * c[..., 1]
+    t0 = time.time()
+    OM.estimate(g, sm, frames=[1, 2, 3])
+    dt = time.time() - t0
+    out["motion"] = {"ms_per_ensemble": round(1e3 * dt * F / 3, 1), "sample": f"3 of {F} frames, {1e3 * dt:.0f} ms"}
+    out["cores"] = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return out
 
 
 def reference_arm(args):
