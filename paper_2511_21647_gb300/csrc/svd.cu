@@ -2,10 +2,9 @@
 // transmission k, the frames' slices form the Casorati matrix X_k (pixels x
 // frames); the filter removes the subspace of the n_c largest eigenvalues of
 // the frame covariance C_k = X_k^H X_k:  X_k <- X_k - X_k Q Q^H.
-//   k_svd_cov      partial covariance tiles: 64 x 64 frames, 8 x 4 per thread,
-//                  over one split of the pixels; slices staged frame-innermost
-//                  in shared memory (double buffered); complex products on
-//                  packed FP32 pairs
+//   k_svd_cov_tc   partial covariance tiles of 128 x 128 frames over one split
+//                  of the pixels on the tensor cores (tcgen05, kind::tf32, FP32
+//                  accumulators in TMEM), FP32-accurate by three TF32 products
 //   k_svd_covsum   deterministic sum of the splits, Hermitian completion
 //   k_svd_cq, k_svd_orth  orthogonal iteration Q <- orth(C Q) towards the
 //                  n_c-dim dominant eigenspace: the product over many CTAs, the
@@ -19,23 +18,112 @@
 
 namespace {
 
-#define SV_T 64            // covariance tile (frames)
-#define SV_PC 32           // pixels per staged chunk
-#define SV_SP 68           // staged row pitch in float2 (frames + 4: 16-byte aligned, shifts banks)
 #define SV_THREADS 512     // subspace CTA
 
 __device__ __forceinline__ float2 sv_cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
-// C_k partial sums for the frame tile pair (ta <= tb) over pixels [p0, p1):
-// part[k][split][a][b] for a in tile ta, b in tile tb.  128 threads: thread
-// (ty, tx) in 8 x 16 owns rows a0 + 8 ty .. + 7 and columns b0 + 4 tx .. + 3
-// (32 complex accumulators); the staged chunk is double buffered.
-__global__ void __launch_bounds__(128) k_svd_cov(const float2* __restrict__ sl, int F, int nt, int P, int ntile,
-                                                 int psplit, float2* __restrict__ part)
+// ---------------------------------------------------------------------------
+// Covariance on the tensor cores.  With X = Xr + i Xi (pixels x frames),
+//   Re C = Xr^T Xr + Xi^T Xi,   Im C = Xr^T Xi - Xi^T Xr,
+// four real products per frame-tile pair, each a K-major GEMM over the pixels
+// (a frame's slice is contiguous in pixels).  FP32 accuracy from TF32 operands:
+// x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and a product a b taken as
+// hi hi + hi lo + lo hi (the dropped lo lo term is 2^-22 of it).  CTA = (frame
+// tile pair ta <= tb of 128 frames each, transmission, pixel split), 128
+// threads; thread r owns frame row a0 + r of the A tile and b0 + r of the B
+// tile.  Per 16-pixel chunk the threads convert their rows into eight operand
+// tiles (A / B x re / im x hi / lo, 128 rows x 16 TF32 each, K-major, no
+// swizzle: core matrix (k group kg of 4, row group mg of 8 rows) at byte
+// kg 2048 + mg 128, row r % 8 at + 16 (r % 8)) of one of two stages, while the
+// 24 MMAs (M = N = 128, K = 8) of the previous chunk run, issued by one thread
+// and committed to that stage's mbarrier.  The chunk after next is loaded into
+// registers meanwhile.  Accumulators in TMEM (lane = A row, column = B row):
+// Re at columns 0-127, Xr^T Xi at 128-255, Xi^T Xr at 256-383; the epilogue
+// writes Re + i (the difference) into part[k][split][a][b] (a in tile ta, b in
+// tile tb).
+// Every mbarrier wait is bounded; on a timeout the CTA records ST_TIMEOUT,
+// waits (bounded) for its MMAs in flight, frees TMEM and returns.
+// ---------------------------------------------------------------------------
+#define SVT_M 128
+#define SVT_PC 16                           // pixels per chunk
+#define SVT_TILE (SVT_M * SVT_PC * 4)       // one operand tile, bytes
+#define SVT_STAGE (8 * SVT_TILE)
+#define SVT_SMEM (2 * SVT_STAGE)
+#define SVT_TMEM_COLS 512
+#define SVT_KMAX 1024                       // pixels per split at most
+enum { SVT_ARH = 0, SVT_ARL, SVT_AIH, SVT_AIL, SVT_BRH, SVT_BRL, SVT_BIH, SVT_BIL };
+
+__device__ __forceinline__ unsigned svt_tf32(float x)
 {
-    __shared__ __align__(16) float2 As[2][SV_PC][SV_SP];
-    __shared__ __align__(16) float2 Bs[2][SV_PC][SV_SP];
-    // tile pair from the linear upper-triangle index
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// hi and lo TF32 parts of four values
+__device__ __forceinline__ void svt_split(float x0, float x1, float x2, float x3, uint4& hi, uint4& lo)
+{
+    hi = make_uint4(svt_tf32(x0), svt_tf32(x1), svt_tf32(x2), svt_tf32(x3));
+    lo = make_uint4(svt_tf32(x0 - __uint_as_float(hi.x)), svt_tf32(x1 - __uint_as_float(hi.y)),
+                    svt_tf32(x2 - __uint_as_float(hi.z)), svt_tf32(x3 - __uint_as_float(hi.w)));
+}
+
+__device__ __forceinline__ void svt_st16(unsigned addr, uint4 v)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M / N) byte
+// offsets in 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t svt_sdesc(unsigned saddr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::tf32: D FP32, A and B TF32 (format 2), both
+// K-major, M = N = 128
+__host__ __device__ constexpr unsigned svt_idesc()
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(SVT_M >> 3) << 17) | ((unsigned)(SVT_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void svt_mma(unsigned tmem_d, uint64_t da, uint64_t db, int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(da), "l"(db), "r"(svt_idesc()), "r"(accumulate)
+        : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void svt_ld32(unsigned taddr, float* v)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + 16u * h));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[16 * h + q] = __uint_as_float(r[q]);
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) k_svd_cov_tc(const float2* __restrict__ sl, int F, int nt, int P, int ntile,
+                                                       int psplit, float2* __restrict__ part,
+                                                       unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char svsm[];
+    __shared__ uint64_t bars[2];
+    __shared__ unsigned s_tmem;
     int pair = blockIdx.x, ta = 0;
     while (pair >= ntile - ta) {
         pair -= ntile - ta;
@@ -43,74 +131,156 @@ __global__ void __launch_bounds__(128) k_svd_cov(const float2* __restrict__ sl, 
     }
     const int tb = ta + pair;
     const int k = blockIdx.y, split = blockIdx.z;
-    const int a0 = ta * SV_T, b0 = tb * SV_T;
+    const int a0 = ta * SVT_M, b0 = tb * SVT_M;
     const int p0 = split * psplit, p1 = min(P, p0 + psplit);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    // acc[i][j] = sum conj(X[a0 + 8 ty + i]) X[b0 + 4 tx + j] as (re, im) packed
-    uint64_t acc[8][4];
+    const int nch = p1 > p0 ? (p1 - p0 + SVT_PC - 1) / SVT_PC : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(SVT_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    const unsigned sbase = smem_u32(svsm);
+    const int r = threadIdx.x;
+    const int fa = a0 + r, fb = b0 + r;
+    const float4* ga = fa < F ? reinterpret_cast<const float4*>(sl + ((size_t)fa * nt + k) * P) : nullptr;
+    const float4* gb = fb < F ? reinterpret_cast<const float4*>(sl + ((size_t)fb * nt + k) * P) : nullptr;
+    const unsigned roff = (unsigned)(r * 16);   // (r / 8) 128 + (r % 8) 16
+    // raw chunk: float4 j of a row holds pixels 2 j, 2 j + 1 of the chunk (re, im, re, im)
+    auto load = [&](int c, float4 (&xa)[8], float4 (&xb)[8]) {
+        const int pc = p0 + c * SVT_PC;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            const int p = pc + 2 * j;   // pixel quads are either inside [p0, p1) or outside (P % 4 == 0)
+            const bool in = c < nch && p < p1;
+            xa[j] = (ga && in) ? __ldg(ga + p / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xb[j] = (gb && in) ? __ldg(gb + p / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    float4 ra[8], rb[8];
+    load(0, ra, rb);
+    unsigned phase = 0;      // bit q: parity of the next completion of bars[q]
+    int pending[2] = {0, 0}; // commits of bars[q] not yet waited for
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const int q = c & 1;
+        float4 na[8], nb[8];
+        load(c + 1, na, nb);
+        if (pending[q]) {
+            // the MMAs of chunk c - 2 read stage q
+            if (!mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) ok = false;
+            phase ^= 1u << q;
+            pending[q] = 0;
+        }
+        if (__syncthreads_or(!ok)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned st = sbase + (unsigned)(q * SVT_STAGE) + roff;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0ull;
-    // stage [pixel][frame] for chunk pc into buffer q with asynchronous 8-byte
-    // copies (zero-filled outside the slice or the frame range): lanes over
-    // pixels, so each warp reads slice rows contiguously
-    auto stage = [&](int pc, int q) {
-        for (int idx = threadIdx.x; idx < SV_T * SV_PC; idx += blockDim.x) {
-            const int r = idx / SV_PC, c = idx - r * SV_PC;
-            const int p = pc + c;
-            const int fa = a0 + r, fb = b0 + r;
-            const bool va = p < p1 && fa < F, vb = p < p1 && fb < F;
-            const float2* ga = va ? sl + ((size_t)fa * nt + k) * P + p : sl;
-            const float2* gb = vb ? sl + ((size_t)fb * nt + k) * P + p : sl;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(&As[q][c][r])), "l"(ga),
-                         "r"(va ? 8 : 0)
-                         : "memory");
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(&Bs[q][c][r])), "l"(gb),
-                         "r"(vb ? 8 : 0)
+        for (int i = 0; i < 4; ++i) {   // k group i: pixels 4 i .. 4 i + 3 of the chunk
+            uint4 h, l;
+            const float4 u = ra[2 * i], v = ra[2 * i + 1];
+            svt_split(u.x, u.z, v.x, v.z, h, l);
+            svt_st16(st + SVT_ARH * SVT_TILE + i * 2048, h);
+            svt_st16(st + SVT_ARL * SVT_TILE + i * 2048, l);
+            svt_split(u.y, u.w, v.y, v.w, h, l);
+            svt_st16(st + SVT_AIH * SVT_TILE + i * 2048, h);
+            svt_st16(st + SVT_AIL * SVT_TILE + i * 2048, l);
+            const float4 w = rb[2 * i], x = rb[2 * i + 1];
+            svt_split(w.x, w.z, x.x, x.z, h, l);
+            svt_st16(st + SVT_BRH * SVT_TILE + i * 2048, h);
+            svt_st16(st + SVT_BRL * SVT_TILE + i * 2048, l);
+            svt_split(w.y, w.w, x.y, x.w, h, l);
+            svt_st16(st + SVT_BIH * SVT_TILE + i * 2048, h);
+            svt_st16(st + SVT_BIL * SVT_TILE + i * 2048, l);
+        }
+        // generic-proxy writes of the stage before the tensor cores read it
+        fence_proxy_async();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned sq = sbase + (unsigned)(q * SVT_STAGE);
+            auto d = [&](int t, int s) { return svt_sdesc(sq + t * SVT_TILE + s * 4096, 2048, 128); };
+            const unsigned dRe = tmem, dP = tmem + 128, dN = tmem + 256;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int acc = (c | s) != 0;
+                svt_mma(dRe, d(SVT_ARH, s), d(SVT_BRH, s), acc);
+                svt_mma(dRe, d(SVT_ARH, s), d(SVT_BRL, s), 1);
+                svt_mma(dRe, d(SVT_ARL, s), d(SVT_BRH, s), 1);
+                svt_mma(dRe, d(SVT_AIH, s), d(SVT_BIH, s), 1);
+                svt_mma(dRe, d(SVT_AIH, s), d(SVT_BIL, s), 1);
+                svt_mma(dRe, d(SVT_AIL, s), d(SVT_BIH, s), 1);
+                svt_mma(dP, d(SVT_ARH, s), d(SVT_BIH, s), acc);
+                svt_mma(dP, d(SVT_ARH, s), d(SVT_BIL, s), 1);
+                svt_mma(dP, d(SVT_ARL, s), d(SVT_BIH, s), 1);
+                svt_mma(dN, d(SVT_AIH, s), d(SVT_BRH, s), acc);
+                svt_mma(dN, d(SVT_AIH, s), d(SVT_BRL, s), 1);
+                svt_mma(dN, d(SVT_AIL, s), d(SVT_BRH, s), 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[q]))
                          : "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    int q = 0;
-    if (p0 < p1) stage(p0, 0);
-    for (int pc = p0; pc < p1; pc += SV_PC) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncthreads();                       // chunk pc staged in q; q ^ 1 free
-        if (pc + SV_PC < p1) stage(pc + SV_PC, q ^ 1);
-#pragma unroll 2
-        for (int c = 0; c < SV_PC; ++c) {
-            const float4 b01 = *reinterpret_cast<const float4*>(&Bs[q][c][4 * tx]);
-            const float4 b23 = *reinterpret_cast<const float4*>(&Bs[q][c][4 * tx + 2]);
-            // conj(a) b = a.re (b.re, b.im) + a.im (b.im, -b.re)
-            const uint64_t bb[4] = {f2_pack(b01.x, b01.y), f2_pack(b01.z, b01.w), f2_pack(b23.x, b23.y),
-                                    f2_pack(b23.z, b23.w)};
-            const uint64_t bs[4] = {f2_pack(b01.y, -b01.x), f2_pack(b01.w, -b01.z), f2_pack(b23.y, -b23.x),
-                                    f2_pack(b23.w, -b23.z)};
+        pending[q] = 1;
 #pragma unroll
-            for (int i2 = 0; i2 < 4; ++i2) {
-                const float4 a = *reinterpret_cast<const float4*>(&As[q][c][8 * ty + 2 * i2]);
-                const uint64_t ar0 = f2_pack(a.x, a.x), ai0 = f2_pack(a.y, a.y);
-                const uint64_t ar1 = f2_pack(a.z, a.z), ai1 = f2_pack(a.w, a.w);
+        for (int j = 0; j < 8; ++j) {
+            ra[j] = na[j];
+            rb[j] = nb[j];
+        }
+    }
+    // the MMAs still in flight complete (bounded) before the accumulators are read or freed
+    for (int cc = 0; cc < 2; ++cc) {
+        // older commit first: the stage of chunk nch - 2, then of nch - 1
+        const int q = (nch + cc) & 1;
+        if (pending[q]) {
+            if (!mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) ok = false;
+            phase ^= 1u << q;
+            pending[q] = 0;
+        }
+    }
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+    } else if (nch > 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float2* dst = part + (((size_t)k * gridDim.z + split) * F) * F;
+        const int a = a0 + 32 * warp + lane;
+        const unsigned lrow = (unsigned)(32 * warp) << 16;
+#pragma unroll 1
+        for (int cg = 0; cg < 4; ++cg) {
+            float re[32], ip[32], in[32];
+            svt_ld32(tmem + lrow + (unsigned)(32 * cg), re);
+            svt_ld32(tmem + lrow + 128u + (unsigned)(32 * cg), ip);
+            svt_ld32(tmem + lrow + 256u + (unsigned)(32 * cg), in);
+            if (a < F) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[2 * i2][j] = f2_fma(ai0, bs[j], f2_fma(ar0, bb[j], acc[2 * i2][j]));
-                    acc[2 * i2 + 1][j] = f2_fma(ai1, bs[j], f2_fma(ar1, bb[j], acc[2 * i2 + 1][j]));
+                for (int j = 0; j < 32; ++j) {
+                    const int b = b0 + 32 * cg + j;
+                    if (b < F) dst[(size_t)a * F + b] = make_float2(re[j], ip[j] - in[j]);
                 }
             }
         }
-        q ^= 1;
     }
-    float2* dst = part + (((size_t)k * gridDim.z + split) * F) * F;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int a = a0 + 8 * ty + i;
-        if (a >= F) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int b = b0 + 4 * tx + j;
-            if (b < F) dst[(size_t)a * F + b] = f2_unpack(acc[i][j]);
-        }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[1])) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SVT_TMEM_COLS)
+                     : "memory");
     }
 }
 
@@ -329,13 +499,20 @@ rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices
     const size_t smem_sub = svd_subspace_smem(F, nc);
     if (smem_sub > 200 * 1024)
         return set_error(h, RCA_ERR_UNSUPPORTED, "frames x (rank + 1) = %d x %d exceeds the subspace kernel", F, nc + 1);
-    const int ntile = (F + SV_T - 1) / SV_T, npair = ntile * (ntile + 1) / 2;
-    // pixel splits: about 8 CTAs per SM in total
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nsplit = std::max(1, std::min((P + SV_PC - 1) / SV_PC, (8 * sms + npair * nt - 1) / (npair * nt)));
-    const int psplit = ((P + nsplit - 1) / nsplit + SV_PC - 1) / SV_PC * SV_PC;
+    // the covariance's pixel quads stay whole: N is a multiple of 4 (geometry rule)
+    if (P % 4 != 0) return set_error(h, RCA_ERR_UNSUPPORTED, "slice pixel count %d not a multiple of 4", P);
+    // (tile pair, transmission, pixel split) CTAs, at least one wave, and at
+    // most SVT_KMAX pixels per split, added on the CUDA cores (k_svd_covsum):
+    // the error of one TMEM accumulation grows with its length (measured on the
+    // 300-frame paper stack: 2.6e-5 of the input with 21 280 pixels per split,
+    // 1.6e-6 with 1 024; 5.7e-7 for the CUDA-core FP32 covariance it replaced)
+    const int ntile = (F + SVT_M - 1) / SVT_M, npair = ntile * (ntile + 1) / 2;
+    int nsplit = std::max({1, sms / (npair * nt), (P + SVT_KMAX - 1) / SVT_KMAX});
+    nsplit = std::min(nsplit, (P + SVT_PC - 1) / SVT_PC);
+    const int psplit = ((P + nsplit - 1) / nsplit + SVT_PC - 1) / SVT_PC * SVT_PC;
     nsplit = (P + psplit - 1) / psplit;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t n_part = (size_t)nt * nsplit * F * F, n_C = (size_t)nt * F * F, n_Q = (size_t)nt * F * nc;
@@ -347,7 +524,10 @@ rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices
     float2* C = reinterpret_cast<float2*>(ws + up(n_part * 8));
     float2* Q = reinterpret_cast<float2*>((char*)C + up(n_C * 8));
     float2* Y = reinterpret_cast<float2*>((char*)Q + up(n_Q * 8));
-    k_svd_cov<<<dim3(npair, nt, nsplit), 128, 0, h->stream>>>(slices, F, nt, P, ntile, psplit, part);
+    cudaError_t ea = cudaFuncSetAttribute(k_svd_cov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SVT_SMEM);
+    if (ea != cudaSuccess) return cuda_check(h, ea, "covariance smem attribute");
+    k_svd_cov_tc<<<dim3(npair, nt, nsplit), 128, SVT_SMEM, h->stream>>>(slices, F, nt, P, ntile, psplit, part,
+                                                                         h->d_status);
     k_svd_covsum<<<dim3((unsigned)std::min<size_t>(((size_t)F * F + 255) / 256, 1024), nt), 256, 0, h->stream>>>(
         part, F, nsplit, C);
     cudaError_t e = cudaFuncSetAttribute(k_svd_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub);
