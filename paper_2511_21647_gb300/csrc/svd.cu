@@ -31,13 +31,14 @@ __device__ __forceinline__ float2 sv_cmul(float2 a, float2 b) { return make_floa
 // hi hi + hi lo + lo hi (the dropped lo lo term is 2^-22 of it).  CTA = (frame
 // tile pair ta <= tb of 128 frames each, transmission, pixel split), 128
 // threads; thread r owns frame row a0 + r of the A tile and b0 + r of the B
-// tile.  Per 16-pixel chunk the threads convert their rows into eight operand
-// tiles (A / B x re / im x hi / lo, 128 rows x 16 TF32 each, K-major, no
-// swizzle: core matrix (k group kg of 4, row group mg of 8 rows) at byte
-// kg 2048 + mg 128, row r % 8 at + 16 (r % 8)) of one of two stages, while the
-// 24 MMAs (M = N = 128, K = 8) of the previous chunk run, issued by one thread
-// and committed to that stage's mbarrier.  The chunk after next is loaded into
-// registers meanwhile.  Accumulators in TMEM (lane = A row, column = B row):
+// tile.  Per 16-pixel chunk these 128 converter threads write their rows into
+// eight operand tiles (A / B x re / im x hi / lo, 128 rows x 16 TF32 each,
+// K-major, no swizzle: core matrix (k group kg of 4, row group mg of 8 rows) at
+// byte kg 2048 + mg 128, row r % 8 at + 16 (r % 8)) of one of three stages and
+// arrive on the stage's `full` barrier; the first thread of a fifth warp waits
+// for it, issues the chunk's 24 MMAs (M = N = 128, K = 8) and commits them to
+// the stage's `empty` barrier, which the converters wait on before reusing
+// the stage.  Each converter loads the next chunk into registers meanwhile.  Accumulators in TMEM (lane = A row, column = B row):
 // Re at columns 0-127, Xr^T Xi at 128-255, Xi^T Xr at 256-383; the epilogue
 // writes Re + i (the difference) into part[k][split][a][b] (a in tile ta, b in
 // tile tb).
@@ -48,7 +49,10 @@ __device__ __forceinline__ float2 sv_cmul(float2 a, float2 b) { return make_floa
 #define SVT_PC 16                           // pixels per chunk
 #define SVT_TILE (SVT_M * SVT_PC * 4)       // one operand tile, bytes
 #define SVT_STAGE (8 * SVT_TILE)
-#define SVT_SMEM (2 * SVT_STAGE)
+#define SVT_STAGES 3
+#define SVT_SMEM (SVT_STAGES * SVT_STAGE)
+#define SVT_CONV 128                        // converter threads (one per tile row)
+#define SVT_THREADS (SVT_CONV + 32)         // + one warp whose first thread issues the MMAs
 #define SVT_TMEM_COLS 512
 #define SVT_KMAX 1024                       // pixels per split at most
 enum { SVT_ARH = 0, SVT_ARL, SVT_AIH, SVT_AIL, SVT_BRH, SVT_BRL, SVT_BIH, SVT_BIL };
@@ -117,13 +121,19 @@ __device__ __forceinline__ void svt_ld32(unsigned taddr, float* v)
     }
 }
 
-__global__ void __launch_bounds__(128, 1) k_svd_cov_tc(const float2* __restrict__ sl, int F, int nt, int P, int ntile,
-                                                       int psplit, float2* __restrict__ part,
-                                                       unsigned* __restrict__ status)
+__device__ __forceinline__ void svt_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(SVT_THREADS, 1) k_svd_cov_tc(const float2* __restrict__ sl, int F, int nt, int P,
+                                                               int ntile, int psplit, float2* __restrict__ part,
+                                                               unsigned* __restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char svsm[];
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t full[SVT_STAGES], empty[SVT_STAGES], done;
     __shared__ unsigned s_tmem;
+    __shared__ volatile int abort_flag;
     int pair = blockIdx.x, ta = 0;
     while (pair >= ntile - ta) {
         pair -= ntile - ta;
@@ -142,8 +152,12 @@ __global__ void __launch_bounds__(128, 1) k_svd_cov_tc(const float2* __restrict_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int q = 0; q < SVT_STAGES; ++q) {
+            mbar_init(&full[q], SVT_CONV);
+            mbar_init(&empty[q], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
         mbar_fence_init();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -151,67 +165,74 @@ __global__ void __launch_bounds__(128, 1) k_svd_cov_tc(const float2* __restrict_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
     const unsigned sbase = smem_u32(svsm);
-    const int r = threadIdx.x;
-    const int fa = a0 + r, fb = b0 + r;
-    const float4* ga = fa < F ? reinterpret_cast<const float4*>(sl + ((size_t)fa * nt + k) * P) : nullptr;
-    const float4* gb = fb < F ? reinterpret_cast<const float4*>(sl + ((size_t)fb * nt + k) * P) : nullptr;
-    const unsigned roff = (unsigned)(r * 16);   // (r / 8) 128 + (r % 8) 16
-    // raw chunk: float4 j of a row holds pixels 2 j, 2 j + 1 of the chunk (re, im, re, im)
-    auto load = [&](int c, float4 (&xa)[8], float4 (&xb)[8]) {
-        const int pc = p0 + c * SVT_PC;
+    if (threadIdx.x < SVT_CONV) {
+        // converter: row r of the A tile (frame a0 + r) and of the B tile (b0 + r)
+        const int r = threadIdx.x;
+        const int fa = a0 + r, fb = b0 + r;
+        const float4* ga = fa < F ? reinterpret_cast<const float4*>(sl + ((size_t)fa * nt + k) * P) : nullptr;
+        const float4* gb = fb < F ? reinterpret_cast<const float4*>(sl + ((size_t)fb * nt + k) * P) : nullptr;
+        const unsigned roff = (unsigned)(r * 16);   // (r / 8) 128 + (r % 8) 16
+        // float4 j of a raw chunk row holds pixels 2 j, 2 j + 1 (re, im, re, im)
+        auto load = [&](int c, float4 (&xa)[8], float4 (&xb)[8]) {
+            const int pc = p0 + c * SVT_PC;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int p = pc + 2 * j;   // pixel quads are either inside [p0, p1) or outside (P % 4 == 0)
-            const bool in = c < nch && p < p1;
-            xa[j] = (ga && in) ? __ldg(ga + p / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
-            xb[j] = (gb && in) ? __ldg(gb + p / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    float4 ra[8], rb[8];
-    load(0, ra, rb);
-    unsigned phase = 0;      // bit q: parity of the next completion of bars[q]
-    int pending[2] = {0, 0}; // commits of bars[q] not yet waited for
-    bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-        const int q = c & 1;
-        float4 na[8], nb[8];
-        load(c + 1, na, nb);
-        if (pending[q]) {
-            // the MMAs of chunk c - 2 read stage q
-            if (!mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) ok = false;
-            phase ^= 1u << q;
-            pending[q] = 0;
-        }
-        if (__syncthreads_or(!ok)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned st = sbase + (unsigned)(q * SVT_STAGE) + roff;
+            for (int j = 0; j < 8; ++j) {
+                const int p = pc + 2 * j;   // pixel pairs are either inside [p0, p1) or outside (P % 4 == 0)
+                const bool in = c < nch && p < p1;
+                xa[j] = (ga && in) ? __ldg(ga + p / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xb[j] = (gb && in) ? __ldg(gb + p / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        float4 ra[8], rb[8];
+        load(0, ra, rb);
+        for (int c = 0; c < nch; ++c) {
+            const int q = c % SVT_STAGES, u = c / SVT_STAGES;
+            float4 na[8], nb[8];
+            load(c + 1, na, nb);
+            // use u of stage q waits until the MMAs of use u - 1 have read it
+            if (u > 0 && !mbar_wait_bounded(&empty[q], (unsigned)(u - 1) & 1u)) abort_flag = 1;
+            if (abort_flag) break;
+            const unsigned st = sbase + (unsigned)(q * SVT_STAGE) + roff;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {   // k group i: pixels 4 i .. 4 i + 3 of the chunk
-            uint4 h, l;
-            const float4 u = ra[2 * i], v = ra[2 * i + 1];
-            svt_split(u.x, u.z, v.x, v.z, h, l);
-            svt_st16(st + SVT_ARH * SVT_TILE + i * 2048, h);
-            svt_st16(st + SVT_ARL * SVT_TILE + i * 2048, l);
-            svt_split(u.y, u.w, v.y, v.w, h, l);
-            svt_st16(st + SVT_AIH * SVT_TILE + i * 2048, h);
-            svt_st16(st + SVT_AIL * SVT_TILE + i * 2048, l);
-            const float4 w = rb[2 * i], x = rb[2 * i + 1];
-            svt_split(w.x, w.z, x.x, x.z, h, l);
-            svt_st16(st + SVT_BRH * SVT_TILE + i * 2048, h);
-            svt_st16(st + SVT_BRL * SVT_TILE + i * 2048, l);
-            svt_split(w.y, w.w, x.y, x.w, h, l);
-            svt_st16(st + SVT_BIH * SVT_TILE + i * 2048, h);
-            svt_st16(st + SVT_BIL * SVT_TILE + i * 2048, l);
+            for (int i = 0; i < 4; ++i) {   // k group i: pixels 4 i .. 4 i + 3 of the chunk
+                uint4 h, l;
+                const float4 x0 = ra[2 * i], x1 = ra[2 * i + 1];
+                svt_split(x0.x, x0.z, x1.x, x1.z, h, l);
+                svt_st16(st + SVT_ARH * SVT_TILE + i * 2048, h);
+                svt_st16(st + SVT_ARL * SVT_TILE + i * 2048, l);
+                svt_split(x0.y, x0.w, x1.y, x1.w, h, l);
+                svt_st16(st + SVT_AIH * SVT_TILE + i * 2048, h);
+                svt_st16(st + SVT_AIL * SVT_TILE + i * 2048, l);
+                const float4 y0 = rb[2 * i], y1 = rb[2 * i + 1];
+                svt_split(y0.x, y0.z, y1.x, y1.z, h, l);
+                svt_st16(st + SVT_BRH * SVT_TILE + i * 2048, h);
+                svt_st16(st + SVT_BRL * SVT_TILE + i * 2048, l);
+                svt_split(y0.y, y0.w, y1.y, y1.w, h, l);
+                svt_st16(st + SVT_BIH * SVT_TILE + i * 2048, h);
+                svt_st16(st + SVT_BIL * SVT_TILE + i * 2048, l);
+            }
+            // this thread's generic-proxy writes before the tensor cores read them
+            fence_proxy_async();
+            svt_arrive(&full[q]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                ra[j] = na[j];
+                rb[j] = nb[j];
+            }
         }
-        // generic-proxy writes of the stage before the tensor cores read it
-        fence_proxy_async();
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    } else if (lane == 0) {
+        // MMA issue (first thread of the fifth warp; the rest of the warp waits
+        // at the __syncwarp below): the 24 MMAs of chunk c once its stage is
+        // full, committed to the stage's empty barrier; the final commit (all
+        // MMAs) to `done`
+        const unsigned dRe = tmem, dP = tmem + 128, dN = tmem + 256;
+        for (int c = 0; c < nch; ++c) {
+            const int q = c % SVT_STAGES, u = c / SVT_STAGES;
+            if (!mbar_wait_bounded(&full[q], (unsigned)u & 1u)) abort_flag = 1;
+            if (abort_flag) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned sq = sbase + (unsigned)(q * SVT_STAGE);
             auto d = [&](int t, int s) { return svt_sdesc(sq + t * SVT_TILE + s * 4096, 2048, 128); };
-            const unsigned dRe = tmem, dP = tmem + 128, dN = tmem + 256;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const int acc = (c | s) != 0;
@@ -229,29 +250,20 @@ __global__ void __launch_bounds__(128, 1) k_svd_cov_tc(const float2* __restrict_
                 svt_mma(dN, d(SVT_AIL, s), d(SVT_BRH, s), 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bars[q]))
+                             smem_u32(&empty[q]))
                          : "memory");
         }
-        pending[q] = 1;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            ra[j] = na[j];
-            rb[j] = nb[j];
-        }
+        // arrives once every MMA issued above has completed (none issued: at once)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
     }
-    // the MMAs still in flight complete (bounded) before the accumulators are read or freed
-    for (int cc = 0; cc < 2; ++cc) {
-        // older commit first: the stage of chunk nch - 2, then of nch - 1
-        const int q = (nch + cc) & 1;
-        if (pending[q]) {
-            if (!mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) ok = false;
-            phase ^= 1u << q;
-            pending[q] = 0;
-        }
-    }
-    if (__syncthreads_or(!ok)) {
+    if (warp == SVT_CONV / 32) __syncwarp();
+    // every thread: the MMAs complete (bounded) before the accumulators are read or freed
+    const bool fin = mbar_wait_bounded(&done, 0u);
+    if (__syncthreads_or(!fin || abort_flag)) {
         if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    } else if (nch > 0) {
+    } else if (nch > 0 && warp < SVT_CONV / 32) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float2* dst = part + (((size_t)k * gridDim.z + split) * F) * F;
         const int a = a0 + 32 * warp + lane;
@@ -274,8 +286,11 @@ __global__ void __launch_bounds__(128, 1) k_svd_cov_tc(const float2* __restrict_
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[0])) : "memory");
-        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[1])) : "memory");
+        for (int q = 0; q < SVT_STAGES; ++q) {
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[q])) : "memory");
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&empty[q])) : "memory");
+        }
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&done)) : "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -526,8 +541,8 @@ rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices
     float2* Y = reinterpret_cast<float2*>((char*)Q + up(n_Q * 8));
     cudaError_t ea = cudaFuncSetAttribute(k_svd_cov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SVT_SMEM);
     if (ea != cudaSuccess) return cuda_check(h, ea, "covariance smem attribute");
-    k_svd_cov_tc<<<dim3(npair, nt, nsplit), 128, SVT_SMEM, h->stream>>>(slices, F, nt, P, ntile, psplit, part,
-                                                                         h->d_status);
+    k_svd_cov_tc<<<dim3(npair, nt, nsplit), SVT_THREADS, SVT_SMEM, h->stream>>>(slices, F, nt, P, ntile, psplit,
+                                                                                 part, h->d_status);
     k_svd_covsum<<<dim3((unsigned)std::min<size_t>(((size_t)F * F + 255) / 256, 1024), nt), 256, 0, h->stream>>>(
         part, F, nsplit, C);
     cudaError_t e = cudaFuncSetAttribute(k_svd_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub);
