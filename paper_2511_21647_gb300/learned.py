@@ -1,7 +1,7 @@
 """Learned localiser: training data from simulated ensembles with known
 microbubble positions, training on the GPU with librca's CNN kernels, and
-evaluation against the NCC localiser (which stays the fallback and the judge
-of localisation error).
+evaluation against the NCC localiser (which stays the fallback and the
+reference the localisation error is compared with).
 
 Targets: every visible microbubble is projected onto the XZ plane of its
 y-slab and the YZ plane of its x-slab (Sec. II-A4's sub-blocks) and drawn as
