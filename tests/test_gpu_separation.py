@@ -129,6 +129,31 @@ def test_fused_enhancement_matches_oracle(S, tiny, tiny_planes, enh):
         assert np.allclose(M[s], M2.cpu().numpy(), rtol=2e-6, atol=0)
 
 
+@pytest.mark.parametrize("F", [64, 300])
+@pytest.mark.parametrize("enh", [0, 1])
+def test_fused_enhancement_random_planes(S, F, enh):
+    """both amplitude modes on the generic plan (64 frames) and the 300-frame
+    compile-time plan, random planes of the tiny geometry"""
+    from paper_2511_21647_gb300 import _lib as L, rca
+    rng = np.random.default_rng(100 + F + enh)
+    shape = S.planes_shape(F)
+    x = (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
+    prm = rca.make_sep_params(400.0, 3)
+    A, M = S.separate_enhance(c64(x), prm, enh=enh)
+    torch.cuda.synchronize()
+    assert S.sync_status() == 0
+    subs = OSep.separate(x.astype(np.complex128), 400.0, np.array(prm.edges_hz[:4]))
+    A, M = A.cpu().numpy(), M.cpu().numpy()
+    for s in range(6):
+        if enh == L.ULM_ENH_XDOPPLER:
+            A_o, M_o = O.xdoppler(subs[s])
+        else:
+            A_o = np.abs(subs[s][:, :, 0] + subs[s][:, :, 1])
+            M_o = A_o.reshape(F, -1).max(axis=1)
+        assert rel(A[s], A_o) < 2e-5, (s, rel(A[s], A_o))
+        assert np.allclose(M[s], M_o, rtol=2e-5, atol=0), s
+
+
 def test_subset_localisation_runs_on_fused_output(S, tiny, tiny_planes):
     """each subset's A / M slice feeds ulm_detect2d and ulm_pair3d as they are;
     the detections equal those of the oracle's amplitude of that subset"""
