@@ -29,17 +29,18 @@ __device__ __forceinline__ float2 sv_cmul(float2 a, float2 b) { return make_floa
 // (a frame's slice is contiguous in pixels).  FP32 accuracy from TF32 operands:
 // x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and a product a b taken as
 // hi hi + hi lo + lo hi (the dropped lo lo term is 2^-22 of it).  CTA = (frame
-// tile pair ta <= tb of 128 frames each, transmission, pixel split), 128
-// threads; thread r owns frame row a0 + r of the A tile and b0 + r of the B
-// tile.  Per 16-pixel chunk these 128 converter threads write their rows into
-// eight operand tiles (A / B x re / im x hi / lo, 128 rows x 16 TF32 each,
-// K-major, no swizzle: core matrix (k group kg of 4, row group mg of 8 rows) at
-// byte kg 2048 + mg 128, row r % 8 at + 16 (r % 8)) of one of three stages and
-// arrive on the stage's `full` barrier; the first thread of a fifth warp waits
-// for it, issues the chunk's 24 MMAs (M = N = 128, K = 8) and commits them to
-// the stage's `empty` barrier, which the converters wait on before reusing
-// the stage.  Each converter loads the next chunk into registers meanwhile.  Accumulators in TMEM (lane = A row, column = B row):
-// Re at columns 0-127, Xr^T Xi at 128-255, Xi^T Xr at 256-383; the epilogue
+// tile pair ta <= tb of 128 frames each, transmission, pixel split), 160
+// threads.  Converter thread r < 128 owns frame row a0 + r of the A tile and
+// b0 + r of the B tile: per 16-pixel chunk it writes its rows into eight
+// operand tiles (A / B x re / im x hi / lo, 128 rows x 16 TF32 each, K-major,
+// no swizzle: core matrix (k group kg of 4, row group mg of 8 rows) at byte
+// kg 2048 + mg 128, row r % 8 at + 16 (r % 8)) of one of three stages and
+// arrives on the stage's `full` barrier; the first thread of the fifth warp
+// waits for it, issues the chunk's 24 MMAs (M = N = 128, K = 8) and commits
+// them to the stage's `empty` barrier, which the converters wait on before
+// reusing the stage.  Each converter loads the next chunk into registers
+// meanwhile.  Accumulators in TMEM (lane = A row, column = B row): Re at
+// columns 0-127, Xr^T Xi at 128-255, Xi^T Xr at 256-383; the epilogue
 // writes Re + i (the difference) into part[k][split][a][b] (a in tile ta, b in
 // tile tb).
 // Every mbarrier wait is bounded; on a timeout the CTA records ST_TIMEOUT,
