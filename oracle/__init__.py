@@ -108,6 +108,7 @@ def lib():
                 "or_track_build": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
                 "or_track_grid": (None, [_P, _D, _P]),
                 "or_track_accumulate": (None, [_P, _I, _P, _P, _P]),
+                "or_track_velocity": (None, [_P, _I, _P, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -376,6 +377,18 @@ def track_accumulate(g, tracks, prm: TrackParams) -> np.ndarray:
     tr = np.ascontiguousarray(tracks, dtype=TRACK)
     lib().or_track_accumulate(_byref(geom(g)), len(tr), _ptr(tr) if len(tr) else None, _byref(prm), _ptr(grid))
     return grid
+
+
+def track_velocity(g, tracks, prm: TrackParams):
+    """velocity sums (speed, axial component) per voxel [nz_v][ny_v][nx_v] (int64,
+    nanometres per frame interval, one term per accumulation sample)"""
+    nx, ny, nz = track_grid(g, prm.voxel)
+    speed = np.zeros((nz, ny, nx), dtype=np.int64)
+    vz = np.zeros((nz, ny, nx), dtype=np.int64)
+    tr = np.ascontiguousarray(tracks, dtype=TRACK)
+    lib().or_track_velocity(_byref(geom(g)), len(tr), _ptr(tr) if len(tr) else None, _byref(prm), _ptr(speed),
+                            _ptr(vz))
+    return speed, vz
 
 
 def track(g, list3d, prm: TrackParams):

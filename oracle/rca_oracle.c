@@ -810,3 +810,44 @@ void or_track_accumulate(const or_geom* g, int ntr, const or_track* tr, const or
         }
     }
 }
+
+/* Velocity volumes (Sec. II-C: density and velocity volumes on the 50 um grid):
+ * at every accumulation sample of an accepted track (the samples and voxels of
+ * or_track_accumulate) the smoothed track's velocity is the derivative of its
+ * quadratic, v = a1 + 2 a2 phi1(tau) per axis (metres per frame interval).  The
+ * voxel adds the speed |v| and the axial component v_z (positive = deeper),
+ * each rounded to a whole nanometre per frame interval, to two integer sums;
+ * mean values are the sums over the density count (times the frame rate for
+ * metres per second). */
+void or_track_velocity(const or_geom* g, int ntr, const or_track* tr, const or_track_params* prm,
+                       long long* speed_sum, long long* vz_sum)
+{
+    int dims[3];
+    or_track_grid(g, prm->voxel, dims);
+    const int L = prm->len;
+    const double m = 0.5 * (double)(L - 1), q = ((double)L * (double)L - 1.0) / 12.0;
+    const double lo[3] = {-0.5 * (double)g->n_el * g->pitch, -0.5 * (double)g->n_el * g->pitch,
+                          g->z0 - 0.5 * g->dz};
+    for (int k = 0; k < ntr; ++k) {
+        if (!tr[k].accepted) continue;
+        for (int s = 0; s <= (L - 1) * prm->substeps; ++s) {
+            const double tau = (double)s / (double)prm->substeps;
+            const double f1 = tau - m, f2 = f1 * f1 - q;
+            int iv[3], inside = 1;
+            double v[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                const double p = tr[k].a[ax][0] + tr[k].a[ax][1] * f1 + tr[k].a[ax][2] * f2;
+                const double c = floor((p - lo[ax]) / prm->voxel);
+                inside = inside && c >= 0.0 && c < (double)dims[ax];
+                iv[ax] = inside ? (int)c : 0;
+                v[ax] = tr[k].a[ax][1] + 2.0 * tr[k].a[ax][2] * f1;
+            }
+            if (inside) {
+                const size_t at = ((size_t)iv[2] * dims[1] + iv[1]) * dims[0] + iv[0];
+                const double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                speed_sum[at] += llrint(sp * 1e9);
+                vz_sum[at] += llrint(v[2] * 1e9);
+            }
+        }
+    }
+}

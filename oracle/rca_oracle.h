@@ -127,6 +127,8 @@ int or_track_build(const or_geom* g, int n, const int* frame, const double* x, c
 void or_track_grid(const or_geom* g, double voxel, int dims[3]);
 void or_track_accumulate(const or_geom* g, int ntr, const or_track* tr, const or_track_params* prm,
                          unsigned* grid);
+void or_track_velocity(const or_geom* g, int ntr, const or_track* tr, const or_track_params* prm,
+                       long long* speed_sum, long long* vz_sum);
 
 #ifdef __cplusplus
 }

@@ -2,7 +2,8 @@
 quadratic against numpy's polynomial fit and exact quadratic paths, the
 pairing against brute-force optimal assignment on sparse scenes, the
 rejection rules on paths whose turn and speed change are known in closed
-form, and the density accumulation on a path whose voxel counts are known."""
+form, the density accumulation on a path whose voxel counts are known, and
+the velocity sums on constant-velocity and accelerating paths."""
 import math
 
 import numpy as np
@@ -191,3 +192,49 @@ def test_density_counts_closed_form(tiny):
     p_out = p + np.array([0.0, 0.0, -5e-3])[None, :]
     _, tr2, grid2 = O.track(g, _to_list(g, np.arange(LEN), p_out), prm)
     assert tr2[0]["accepted"] == 1 and grid2.sum() == 0
+
+
+@pytest.mark.parametrize("v", [(0.0, 0.0, 25e-6), (0.0, 0.0, -25e-6), (30e-6, 40e-6, 0.0), (-12e-6, 0.0, 16e-6)])
+def test_velocity_sums_constant_velocity(tiny, v):
+    """A straight path at v metres per frame: every accumulation sample adds |v|
+    and v_z in whole nanometres per frame to its voxel (|v| = 25, 25, 50, 20 um)."""
+    g = _geom(tiny)
+    prm = O.track_params(substeps=10, voxel=50e-6)
+    vox = prm.voxel
+    lo = np.array([-0.5 * g.n_el * g.pitch, -0.5 * g.n_el * g.pitch, g.z0 - 0.5 * g.dz])
+    tau = np.arange(LEN, dtype=np.float64)
+    p0 = lo + np.array([60.5, 60.5, 60.5]) * vox
+    p = p0[None, :] + np.asarray(v)[None, :] * tau[:, None]
+    _, tr, grid = O.track(g, _to_list(g, np.arange(LEN), p), prm)
+    assert len(tr) == 1 and tr[0]["accepted"] == 1
+    speed, vz = O.track_velocity(g, tr, prm)
+    sp_nm = round(1e9 * math.sqrt(sum(x * x for x in v)))
+    vz_nm = round(1e9 * v[2])
+    assert grid.sum() == (LEN - 1) * prm.substeps + 1
+    assert np.array_equal(speed, grid.astype(np.int64) * sp_nm)
+    assert np.array_equal(vz, grid.astype(np.int64) * vz_nm)
+
+
+def test_velocity_sums_accelerating_path(tiny):
+    """z = z0 + u tau + w tau^2 with u = 20 um and w = 0.25 um per frame^2: the
+    smoothed velocity at sample s (tau = s / 10) is u + 2 w tau = 20 000 + 50 s
+    nanometres per frame, positive (deeper); a track wholly outside the grid
+    adds nothing."""
+    g = _geom(tiny)
+    prm = O.track_params(substeps=10, voxel=50e-6)
+    vox = prm.voxel
+    lo = np.array([-0.5 * g.n_el * g.pitch, -0.5 * g.n_el * g.pitch, g.z0 - 0.5 * g.dz])
+    tau = np.arange(LEN, dtype=np.float64)
+    p = _path(lo + np.array([30.5, 30.5, 3.5]) * vox, np.array([0.0, 0.0, 20e-6]), np.array([0.0, 0.0, 0.25e-6]), tau)
+    _, tr, grid = O.track(g, _to_list(g, np.arange(LEN), p), prm)
+    assert len(tr) == 1 and tr[0]["accepted"] == 1
+    speed, vz = O.track_velocity(g, tr, prm)
+    ns = (LEN - 1) * prm.substeps + 1
+    want = sum(20000 + 50 * s for s in range(ns))
+    assert grid.sum() == ns and vz.sum() == want and speed.sum() == want
+    assert np.all(speed[grid == 0] == 0)
+    p_out = p + np.array([0.0, 0.0, -5e-3])[None, :]
+    _, tr2, _ = O.track(g, _to_list(g, np.arange(LEN), p_out), prm)
+    s2, v2 = O.track_velocity(g, tr2, prm)
+    assert tr2[0]["accepted"] == 1 and not s2.any() and not v2.any()
+
