@@ -592,7 +592,8 @@ def pipeline_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, planes, 
     on the unfiltered slices, the SVD clutter filter (rank 16, 30 subspace
     iterations), Stage 2 + projection, separation into three speeds x up /
     down fused with each subset's XDoppler, and per subset detection, pairing
-    and tracking into one density grid (zeroed per ensemble).  Context for the
+    and tracking into one density grid and its velocity volumes (zeroed per
+    ensemble).  Context for the
     paper's 0.52 s per 300-volume ensemble on its own GPU and data."""
     import torch
     h, t = sess.h, sess.t
@@ -606,6 +607,7 @@ def pipeline_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, planes, 
     tp = R.make_track_params()
     nx, ny, nz = R.ulm_density_shape(t, tp.voxel_m)
     grid = torch.zeros((nz, ny, nx), dtype=torch.int32, device=dev)
+    vel = torch.zeros((2, nz, ny, nx), dtype=torch.int64, device=dev)
     trk = [torch.zeros((cap3d, L.TRACK.itemsize // 4), dtype=torch.int32, device=dev) for _ in range(ns)]
     ntr = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(ns)]
     parts = ["stage1", "motion", "svd", "stage2", "separate", "localise_track"]
@@ -627,11 +629,13 @@ def pipeline_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, planes, 
         R.ulm_separate_enhance(h, t, planes, L.RCA_C32, F, sp, L.ULM_ENH_XDOPPLER, A, M)
         mark(5)
         grid.zero_()
+        vel.zero_()
         for s in range(ns):
             out2d, n2d, out3d, n3d = bufs[s]
             R.ulm_detect2d(h, t, A[s], M[s], F, prm, out2d, cap2d, n2d)
             R.ulm_pair3d(h, t, out2d, n2d, cap2d, F, out3d, cap3d, n3d)
             R.ulm_track(h, t, out3d, n3d, cap3d, F, tp, trk[s], cap3d, ntr[s], grid)
+            R.ulm_track_velocity(h, t, trk[s], ntr[s], cap3d, tp, vel[0], vel[1])
         mark(6)
 
     for _ in range(2):
@@ -649,7 +653,7 @@ def pipeline_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, planes, 
         kept += int(trk[s][:k].cpu().numpy().view(L.TRACK).reshape(-1)["accepted"].sum())
     return {"ms_per_ensemble": round(tot, 3), "volumes_per_s": round(F / (tot / 1e3), 1), "parts_ms": part_ms,
             "order": "ingest (no clutter removal) + Stage 1 | motion | SVD rank 16 | Stage 2 + projection | "
-                     "separation x6 + XDoppler | per subset: detect, pair, track",
+                     "separation x6 + XDoppler | per subset: detect, pair, track, density + velocity",
             "n3d_per_subset": [int(b[3].item()) for b in bufs], "tracks_kept": kept,
             "density_counts": int(grid.sum().item()),
             "paper_ms_per_ensemble_context": 520.0, "status": R.rca_sync_status(h)}
@@ -658,18 +662,21 @@ def pipeline_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, planes, 
 def tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K):
     """Fixed-length tracking (Sec. II-A6) of the last step's 3D list: ten-point
     tracks, 150 um link radius, 45 degree / half-mean-speed rejection, 50 um
-    density grid; not part of the timed step (the paper's tracking follows the
-    projection path)."""
+    density and velocity volumes; not part of the timed step (the paper's
+    tracking follows the projection path)."""
     import torch
     prm = R.make_track_params()
     nx, ny, nz = R.ulm_density_shape(sess.t, prm.voxel_m)
     grid = torch.zeros((nz, ny, nx), dtype=torch.int32, device=out3d.device)
+    speed = torch.zeros((nz, ny, nx), dtype=torch.int64, device=out3d.device)
+    vz = torch.zeros_like(speed)
     cap_t = cap3d
     out = torch.zeros((cap_t, L.TRACK.itemsize // 4), dtype=torch.int32, device=out3d.device)
     nt = torch.zeros(1, dtype=torch.int32, device=out3d.device)
 
     def run():
         R.ulm_track(sess.h, sess.t, out3d, n3d, cap3d, F, prm, out, cap_t, nt, grid)
+        R.ulm_track_velocity(sess.h, sess.t, out, nt, cap_t, prm, speed, vz)
 
     for _ in range(3):
         run()
@@ -686,7 +693,8 @@ def tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K):
             "accepted": int(rec["accepted"].sum()), "localisations": int(n3d.item()),
             "params": {"len": prm.len, "max_step_m": prm.max_step_m, "max_turn_deg": 45.0,
                        "max_speed_change": prm.max_speed_change, "voxel_m": prm.voxel_m, "substeps": prm.substeps},
-            "density_grid": [nz, ny, nx], "kernels": 6, "status": R.rca_sync_status(sess.h)}
+            "density_grid": [nz, ny, nx], "velocity_volumes": "speed and axial sums, nm per frame, int64",
+            "kernels": 7, "status": R.rca_sync_status(sess.h)}
 
 
 def reduced_form(R, L, sess, rf, F, prm, W, K, stream):

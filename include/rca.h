@@ -481,6 +481,20 @@ rca_status ulm_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* list3d
                      int n_frames, const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks_dev,
                      uint32_t* density);
 
+/* Velocity volumes of the tracks ulm_track wrote (Sec. II-C: density and
+ * velocity volumes): at every accumulation sample of an accepted track (the
+ * samples and voxels of the density), the smoothed track's velocity is the
+ * derivative of its quadratic, v = a1 + 2 a2 phi1(tau) per axis (metres per
+ * frame interval); the voxel adds |v| and v_z (positive = deeper), each
+ * rounded to a whole nanometre per frame interval, to two 64-bit integer sums
+ * (exact in any order).  Mean speed of a voxel = speed_sum / density count x
+ * frame rate (m/s).  Accumulated INTO the sums (zero them first).
+ *   tracks, *n_tracks_dev, cap_tracks: as ulm_track wrote them; prm: the same
+ *   parameters; speed_sum, vz_sum: device int64 [nz][ny][nx] (ulm_density_shape).
+ * Host-side errors: invalid parameters or sizes (INVALID_ARG). */
+rca_status ulm_track_velocity(rca_handle* h, const rca_tables* t, const ulm_track_rec* tracks, const int* n_tracks_dev,
+                              int cap_tracks, const ulm_track_params* prm, int64_t* speed_sum, int64_t* vz_sum);
+
 /* ---------------------------------------------------------------------- */
 /* Learned localiser (the paper's future-work form, Sec. IV)               */
 /* ---------------------------------------------------------------------- */

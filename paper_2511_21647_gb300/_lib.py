@@ -125,6 +125,7 @@ SIGNATURES = {
     "ulm_separate": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_sep_params), _P]),
     "ulm_separate_enhance": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_sep_params), _I, _P, _P]),
     "ulm_track": (_S, [_P, _P, _P, _P, _I, _I, C.POINTER(ulm_track_params), _P, _I, _P, _P]),
+    "ulm_track_velocity": (_S, [_P, _P, _P, _P, _I, C.POINTER(ulm_track_params), _P, _P]),
     "ulm_cnn_create": (_S, [_P, C.POINTER(ulm_cnn_desc), C.POINTER(_P)]),
     "ulm_cnn_destroy": (_S, [_P]),
     "ulm_cnn_param_count": (_S, [_P, C.POINTER(_SZ)]),

@@ -608,6 +608,25 @@ extern "C" rca_status ulm_track(rca_handle* h, const rca_tables* t, const ulm_lo
     return launch_track(h, t, L, n3d, cap3d, F, prm, out, cap_tracks, n_tracks, density);
 }
 
+extern "C" rca_status ulm_track_velocity(rca_handle* h, const rca_tables* t, const ulm_track_rec* tracks,
+                                         const int* n_tracks, int cap_tracks, const ulm_track_params* prm,
+                                         int64_t* speed_sum, int64_t* vz_sum)
+{
+    CHECK_HANDLE(h);
+    if (!t || !prm) return set_error(h, RCA_ERR_INVALID_ARG, "null tables or tracking parameters");
+    if (prm->len < 2 || prm->len > ULM_TRACK_MAX_LEN || prm->substeps < 1 || prm->substeps > 1024 ||
+        !(prm->voxel_m > 0.0))
+        return set_error(h, RCA_ERR_INVALID_ARG, "track length, substeps or voxel out of range");
+    if (!n_tracks || !speed_sum || !vz_sum || cap_tracks < 0 || (cap_tracks > 0 && !tracks))
+        return set_error(h, RCA_ERR_INVALID_ARG, "null tracks, count or velocity sums");
+    int d[3];
+    density_shape(t->gd, prm->voxel_m, d);
+    if (d[0] <= 0 || d[2] <= 0 || (double)d[0] * d[1] * d[2] > 4.0e9)
+        return set_error(h, RCA_ERR_INVALID_ARG, "velocity grid of %d x %d x %d voxels", d[0], d[1], d[2]);
+    DeviceGuard dg(h->device);
+    return launch_track_velocity(h, t, tracks, n_tracks, cap_tracks, prm, speed_sum, vz_sum);
+}
+
 extern "C" rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
                                    const ulm_params* prm, ulm_loc2d* out2d, int cap2d, int* n2d, ulm_loc3d* out3d,
                                    int cap3d, int* n3d)

@@ -239,6 +239,9 @@ rca_status launch_separate(rca_handle* h, const rca_tables* t, const void* plane
                            const ulm_sep_params* prm, int enh, float2* sub, float* A, float* M);
 rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slices, int F, float* motion,
                          float* shifts, int* peaks);
+rca_status launch_track_velocity(rca_handle* h, const rca_tables* t, const ulm_track_rec* tracks,
+                                 const int* n_tracks, int cap_tracks, const ulm_track_params* prm, int64_t* speed,
+                                 int64_t* vz);
 rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d, int F,
                         const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks, unsigned* density);
 rca_status launch_stage2(rca_handle* h, const rca_tables* t, const float2* slices, int F, void* planes,

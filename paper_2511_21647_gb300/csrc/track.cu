@@ -10,6 +10,8 @@
 //                     least-squares quadratic, apply the turn and speed tests
 //   k_track_scan / k_track_write   compaction in order of the first point
 //   k_track_accumulate one thread per (track, sample): density counts
+//   k_track_velocity   one thread per (track, sample): velocity sums (speed and
+//                      axial component, whole nanometres per frame interval)
 // Every decision and coefficient is computed in double precision with the
 // operations in a fixed order; this unit is compiled without fused
 // multiply-add contraction, so each double result rounds exactly as written.
@@ -225,6 +227,43 @@ __global__ void k_track_accumulate(TrackConst c, const ulm_track_rec* __restrict
     }
 }
 
+// Velocity at every accumulation sample of an accepted track: the derivative
+// of the smoothed quadratic, v = a1 + 2 a2 phi1(tau) per axis (metres per frame
+// interval); the voxel of the sample (as for the density) adds |v| and v_z,
+// each rounded to a whole nanometre, to 64-bit integer sums, so the result is
+// exact whatever the order of the atomic additions.
+__global__ void k_track_velocity(TrackConst c, const ulm_track_rec* __restrict__ tr, const int* __restrict__ n_tracks,
+                                 int cap_tracks, unsigned long long* __restrict__ speed,
+                                 unsigned long long* __restrict__ vz)
+{
+    const int nt = min(*n_tracks, cap_tracks);
+    const int ns = (c.len - 1) * c.substeps + 1;
+    const long long total = (long long)nt * ns;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(w / ns), s = (int)(w - (long long)k * ns);
+        if (!tr[k].accepted) continue;
+        const double tau = (double)s / (double)c.substeps;
+        const double f1 = tau - c.m, f2 = f1 * f1 - c.q;
+        int iv[3];
+        double v[3];
+        bool inside = true;
+        for (int ax = 0; ax < 3; ++ax) {
+            const double p = tr[k].a[ax][0] + tr[k].a[ax][1] * f1 + tr[k].a[ax][2] * f2;
+            const double cv = floor((p - c.lo[ax]) / c.voxel);
+            inside = inside && cv >= 0.0 && cv < (double)c.dims[ax];
+            iv[ax] = inside ? (int)cv : 0;
+            v[ax] = tr[k].a[ax][1] + 2.0 * tr[k].a[ax][2] * f1;
+        }
+        if (inside) {
+            const size_t at = ((size_t)iv[2] * c.dims[1] + iv[1]) * c.dims[0] + iv[0];
+            const double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            atomicAdd(speed + at, (unsigned long long)llrint(sp * 1e9));
+            atomicAdd(vz + at, (unsigned long long)llrint(v[2] * 1e9));
+        }
+    }
+}
+
 }  // namespace
 
 void density_shape(const GeomDev& g, double voxel, int dims[3])
@@ -234,10 +273,8 @@ void density_shape(const GeomDev& g, double voxel, int dims[3])
     dims[2] = (int)std::ceil((double)g.nz * g.dz / voxel);
 }
 
-rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d, int F,
-                        const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks, unsigned* density)
+static TrackConst track_const(const GeomDev& g, const ulm_track_params* prm)
 {
-    const GeomDev& g = t->gd;
     TrackConst c;
     c.half_span = 0.5 * (double)(g.N - 1);
     c.pitch = g.pitch;
@@ -262,7 +299,29 @@ rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, 
     c.cos_max_turn = prm->cos_max_turn;
     c.max_speed_change = prm->max_speed_change;
     density_shape(g, prm->voxel_m, c.dims);
+    return c;
+}
 
+rca_status launch_track_velocity(rca_handle* h, const rca_tables* t, const ulm_track_rec* tracks,
+                                 const int* n_tracks, int cap_tracks, const ulm_track_params* prm, int64_t* speed,
+                                 int64_t* vz)
+{
+    const TrackConst c = track_const(t->gd, prm);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t samples = (size_t)std::max(cap_tracks, 1) * ((size_t)(c.len - 1) * c.substeps + 1);
+    const int grid_a = (int)std::min<size_t>((samples + TR_THREADS - 1) / TR_THREADS, (size_t)sms * 16);
+    k_track_velocity<<<grid_a, TR_THREADS, 0, h->stream>>>(c, tracks, n_tracks, cap_tracks,
+                                                           reinterpret_cast<unsigned long long*>(speed),
+                                                           reinterpret_cast<unsigned long long*>(vz));
+    return cuda_check(h, cudaGetLastError(), "velocity kernel");
+}
+
+rca_status launch_track(rca_handle* h, const rca_tables* t, const ulm_loc3d* L, const int* n3d, int cap3d, int F,
+                        const ulm_track_params* prm, ulm_track_rec* out, int cap_tracks, int* n_tracks, unsigned* density)
+{
+    const TrackConst c = track_const(t->gd, prm);
     rca_status st = RCA_OK;
     const size_t nmax = (size_t)std::max(cap3d, 1);
     // workspace: offsets [F + 2], nxt, prv, flag [n], pos [n + 1], records [n]

@@ -239,6 +239,11 @@ def ulm_track(h, t, list3d, n3d, cap3d, n_frames, prm, out, cap_tracks, n_tracks
                               _ptr(n_tracks), _ptr(density)), h)
 
 
+def ulm_track_velocity(h, t, tracks, n_tracks, cap_tracks, prm, speed_sum, vz_sum):
+    _check(L.load().ulm_track_velocity(h, t, _ptr(tracks), _ptr(n_tracks), cap_tracks, C.byref(prm), _ptr(speed_sum),
+                                       _ptr(vz_sum)), h)
+
+
 def ulm_pair3d_noalloc(h, t, list2d, n2d, cap2d, n_frames, out3d, cap3d, n3d):
     """ulm_pair3d on the library's fixed per-device scratch (no allocation)."""
     _check(L.load().ulm_pair3d_noalloc(h, t, _ptr(list2d), _ptr(n2d), cap2d, n_frames, _ptr(out3d), cap3d, _ptr(n3d)), h)

@@ -92,6 +92,47 @@ def test_tracks_and_density_bit_exact_on_synthetic_scenes(S, tiny, seed, n_bub):
     assert np.mean(same) > 0.9
 
 
+@pytest.mark.parametrize("seed,n_bub", [(23, 120)])
+def test_velocity_sums_bit_exact(S, tiny, seed, n_bub):
+    """velocity volumes of the GPU's own tracks (ulm_track_velocity on the
+    records ulm_track wrote) equal the oracle's sums on the oracle's tracks"""
+    from paper_2511_21647_gb300 import _lib, rca
+    from synth import track_scene
+    g = tiny.geom
+    F = 64
+    sc = track_scene(g, F, n_bub, seed=seed)
+    rec = _gpu_list(sc.frame, sc.x, sc.y, sc.z)
+    prm = rca.make_track_params()
+    n = len(rec)
+    dev = torch.from_numpy(rec.view(np.int32).reshape(-1, 10).copy()).cuda()
+    n3d = torch.tensor([n], dtype=torch.int32, device="cuda")
+    cap = 1 << 14
+    out = torch.zeros((cap, _lib.TRACK.itemsize // 4), dtype=torch.int32, device="cuda")
+    nt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nx, ny, nz = rca.ulm_density_shape(S.t, prm.voxel_m)
+    dens = torch.zeros((nz, ny, nx), dtype=torch.int32, device="cuda")
+    rca.ulm_track(S.h, S.t, dev, n3d, n, F, prm, out, cap, nt, dens)
+    speed = torch.zeros((nz, ny, nx), dtype=torch.int64, device="cuda")
+    vz = torch.zeros_like(speed)
+    rca.ulm_track_velocity(S.h, S.t, out, nt, cap, prm, speed, vz)
+    torch.cuda.synchronize()
+    assert S.sync_status() == 0
+    _, tr_o, grid_o = O.track(g, _oracle_list(rec), oracle_prm(prm))
+    sp_o, vz_o = O.track_velocity(g, tr_o, oracle_prm(prm))
+    assert np.array_equal(dens.cpu().numpy().view(np.uint32), grid_o)
+    assert np.array_equal(speed.cpu().numpy(), sp_o) and np.array_equal(vz.cpu().numpy(), vz_o)
+    assert sp_o.sum() > 0 and (vz_o > 0).any() and (vz_o < 0).any()
+    # mean speed where counted: positive and within the scene's speeds (per frame at 400 Hz)
+    m = grid_o > 0
+    mean_mps = sp_o[m] / grid_o[m] * 1e-9 * 400.0
+    print(f"\nvelocity volumes: {int(m.sum())} voxels, mean speed {mean_mps.mean() * 1e3:.2f} mm/s")
+    assert mean_mps.min() > 0
+    with pytest.raises(rca.RcaError) as e:
+        bad = rca.make_track_params(voxel_m=0.0)
+        rca.ulm_track_velocity(S.h, S.t, out, nt, cap, bad, speed, vz)
+    assert e.value.status == _lib.RCA_ERR_INVALID_ARG
+
+
 def _chain(succ, i, n=10):
     out = []
     for _ in range(n - 1):
