@@ -439,13 +439,7 @@ def main():
             "vs_baseline": None,
             "dtype": "i16/f16/bf16+f32acc" if reduced else "f32",
             "data": "synthetic (seeded point scatterers; paper's in-vivo / Field II data unavailable)",
-            "config": {"workload": f"{w.name}: RCA {g.n_el}+{g.n_el} el, {nt} tx, {F} frames, {g.ns} samples, "
-                                   f"planes {g.nz}x{g.n_el}, P={g.P}, NCC d={w.ncc_d}",
-                       "frames": F, "n_el": g.n_el, "n_tx": nt, "ns": g.ns, "nz": g.nz, "us": g.us,
-                       "precision": args.precision,
-                       "l2": "inputs larger than L2 (RF %.2f GB, planes %.2f GB)" % (
-                           rf_dev.numel() * rf_dev.element_size() / 1e9, planes.numel() * planes.element_size() / 1e9),
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(w, F, args.precision, world),
             "stages": stage_roof,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -987,6 +981,20 @@ def cpu_next_rows(w, L, out3d, n3d, planes, slices, F):
     return out
 
 
+def workload_config(w, F, precision, world):
+    """the `config` object of the bench line, the same for both arms"""
+    g = w.geom
+    nt = g.n_tx
+    reduced = precision == "reduced"
+    rf_gb = F * nt * g.n_el * g.ns * (2 if reduced else 4) / 1e9
+    pl_gb = F * 4 * g.n_slab * g.nz * g.n_el * (4 if reduced else 8) / 1e9
+    return {"workload": f"{w.name}: RCA {g.n_el}+{g.n_el} el, {nt} tx, {F} frames, {g.ns} samples, "
+                        f"planes {g.nz}x{g.n_el}, P={g.P}, NCC d={w.ncc_d}",
+            "frames": F, "n_el": g.n_el, "n_tx": nt, "ns": g.ns, "nz": g.nz, "us": g.us, "precision": precision,
+            "l2": "inputs larger than L2 (RF %.2f GB, planes %.2f GB)" % (rf_gb, pl_gb),
+            "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args):
     """The FP64 CPU oracle timed on this host (the method has no other
     reference implementation); rank 0 only."""
@@ -1011,7 +1019,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": len(times), "warmup": args.warmup, "ms_per_step": round(F / value * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "frames": F},
+            "data": "synthetic", "config": workload_config(w, F, args.precision, args.gpus),
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
