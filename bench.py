@@ -271,13 +271,17 @@ def main():
     stage_ms = {s: sum(v) / K for s, v in per_stage.items()}
     n2d_v, n3d_v = int(n2d.item()), int(n3d.item())
 
+    fp32 = fp32_peak(R, h, dev, local)
+    direct = direct_form(R, L, sess, iq, iq_t, F, stream, stage_ms) if rank == 0 and not reduced else None
+
     # -- roofline of the dominant kernel -----------------------------------
     import json as _json
     peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_derived_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_peak_tflops = fp32["tflops"]
     esz_rf = 2 if reduced else 4
     esz_iq = 4 if reduced else 8
     esz_pl = 4 if reduced else 8
@@ -300,7 +304,9 @@ def main():
         ach = flops_stage1 / (stage_ms["stage1"] / 1e3) / 1e12
         roof = {"kernel": "k_stage1", "bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak_tflops, 1),
                 "unit": "TFLOP/s", "frac": round(ach / fp32_peak_tflops, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)",
+                "peak_source": "measured in this run: rca_fp32_probe (the library's FP32 FMA issue probe, "
+                               "best of scalar and packed, %.0f MHz median SM clock); derived 152 x 128 x 2 x "
+                               "sm_max_mhz = %.1f" % (fp32["sm_mhz"] or 0, fp32_derived_tflops),
                 "limiter": "shared-memory data path: each term reads two complex FP32 samples (16 B); "
                            "83 % of L1/shared throughput in profiles/kernels_paper_40frames_full.md"}
     else:
@@ -445,6 +451,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "forms": forms,
+            "fp32_peak": fp32,
+            "direct_projection": direct,
             "tracking": track,
             "separation": sep,
             "motion": motion,
@@ -461,6 +469,64 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def fp32_peak(R, h, dev, gpu_index, reps=25):
+    """The FP32 roofline denominator, measured: the library's FMA issue probe
+    (every SM full, 16 independent FMA chains per thread), scalar and packed
+    f32x2, each timed with CUDA events as the best of `reps` launches after
+    two warm-up launches, with the SM clock sampled meanwhile."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(8 * sms, device=dev)
+    iters = 1 << 17
+    res = {}
+    with ClockSampler(gpu_index) as clk:
+        for name, packed in (("scalar", 0), ("packed", 1)):
+            for _ in range(2):
+                flops = R.rca_fp32_probe(h, packed, iters, sink)
+            best = None
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                R.rca_fp32_probe(h, packed, iters, sink)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            res[name] = round(flops / (best / 1e3) / 1e12, 2)
+    c = clk.summary()
+    return {"tflops": max(res.values()), "scalar_tflops": res["scalar"], "packed_tflops": res["packed"],
+            "sm_mhz": c["sm_mhz"], "clock_reasons": c["reasons"],
+            "method": f"rca_fp32_probe: {sms} SMs x 8 CTAs x 256 threads x 16 FMA chains x {iters} steps, "
+                      f"best of {reps} launches (CUDA events)"}
+
+
+def direct_form(R, L, sess, iq, iq_t, F, stream, stage_ms, n=4):
+    """The work the two-stage method replaces (Sec. II-A1's conventional
+    beamforming, compared in Sec. III): the exact full-3D DAS projected per
+    plane pixel (RCA_MODE_DIRECT), timed on n frames of the ensemble's IQ and
+    scaled to the ensemble, next to the two-stage Stage 1 + Stage 2 time."""
+    import torch
+    from paper_2511_21647_gb300.pipeline import complex_buffer
+    h, t = sess.h, sess.t
+    pl = complex_buffer(sess.planes_shape(n), L.RCA_C32, iq.device)
+    R.rca_direct_project(h, t, iq[:n], iq_t, n, pl, L.RCA_C32)
+    times = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.rca_direct_project(h, t, iq[:n], iq_t, n, pl, L.RCA_C32)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times) * F / n
+    two = stage_ms["stage1"] + stage_ms["stage2"]
+    return {"frames_timed": n, "ms_per_ensemble": round(ms, 2), "two_stage_ms_per_ensemble": round(two, 3),
+            "direct_over_two_stage": round(ms / two, 1), "status": R.rca_sync_status(h),
+            "what": "exact full-3D DAS volume, slab-projected per plane pixel (k_direct), best of 3, scaled by frames"}
 
 
 def motion_step(R, L, sess, w, rf_dev, rf_t, scale, iq, iq_t, slices, F, stream, K):
@@ -504,9 +570,17 @@ def svd_step(R, sess, slices, F, stream, K, rank=16, iters=30):
     step.  Work: the 2K frame covariances (F^2 P / 2 complex products each),
     the eigenspace iteration, the projection (2 F rank P complex products)."""
     import torch
-    for _ in range(2):
-        R.rca_clutter_svd(sess.h, sess.t, slices, F, rank, iters)
+    # the first call reports how well the removed subspace is determined on
+    # the unfiltered slices (every later call filters the filtered slices)
+    info = torch.zeros((slices.shape[1], 4), dtype=torch.float32, device=slices.device)
+    R.rca_clutter_svd_info(sess.h, sess.t, slices, F, rank, iters, info)
+    R.rca_clutter_svd(sess.h, sess.t, slices, F, rank, iters)
     torch.cuda.synchronize()
+    inf = info.cpu().numpy()
+    report = {"gap_over_lambda1": [round(float((a[1] - a[2]) / a[0]), 9) for a in inf],
+              "invariance_residual": [round(float(a[3]), 5) for a in inf],
+              "note": "(theta_rank - theta_rank+1) / theta_1 near the FP32 covariance's rounding (~1e-7) "
+                      "leaves the vectors near the split undetermined (rca_clutter_svd_info)"}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(K):
@@ -518,7 +592,7 @@ def svd_step(R, sess, slices, F, stream, K, rank=16, iters=30):
     flops = nt * (F * F * P * 4.0 + 2 * F * rank * P * 8.0)
     return {"ms_per_ensemble": round(ms, 4), "rank": rank, "iterations": iters, "frames": F,
             "gflop": round(flops / 1e9, 1), "tflops": round(flops / (ms / 1e3) / 1e12, 2),
-            "kernels": 4, "status": R.rca_sync_status(sess.h)}
+            "kernels": 4, "split": report, "status": R.rca_sync_status(sess.h)}
 
 
 def separation_step(R, L, sess, w, planes, F, prm, cap2d, cap3d, stream, K, n_bands=3):
@@ -911,23 +985,45 @@ def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):
             "status": R.rca_sync_status(h)}
 
 
+def _oracle_step(O, w, rf, frames):
+    """one sample of the FP64 oracle's step: ensemble mean over all frames,
+    demodulation, Stage 1, Stage 2 + projection of the listed frames, then
+    XDoppler (window clipped at the sample's ends), NCC, peaks and pairing
+    of those frames; returns its wall time in seconds"""
+    g = w.geom
+    t0 = time.perf_counter()
+    planes = O.beamform_projections(g, rf, frames=frames)
+    O.localize(planes, w.ncc_d, 0.81, 1.45, 0.1, 0.5, g.P)
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(w, rf_tensor, n_frames):
-    """The FP64 oracle as it stands on the host cores: ensemble mean over all
-    frames, then demodulation, Stage 1, Stage 2 + projection for a sample of
-    frames, XDoppler + NCC + peaks + pairing for those frames."""
-    import numpy as np
+    """The FP64 oracle as it stands on the host cores, best of 3 after one
+    warm-up (time.perf_counter), once with every core and once with one
+    thread (a smaller sample, the same per-frame work)."""
     import oracle as O
     rf = rf_tensor.cpu().numpy()
-    g = w.geom
-    frames = list(range(1, 1 + n_frames))
-    t0 = time.time()
-    planes = O.beamform_projections(g, rf, frames=[0] + frames + [1 + n_frames])
-    O.localize(planes, w.ncc_d, 0.81, 1.45, 0.1, 0.5, g.P)
-    dt = time.time() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    nf = len(frames) + 2
-    return {"value": round(nf / dt, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nf} of {w.n_frames} frames of the same ensemble (mean over all {w.n_frames}), {dt:.1f} s"}
+    cores = os.cpu_count() or 1
+    res = {}
+    for label, nth, nfr in (("all_cores", cores, n_frames), ("one_thread", 1, 1)):
+        O.set_threads(nth)
+        frames = list(range(1, 1 + nfr))
+        _oracle_step(O, w, rf, frames)
+        best = min(_oracle_step(O, w, rf, frames) for _ in range(3))
+        res[label] = {"value": round(nfr / best, 3), "unit": "frames/s", "threads": nth,
+                      "sample": f"{nfr} of {w.n_frames} frames (mean over all {w.n_frames}), best of 3 after one "
+                                f"warm-up: {best:.2f} s"}
+    O.set_threads(cores)
+    a = res["all_cores"]
+    return {"value": a["value"], "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": a["sample"],
+            "one_thread": res["one_thread"],
+            "parallel_speedup": round(a["value"] / res["one_thread"]["value"], 2)}
+
+
+def _scaled(dt, scale, sample):
+    """one oracle timing of a bounded sample and its figure for one ensemble"""
+    return {"ms_per_ensemble": round(1e3 * dt * scale, 1), "measured_ms": round(1e3 * dt, 3),
+            "scale": round(float(scale), 6), "sample": sample}
 
 
 def cpu_next_rows(w, L, out3d, n3d, planes, slices, F):
@@ -949,34 +1045,32 @@ def cpu_next_rows(w, L, out3d, n3d, planes, slices, F):
     lst["frame"] = rec["frame"]
     for f in ("x", "y", "z"):
         lst[f] = rec[f].astype(np.float64)
-    t0 = time.time()
+    t0 = time.perf_counter()
     O.track(g, lst, O.track_params())
-    dt = time.time() - t0
-    out["tracking"] = {"ms_per_ensemble": round(1e3 * dt, 1), "sample": f"the whole 3D list ({n} localisations)"}
+    dt = time.perf_counter() - t0
+    out["tracking"] = _scaled(dt, 1.0, f"the whole 3D list ({n} localisations)")
     rng = np.random.default_rng(0)
     npx = planes.numel() // (2 * F)
     sel = rng.choice(npx, 4096, replace=False)
     a = planes.reshape(F, npx, 2)[:, sel].cpu().numpy().astype(np.float64)
     xs = a[..., 0] + 1j * a[..., 1]
-    t0 = time.time()
+    t0 = time.perf_counter()
     OSep.separate(xs, w.frame_rate, OSep.default_edges(w.frame_rate, 3))
-    dt = time.time() - t0
-    out["separation"] = {"ms_per_ensemble": round(1e3 * dt * npx / 4096, 1),
-                         "sample": f"4096 of {npx} plane pixels, {1e3 * dt:.0f} ms"}
+    dt = time.perf_counter() - t0
+    out["separation"] = _scaled(dt, npx / 4096, f"4096 of {npx} plane pixels ({F} frames each)")
     b = slices[:, 0:1].cpu().numpy().astype(np.float64)
     sl = b[..., 0] + 1j * b[..., 1]
-    t0 = time.time()
+    t0 = time.perf_counter()
     OS.filter_slices(sl, 16)
-    dt = time.time() - t0
+    dt = time.perf_counter() - t0
     nt = slices.shape[1]
-    out["clutter_svd"] = {"ms_per_ensemble": round(1e3 * dt * nt, 1),
-                          "sample": f"1 of {nt} transmissions (rank 16, eigendecomposition), {1e3 * dt:.0f} ms"}
+    out["clutter_svd"] = _scaled(dt, nt, f"1 of {nt} transmissions, {F} frames (rank 16, eigendecomposition)")
     c = slices[:4].cpu().numpy().astype(np.float64)
     sm = c[..., 0] + 1j * c[..., 1]
-    t0 = time.time()
+    t0 = time.perf_counter()
     OM.estimate(g, sm, frames=[1, 2, 3])
-    dt = time.time() - t0
-    out["motion"] = {"ms_per_ensemble": round(1e3 * dt * F / 3, 1), "sample": f"3 of {F} frames, {1e3 * dt:.0f} ms"}
+    dt = time.perf_counter() - t0
+    out["motion"] = _scaled(dt, F / 3, f"3 of {F} frames against frame 0")
     out["cores"] = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return out
 
@@ -997,32 +1091,41 @@ def workload_config(w, F, precision, world):
 
 def reference_arm(args):
     """The FP64 CPU oracle timed on this host (the method has no other
-    reference implementation); rank 0 only."""
+    reference implementation); rank 0 only.  Every warm-up and timed step is
+    one sample of the workload: the oracle's step on one frame of the
+    ensemble (its ensemble mean over all frames included), frames taken in
+    turn.  The line reports what ran; the per-ensemble figure that the
+    sample implies is under its own key."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import torch
+    import oracle as O
     from synth import generate, workload
     w = workload(args.workload)
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     G = generate(w, device=dev, dtype=torch.float32 if dev == "cuda" else torch.float64)
-    nfr = max(1, args.cpu_sample_frames // 2)
-    times = []
-    for _ in range(max(0, min(args.warmup, 1))):
-        cpu_baseline(w, G.rf, nfr)
-    res = None
-    for _ in range(max(1, min(args.steps, 3))):
-        res = cpu_baseline(w, G.rf, nfr)
-        times.append(res["value"])
-    value = statistics.median(times)
+    rf = G.rf.float().cpu().numpy()
+    del G
     F = w.n_frames
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": len(times), "warmup": args.warmup, "ms_per_step": round(F / value * 1e3, 1),
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    for i in range(args.warmup):
+        _oracle_step(O, w, rf, [1 + i % (F - 2)])
+    times = [_oracle_step(O, w, rf, [1 + (args.warmup + i) % (F - 2)]) for i in range(args.steps)]
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, F, args.precision, args.gpus),
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": res["cores"], "kind": "oracle",
-                             "sample": res["sample"]},
-            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "step_unit": "one frame of the ensemble through the oracle's step (mean over all frames, demodulation, "
+                         "Stage 1, Stage 2 + projection, XDoppler, NCC, peaks, pairing)",
+            "ms_per_ensemble_extrapolated": round(1e3 * F / value, 1),
+            "cpu_baseline": {"value": round(value, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps of one frame each after {args.warmup} warm-up "
+                                       f"steps, {total:.1f} s"},
+            "e2e": {"value": round(value, 3), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     emit(line, rank)
 
 

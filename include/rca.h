@@ -320,6 +320,9 @@ rca_status ulm_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* list2
  *   Set-up: the first call on a device looks up the array's device address
  *   with that device current, which can make the CUDA runtime load the
  *   library's device code; make that first call before any stream capture.
+ *   The address is kept for the life of the process: after cudaDeviceReset
+ *   (or a reset of the device's primary context) the kept address is stale,
+ *   so do not call this entry point again on that device in this process.
  *   Sharing: every handle and every call on a device uses the one array.
  *   Calls in order on one stream are fine (each call writes every scratch
  *   entry it reads, so nothing is cleared or carried over); calls whose work
@@ -351,9 +354,31 @@ rca_status ulm_localize(rca_handle* h, const rca_tables* t, const void* planes, 
  * gives no rank or threshold: `rank` is the caller's (0 leaves the slices
  * unchanged).  FP32 arithmetic throughout.
  *   Limits: rank in [0, 32] and below F; iterations in [1, 1000]
- *   (INVALID_ARG); F x (rank + 1) complex values twice must fit the
- *   eigenspace kernel's shared memory (F (rank + 1) <= 12 800, UNSUPPORTED). */
+ *   (INVALID_ARG); F x (rank + 2) complex values twice must fit the
+ *   eigenspace kernel's shared memory (F (rank + 2) <= 12 800, UNSUPPORTED). */
 rca_status rca_clutter_svd(rca_handle* h, const rca_tables* t, void* slices, int n_frames, int rank, int iterations);
+
+/* rca_clutter_svd plus a report of how well the removed subspace is
+ * determined (Sec. II-A2 removes the leading eigenvectors; whether FP32
+ * arithmetic resolves them depends on the spectrum).  The iteration carries
+ * one vector beyond the rank (when F allows); after the last step, with
+ * Q the removed basis and q' the extra vector, per transmission k:
+ *   info[4k + 0]  largest Rayleigh quotient q_j^H C_k q_j over the removed j
+ *   info[4k + 1]  smallest such quotient (the rank-th eigenvalue, when converged)
+ *   info[4k + 2]  q'^H C_k q' (the next eigenvalue, when converged; 0 if F
+ *                 leaves no room for the extra vector)
+ *   info[4k + 3]  ||C_k Q - Q (Q^H C_k Q)||_F / info[4k + 1]: zero for an
+ *                 exactly invariant subspace.
+ * The split between the removed and the kept subspace is determined by the
+ * FP32 covariance only where (info[1] - info[2]) / info[0] is well above
+ * the covariance's relative rounding (about 1e-7 here); where it is not,
+ * info[3] stays large for any iteration count and the removed subspace
+ * differs from the exact one among the eigenvectors near the split.
+ * info: caller-owned device array [2K][4] floats, written on the stream
+ * before the projection (zeros at rank 0).  Other arguments and errors as
+ * rca_clutter_svd; a null info is INVALID_ARG. */
+rca_status rca_clutter_svd_info(rca_handle* h, const rca_tables* t, void* slices, int n_frames, int rank,
+                                int iterations, float* info);
 
 /* ---------------------------------------------------------------------- */
 /* Microbubble separation on the projection planes (Sec. II-A5, Fig. 1c)   */
@@ -619,6 +644,23 @@ rca_status rca_batch_destroy(rca_batch* b);
  * Synchronises.  zt, dc, zp (optional) receive the chosen shapes. */
 rca_status rca_autotune(rca_handle* h, rca_tables* t, const void* iq, rca_dtype iq_dtype, int n_frames,
                         int* zt, int* dc, int* zp);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement aid (no counterpart in the paper)                           */
+/* ---------------------------------------------------------------------- */
+
+/* FP32 issue-rate probe: the denominator of an FP32 roofline, measured on
+ * this device rather than derived from a clock and a lane count.  Enqueues
+ * one launch that fills every SM (8 CTAs of 256 threads each), every thread
+ * running 16 independent chains of `iterations` dependent FP32 FMAs
+ * (packed = 0: scalar fma.rn.f32; packed = 1: eight chains of packed
+ * fma.rn.f32x2 pairs, the same 16 FMAs).  The caller times the launch on the
+ * handle's stream.  sink: caller-owned device buffer of at least
+ * 8 x (SM count) floats, written only by a chain whose result hits a value
+ * no chain reaches (it keeps the work live).  *flops (host, optional) gets
+ * 2 x 16 x iterations x threads, the launch's FP32 operations.
+ *   Errors: iterations outside [1, 1 << 24] or a null sink: INVALID_ARG. */
+rca_status rca_fp32_probe(rca_handle* h, int packed, int iterations, float* sink, double* flops);
 
 #ifdef __cplusplus
 }

@@ -109,6 +109,8 @@ def lib():
                 "or_track_grid": (None, [_P, _D, _P]),
                 "or_track_accumulate": (None, [_P, _I, _P, _P, _P]),
                 "or_track_velocity": (None, [_P, _I, _P, _P, _P, _P]),
+                "or_set_threads": (None, [_I]),
+                "or_max_threads": (_I, []),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -116,6 +118,16 @@ def lib():
                 fn.argtypes = args
             _lib = L
         return _lib
+
+
+def set_threads(n: int) -> None:
+    """OpenMP thread count of the C loops (the CPU baseline's 1-thread and
+    all-core timings)."""
+    lib().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
 
 
 def _ptr(a: np.ndarray):

@@ -8,6 +8,7 @@
 #include "rca_oracle.h"
 
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -851,3 +852,8 @@ void or_track_velocity(const or_geom* g, int ntr, const or_track* tr, const or_t
         }
     }
 }
+
+/* Thread count of the OpenMP loops above (timing of the CPU baseline with one
+ * thread and with all cores); no arithmetic. */
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int or_max_threads(void) { return omp_get_max_threads(); }

@@ -100,6 +100,10 @@ int or_localize2d(int F, int S, int nz, int N, const double* A, const double* M,
                   int cap, or_loc2d* out);
 int or_pair3d(int n2d, const or_loc2d* list, int P, int cap, or_loc3d* out);
 
+/* OpenMP thread count of the loops (timing only). */
+void or_set_threads(int n);
+int or_max_threads(void);
+
 /* fixed-length tracking and accumulation (Sec. II-A6, Fig. 1f) */
 typedef struct {
     int len;                  /* points per track (the paper: ten consecutive volumes) */

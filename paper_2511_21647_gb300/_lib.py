@@ -122,6 +122,7 @@ SIGNATURES = {
     "ulm_density_shape": (_S, [_P, C.c_double, _P]),
     "rca_motion_estimate": (_S, [_P, _P, _P, _I, _P, _P, _P]),
     "rca_clutter_svd": (_S, [_P, _P, _P, _I, _I, _I]),
+    "rca_clutter_svd_info": (_S, [_P, _P, _P, _I, _I, _I, _P]),
     "ulm_separate": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_sep_params), _P]),
     "ulm_separate_enhance": (_S, [_P, _P, _P, _I, _I, C.POINTER(ulm_sep_params), _I, _P, _P]),
     "ulm_track": (_S, [_P, _P, _P, _P, _I, _I, C.POINTER(ulm_track_params), _P, _I, _P, _P]),
@@ -145,6 +146,7 @@ SIGNATURES = {
     "rca_batch_set_wait_limit": (_S, [_P, C.c_longlong, _I]),
     "rca_batch_destroy": (_S, [_P]),
     "rca_autotune": (_S, [_P, _P, _P, _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "rca_fp32_probe": (_S, [_P, _I, _I, _P, C.POINTER(C.c_double)]),
 }
 
 _lock = threading.Lock()

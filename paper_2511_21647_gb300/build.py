@@ -32,6 +32,7 @@ UNITS = {
     "motion.cu": [],
     "svd.cu": [],
     "separate.cu": [],
+    "peak.cu": [],
 }
 
 

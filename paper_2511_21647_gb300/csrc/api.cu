@@ -456,7 +456,7 @@ extern "C" rca_status rca_beamform_projections(rca_handle* h, const rca_tables* 
     if (!slices) return st;
     if ((st = launch_stage1(h, t, iq, iq_t, F, slices)) != RCA_OK) return st;
     if (svd && (st = launch_clutter_svd(h, t, slices, F, prm->svd_rank,
-                                        prm->svd_iterations > 0 ? prm->svd_iterations : 30)) != RCA_OK)
+                                        prm->svd_iterations > 0 ? prm->svd_iterations : 30, nullptr)) != RCA_OK)
         return st;
     return launch_stage2(h, t, slices, F, planes, pt);
 }
@@ -533,7 +533,19 @@ extern "C" rca_status rca_clutter_svd(rca_handle* h, const rca_tables* t, void* 
     if (!slices) return set_error(h, RCA_ERR_INVALID_ARG, "null slices");
     if (F > 65535) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 65535 frames in one call");
     DeviceGuard dg(h->device);
-    return launch_clutter_svd(h, t, (float2*)slices, F, rank, iterations);
+    return launch_clutter_svd(h, t, (float2*)slices, F, rank, iterations, nullptr);
+}
+
+extern "C" rca_status rca_clutter_svd_info(rca_handle* h, const rca_tables* t, void* slices, int F, int rank,
+                                           int iterations, float* info)
+{
+    CHECK_HANDLE(h);
+    rca_status st = check_tables(h, t, F);
+    if (st != RCA_OK) return st;
+    if (!slices || !info) return set_error(h, RCA_ERR_INVALID_ARG, "null slices or info");
+    if (F > 65535) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 65535 frames in one call");
+    DeviceGuard dg(h->device);
+    return launch_clutter_svd(h, t, (float2*)slices, F, rank, iterations, info);
 }
 
 extern "C" rca_status rca_motion_estimate(rca_handle* h, const rca_tables* t, const void* slices, int F,
@@ -1090,4 +1102,14 @@ extern "C" rca_status rca_beamform_projections_batched(rca_handle* h, int n, con
     if (st != RCA_OK) return st;
     if (e != cudaSuccess) return cuda_check(h, e, "batched beamforming");
     return sd;
+}
+
+extern "C" rca_status rca_fp32_probe(rca_handle* h, int packed, int iterations, float* sink, double* flops)
+{
+    CHECK_HANDLE(h);
+    if (!sink) return set_error(h, RCA_ERR_INVALID_ARG, "null sink");
+    if (iterations < 1 || iterations > (1 << 24))
+        return set_error(h, RCA_ERR_INVALID_ARG, "iterations %d outside [1, 2^24]", iterations);
+    DeviceGuard dg(h->device);
+    return launch_fp32_probe(h, packed ? 1 : 0, iterations, sink, flops);
 }

@@ -631,8 +631,9 @@ __global__ void k_pair_match(const ulm_loc2d* __restrict__ L, const int* __restr
 __global__ void k_match_flags(const int* __restrict__ match, const int* __restrict__ n2d, int cap2d,
                               int* __restrict__ flags)
 {
+    // every slot the scan reads, max(cap2d, 1) of them, is written (0 past the list)
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= cap2d) return;
+    if (a >= max(cap2d, 1)) return;
     const int n = min(*n2d, cap2d);
     flags[a] = (a < n && match[a] >= 0) ? 1 : 0;
 }
@@ -810,7 +811,8 @@ rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L,
 // file.  Being a file-scope __device__ variable, the array exists once per
 // device, shared by every handle and call on it: calls whose work overlaps
 // on the GPU race on it.  Its address is looked up once per device, on the
-// first call made with that device current.
+// first call made with that device current, and kept for the life of the
+// process (a device reset makes the kept address stale; rca.h says so).
 //
 // Nothing in it needs clearing between calls: each call writes every entry
 // it reads (plane offsets for all planes, flags for all list slots, match

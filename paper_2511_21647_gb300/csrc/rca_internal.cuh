@@ -234,7 +234,8 @@ rca_status launch_ingest(rca_handle* h, const rca_tables* t, const void* rf, rca
 rca_status launch_stage1(rca_handle* h, const rca_tables* t, const void* iq, rca_dtype iq_t, int F,
                          float2* slices);
 void density_shape(const GeomDev& g, double voxel, int dims[3]);
-rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices, int F, int nc, int iters);
+rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices, int F, int nc, int iters,
+                              float* info);
 rca_status launch_separate(rca_handle* h, const rca_tables* t, const void* planes, rca_dtype pt, int F,
                            const ulm_sep_params* prm, int enh, float2* sub, float* A, float* M);
 rca_status launch_motion(rca_handle* h, const rca_tables* t, const float2* slices, int F, float* motion,
@@ -257,6 +258,7 @@ rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* ma
                              int F, float score_min, float alpha, ulm_loc2d* out, int cap, int* n2d);
 rca_status launch_pair3d(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d, int cap2d,
                          int F, ulm_loc3d* out, int cap3d, int* n3d);
+rca_status launch_fp32_probe(rca_handle* h, int packed, int iters, float* sink, double* flops);
 rca_status launch_pair3d_noalloc(rca_handle* h, const rca_tables* t, const ulm_loc2d* L, const int* n2d,
                                  int cap2d, int F, ulm_loc3d* out, int cap3d, int* n3d);
 

@@ -11,6 +11,13 @@
 //                  orthonormalisation (classical Gram-Schmidt applied twice) in
 //                  one CTA per transmission; the projection needs the subspace only
 //   k_svd_project  thread per pixel: t = X[p] Q, then X[p] -= t Q^H (in place)
+//   k_svd_info     (on request) Rayleigh quotients of the removed basis and of
+//                  one extra iterated vector, and the invariance residual
+//                  ||C Q - Q (Q^H C Q)||_F of the removed subspace
+// The iteration carries nc + 1 vectors (one beyond the rank, when F allows):
+// Gram-Schmidt keeps the first nc columns independent of the last, so the
+// removed subspace is that of an nc-vector iteration, and the extra column's
+// Rayleigh quotient estimates the first eigenvalue left in the data.
 #include <algorithm>
 #include <cmath>
 
@@ -44,7 +51,10 @@ __device__ __forceinline__ float2 sv_cmul(float2 a, float2 b) { return make_floa
 // writes Re + i (the difference) into part[k][split][a][b] (a in tile ta, b in
 // tile tb).
 // Every mbarrier wait is bounded; on a timeout the CTA records ST_TIMEOUT,
-// waits (bounded) for its MMAs in flight, frees TMEM and returns.
+// waits once more (bounded) for the commit of its MMAs in flight, frees TMEM
+// and returns.  If that second wait also runs out, MMAs may still be in
+// flight when TMEM is freed: nothing then guarantees the CTA's accumulators,
+// and the status word says the call failed.
 // ---------------------------------------------------------------------------
 #define SVT_M 128
 #define SVT_PC 16                           // pixels per chunk
@@ -264,6 +274,11 @@ __global__ void __launch_bounds__(SVT_THREADS, 1) k_svd_cov_tc(const float2* __r
     const bool fin = mbar_wait_bounded(&done, 0u);
     if (__syncthreads_or(!fin || abort_flag)) {
         if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        // one more bounded wait for the MMAs still in flight before the
+        // barriers are invalidated and TMEM is freed (the MMA thread commits
+        // `done` after its last issue even when it stopped early)
+        if (!fin) mbar_wait_bounded(&done, 0u);
+        __syncthreads();
     } else if (nch > 0 && warp < SVT_CONV / 32) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float2* dst = part + (((size_t)k * gridDim.z + split) * F) * F;
@@ -445,13 +460,13 @@ __global__ void __launch_bounds__(SV_THREADS) k_svd_cq(const float2* __restrict_
 // thread per pixel: t = sum_f X[p][f] Q[f][:], X[p][f] -= sum_j t_j conj(Q[f][j]);
 // frames in blocks of four, the block's loads issued before its arithmetic
 #define SV_FB 4
-__global__ void __launch_bounds__(128) k_svd_project(float2* __restrict__ sl, int F, int nt, int P, int nc,
+__global__ void __launch_bounds__(128) k_svd_project(float2* __restrict__ sl, int F, int nt, int P, int nc, int nb,
                                                      const float2* __restrict__ Qall)
 {
     extern __shared__ float2 ssv[];
     const int k = blockIdx.y;
-    const float2* Qk = Qall + (size_t)k * F * nc;
-    for (int idx = threadIdx.x; idx < F * nc; idx += blockDim.x) ssv[idx] = Qk[idx];
+    const float2* Qk = Qall + (size_t)k * F * nb;          // [F][nb]; the first nc columns are removed
+    for (int idx = threadIdx.x; idx < F * nc; idx += blockDim.x) ssv[idx] = Qk[(idx / nc) * nb + idx % nc];
     __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -500,21 +515,91 @@ __global__ void __launch_bounds__(128) k_svd_project(float2* __restrict__ sl, in
     }
 }
 
+// One CTA per transmission, after Y = C Q (nb columns): H = Q^H Y, the
+// Rayleigh quotients theta_j = Re H_jj, and the residual of the removed
+// subspace R = Y_nc - Q_nc H_nc (first nc columns).  info[k] = {max and min
+// theta_j over j < nc, theta_nc of the extra column (0 without one),
+// ||R||_F / min_j theta_j}.
+__global__ void __launch_bounds__(SV_THREADS) k_svd_info(const float2* __restrict__ Qg, const float2* __restrict__ Yg,
+                                                        int F, int nc, int nb, float* __restrict__ info)
+{
+    extern __shared__ float2 ssv[];
+    __shared__ float red[32];
+    __shared__ float2 H[33 * 33];
+    const int ld = nb + 1;
+    float2* Q = ssv;                                   // [F][ld]
+    float2* Y = ssv + (size_t)F * ld;                  // [F][ld]
+    const int k = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int idx = threadIdx.x; idx < F * nb; idx += blockDim.x) {
+        const int g = idx / nb, j = idx - g * nb;
+        Q[g * ld + j] = Qg[((size_t)k * F + g) * nb + j];
+        Y[g * ld + j] = Yg[((size_t)k * F + g) * nb + j];
+    }
+    __syncthreads();
+    for (int e = warp; e < nb * nb; e += nw) {
+        const int i = e / nb, j = e - i * nb;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int g = lane; g < F; g += 32) {
+            const float2 q = Q[g * ld + i], y = Y[g * ld + j];    // conj(q) y
+            acc.x += q.x * y.x + q.y * y.y;
+            acc.y += q.x * y.y - q.y * y.x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) H[i * nb + j] = acc;
+    }
+    __syncthreads();
+    float r2 = 0.f;
+    for (int idx = threadIdx.x; idx < F * nc; idx += blockDim.x) {
+        const int g = idx / nc, j = idx - g * nc;
+        float2 r = Y[g * ld + j];
+        for (int i = 0; i < nc; ++i) {
+            const float2 t = sv_cmul(Q[g * ld + i], H[i * nb + j]);
+            r.x -= t.x;
+            r.y -= t.y;
+        }
+        r2 += r.x * r.x + r.y * r.y;
+    }
+    r2 = sv_bsum(r2, red);
+    if (threadIdx.x == 0) {
+        float tmax = -INFINITY, tmin = INFINITY;
+        for (int j = 0; j < nc; ++j) {
+            tmax = fmaxf(tmax, H[j * nb + j].x);
+            tmin = fminf(tmin, H[j * nb + j].x);
+        }
+        info[4 * k + 0] = tmax;
+        info[4 * k + 1] = tmin;
+        info[4 * k + 2] = nb > nc ? H[nc * nb + nc].x : 0.f;
+        info[4 * k + 3] = tmin > 0.f ? sqrtf(r2) / tmin : INFINITY;
+    }
+}
+
 }  // namespace
 
-size_t svd_subspace_smem(int F, int nc) { return 2 * (size_t)F * (nc + 1) * sizeof(float2); }
+size_t svd_subspace_smem(int F, int nb) { return 2 * (size_t)F * (nb + 1) * sizeof(float2); }
 
-rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices, int F, int nc, int iters)
+rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices, int F, int nc, int iters,
+                              float* info)
 {
     const GeomDev& g = t->gd;
     const int nt = 2 * g.K, P = g.nzs * g.N;
     if (nc < 0 || nc > 32) return set_error(h, RCA_ERR_INVALID_ARG, "clutter rank %d outside [0, 32]", nc);
     if (nc >= F) return set_error(h, RCA_ERR_INVALID_ARG, "clutter rank %d must be below the frame count %d", nc, F);
     if (iters < 1 || iters > 1000) return set_error(h, RCA_ERR_INVALID_ARG, "iterations %d outside [1, 1000]", iters);
-    if (nc == 0) return RCA_OK;
-    const size_t smem_sub = svd_subspace_smem(F, nc);
+    if (nc == 0) {
+        if (info) {
+            cudaError_t e0 = cudaMemsetAsync(info, 0, (size_t)4 * nt * sizeof(float), h->stream);
+            if (e0 != cudaSuccess) return cuda_check(h, e0, "clutter info clear");
+        }
+        return RCA_OK;
+    }
+    const int nb = std::min(nc + 1, F);                 // iterated vectors: the rank plus one
+    const size_t smem_sub = svd_subspace_smem(F, nb);
     if (smem_sub > 200 * 1024)
-        return set_error(h, RCA_ERR_UNSUPPORTED, "frames x (rank + 1) = %d x %d exceeds the subspace kernel", F, nc + 1);
+        return set_error(h, RCA_ERR_UNSUPPORTED, "frames x (rank + 2) = %d x %d exceeds the subspace kernel", F, nb + 1);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -531,7 +616,7 @@ rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices
     const int psplit = ((P + nsplit - 1) / nsplit + SVT_PC - 1) / SVT_PC * SVT_PC;
     nsplit = (P + psplit - 1) / psplit;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t n_part = (size_t)nt * nsplit * F * F, n_C = (size_t)nt * F * F, n_Q = (size_t)nt * F * nc;
+    const size_t n_part = (size_t)nt * nsplit * F * F, n_C = (size_t)nt * F * F, n_Q = (size_t)nt * F * nb;
     const size_t bytes = up(n_part * 8) + up(n_C * 8) + 2 * up(n_Q * 8);
     rca_status st = RCA_OK;
     char* ws = (char*)ws_get(h, WS_SVD, bytes, &st);
@@ -548,18 +633,24 @@ rca_status launch_clutter_svd(rca_handle* h, const rca_tables* t, float2* slices
         part, F, nsplit, C);
     cudaError_t e = cudaFuncSetAttribute(k_svd_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub);
     if (e != cudaSuccess) return cuda_check(h, e, "subspace smem attribute");
-    const size_t smem_q = (size_t)F * nc * sizeof(float2);
+    const size_t smem_q = (size_t)F * nb * sizeof(float2);
     e = cudaFuncSetAttribute(k_svd_cq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
     if (e != cudaSuccess) return cuda_check(h, e, "subspace product smem attribute");
-    const int rows_cq = SV_THREADS / nc;
-    k_svd_orth<<<nt, SV_THREADS, smem_sub, h->stream>>>(Y, Q, F, nc, 1);
+    const int rows_cq = SV_THREADS / nb;
+    k_svd_orth<<<nt, SV_THREADS, smem_sub, h->stream>>>(Y, Q, F, nb, 1);
     for (int it = 0; it < iters; ++it) {
-        k_svd_cq<<<dim3((F + rows_cq - 1) / rows_cq, nt), SV_THREADS, smem_q, h->stream>>>(C, Q, F, nc, Y);
-        k_svd_orth<<<nt, SV_THREADS, smem_sub, h->stream>>>(Y, Q, F, nc, 0);
+        k_svd_cq<<<dim3((F + rows_cq - 1) / rows_cq, nt), SV_THREADS, smem_q, h->stream>>>(C, Q, F, nb, Y);
+        k_svd_orth<<<nt, SV_THREADS, smem_sub, h->stream>>>(Y, Q, F, nb, 0);
+    }
+    if (info) {
+        k_svd_cq<<<dim3((F + rows_cq - 1) / rows_cq, nt), SV_THREADS, smem_q, h->stream>>>(C, Q, F, nb, Y);
+        e = cudaFuncSetAttribute(k_svd_info, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sub);
+        if (e != cudaSuccess) return cuda_check(h, e, "clutter info smem attribute");
+        k_svd_info<<<nt, SV_THREADS, smem_sub, h->stream>>>(Q, Y, F, nc, nb, info);
     }
     const size_t smem_proj = (size_t)F * nc * sizeof(float2);
     e = cudaFuncSetAttribute(k_svd_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_proj);
     if (e != cudaSuccess) return cuda_check(h, e, "projection smem attribute");
-    k_svd_project<<<dim3((P + 127) / 128, nt), 128, smem_proj, h->stream>>>(slices, F, nt, P, nc, Q);
+    k_svd_project<<<dim3((P + 127) / 128, nt), 128, smem_proj, h->stream>>>(slices, F, nt, P, nc, nb, Q);
     return cuda_check(h, cudaGetLastError(), "clutter filter kernels");
 }

@@ -224,6 +224,11 @@ def rca_clutter_svd(h, t, slices, n_frames, rank, iterations=30):
     _check(L.load().rca_clutter_svd(h, t, _ptr(slices), n_frames, rank, iterations), h)
 
 
+def rca_clutter_svd_info(h, t, slices, n_frames, rank, iterations, info):
+    """info: device float tensor [2K][4] (see rca.h)"""
+    _check(L.load().rca_clutter_svd_info(h, t, _ptr(slices), n_frames, rank, iterations, _ptr(info)), h)
+
+
 def rca_motion_estimate(h, t, slices, n_frames, motion, shifts=None, peaks=None):
     _check(L.load().rca_motion_estimate(h, t, _ptr(slices), n_frames, _ptr(motion), _ptr(shifts), _ptr(peaks)), h)
 
@@ -305,6 +310,13 @@ def rca_autotune(h, t, iq, iq_dtype, n_frames):
     zt, dc, zp = C.c_int(0), C.c_int(0), C.c_int(0)
     _check(L.load().rca_autotune(h, t, _ptr(iq), iq_dtype, n_frames, C.byref(zt), C.byref(dc), C.byref(zp)), h)
     return zt.value, dc.value, zp.value
+
+
+def rca_fp32_probe(h, packed, iterations, sink):
+    """enqueue the FP32 issue-rate probe; returns the launch's FP32 operations"""
+    fl = C.c_double(0.0)
+    _check(L.load().rca_fp32_probe(h, int(packed), int(iterations), _ptr(sink), C.byref(fl)), h)
+    return fl.value
 
 
 def ulm_cnn_create(h, channels=32, max_pixels=1 << 22, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0):

@@ -120,30 +120,34 @@ def test_checkpoint_roundtrip(handle, net, tmp_path):
 
 
 def test_training_and_gain_over_ncc(handle):
-    """Short run (the bench trains longer): the loss falls, and on held-out
-    ensembles at 0.05 and 0.11 MB/mm^3 the CNN and NCC localisations are
-    scored against the ground truth (detection accuracy, missing rate,
-    RMSE).  The CNN must localise: RMSE under half a wavelength (99 um) and
-    within 1.5x the NCC path's, missing rate under 0.9; the comparison is
-    printed."""
+    """The learned form's gain: trained as the benchmark trains it (20 480
+    generated planes of 40 ensembles with 10-60 MBs, 2000 Adam steps), then
+    scored on held-out seeds at 0.053 and 0.107 MB/mm^3 (20 and 40 MBs in the
+    8 x 6.85 x 6.85 mm volume), against the ground truth, beside the NCC path
+    on the same planes (matching within 0.2 mm in 3D).  At both densities the
+    CNN must localise more accurately than NCC (lower RMSE) and with a higher
+    detection accuracy (matches / detections), and miss no more than NCC plus
+    0.05; the loss must fall below a fifth of its start."""
     from dataclasses import replace
     from paper_2511_21647_gb300 import learned, rca
     from synth import workload
     psf = json.load(open(os.path.join(HERE, "golden", "psf_sigma.json")))["tiny"]
     g = workload("tiny").geom
-    data = learned.build_dataset(g, learned.training_workloads(12, frames=64))
+    data = learned.build_dataset(g, learned.training_workloads(40, frames=64))
     c = rca.ulm_cnn_create(handle, max_pixels=1 << 21, seed=1)
     try:
-        hist = learned.train(c, data, steps=600, batch=64, log_every=100)
-        assert hist[-1][1] < 0.5 * hist[0][1], hist
+        hist = learned.train(c, data, steps=2000, batch=64, log_every=500)
+        assert hist[-1][1] < 0.2 * hist[0][1], hist
         prm = rca.make_ulm_params(d=5, sig_z=psf["sig_z"], sig_lat=psf["sig_lat"], alpha=0.1, ncc_min=0.5)
-        for n_mb, seed in ((20, 9100), (40, 9200)):
+        for n_mb, seed in ((20, 9100), (40, 9200), (20, 9300), (40, 9400)):
             w = replace(workload("tiny"), n_mb=n_mb, seed=seed)
             res = learned.evaluate(g, w, c, prm)
-            print(f"\nheld-out {res['density_per_mm3']} MB/mm^3: NCC {res['ncc']}  CNN {res['cnn']}")
-            assert res["status"] == 0
-            assert res["cnn"]["rmse_um"] is not None and res["cnn"]["rmse_um"] < 99
-            assert res["cnn"]["rmse_um"] < 1.5 * max(res["ncc"]["rmse_um"] or 0.0, 20.0)
-            assert res["cnn"]["missing_rate"] < 0.9
+            ncc, cnn = res["ncc"], res["cnn"]
+            print(f"\nheld-out seed {seed}, {res['density_per_mm3']} MB/mm^3: NCC {ncc}  CNN {cnn}")
+            assert res["status"] == 0 and res["density_per_mm3"] >= 0.05
+            assert ncc["rmse_um"] is not None and cnn["rmse_um"] is not None
+            assert cnn["rmse_um"] < ncc["rmse_um"], (seed, cnn["rmse_um"], ncc["rmse_um"])
+            assert cnn["detection_accuracy"] > ncc["detection_accuracy"], seed
+            assert cnn["missing_rate"] <= ncc["missing_rate"] + 0.05, seed
     finally:
         rca.ulm_cnn_destroy(c)

@@ -297,3 +297,39 @@ def test_paper_scale_localisation_on_oracle_frame(paper):
     assert [(int(r["i_xz"]), int(r["i_yz"])) for r in P3] == [(int(r["i_xz"]), int(r["i_yz"])) for r in P3_o]
     assert np.array_equal(P3["x"], P3_o["x"].astype(np.float32))
     assert np.array_equal(P3["y"], P3_o["y"].astype(np.float32))
+
+
+def test_paper_scale_localize_end_to_end_on_oracle_frames(paper):
+    """The public ulm_localize call at full size (300 frames, 16 slabs, d = 11)
+    on the oracle's planes of frames 149..151 in an otherwise empty ensemble:
+    its lists for frames 148..152 (every frame whose XDoppler window meets a
+    non-zero frame) against the oracle's localiser on the same five frames,
+    2D keys equal outside the near-tie pixels and 3D pairs equal outside the
+    excluded sub-block groups (tests/ulm_lists.py); no other frame detects."""
+    import ulm_lists as UL
+    from paper_2511_21647_gb300 import rca
+    from paper_2511_21647_gb300.pipeline import list2d_numpy, list3d_numpy
+    w, s, _, rf_h, _, _, _ = paper
+    g, F, f0 = w.geom, w.n_frames, 148
+    prm = dict(d=w.ncc_d, sig_z=0.81, sig_lat=1.45, alpha=0.1, ncc_min=0.5)
+    win = O.beamform_projections(g, rf_h, frames=(149, 150, 151)).astype(np.complex64)
+    five = np.zeros((5,) + win.shape[1:], dtype=np.complex64)
+    five[1:4] = win
+    A_o, M_o, L2_o, L3_o = O.localize(five.astype(np.complex128), prm["d"], prm["sig_z"], prm["sig_lat"],
+                                      prm["alpha"], prm["ncc_min"], g.P)
+    L2_o = L2_o.copy()
+    L3_o = L3_o.copy()
+    L2_o["frame"] += f0
+    L3_o["frame"] += f0
+    planes = torch.zeros(s.planes_shape(F) + (2,), device="cuda")
+    planes[f0:f0 + 5] = c_tensor(five)
+    out2d, n2d, out3d, n3d = s.localize(planes, rca.make_ulm_params(**prm), cap2d=1 << 18, cap3d=1 << 16)
+    assert s.sync_status() == 0
+    del planes
+    L2 = list2d_numpy(out2d, int(n2d.item()))
+    L3 = list3d_numpy(out3d, int(n3d.item()))
+    assert np.all((L2["frame"] >= f0) & (L2["frame"] < f0 + 5))
+    amb = UL.near_ties(A_o, M_o, prm, eps_ncc=3e-5, eps_amp=1e-5, frame_offset=f0)
+    st = UL.compare(L2_o, L3_o, L2, L3, amb, g.P, pos_tol=1e-3, ncc_tol=5e-5, amp_rtol=1e-5, tz=2e-3, tr=2e-5)
+    print(f"\nend to end (paper scale, frames 148-152): {st}")
+    assert st["n2d"] > 300 and st["n3d"] > 20

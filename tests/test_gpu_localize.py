@@ -98,29 +98,11 @@ def _key(L2):
     return [(int(r["frame"]), int(r["axis"]), int(r["slab"]), int(r["iz"]), int(r["ilat"])) for r in L2]
 
 
-def _near_ties(A32, M32, prm, eps=3e-5):
-    """pixels whose candidate decision is within eps of flipping (oracle NCC)"""
-    amb = set()
-    F, _, S_, nz, N = A32.shape
-    for t in range(F):
-        for axis in (0, 1):
-            for b in range(S_):
-                a = A32[t, axis, b].astype(np.float64)
-                n = O.ncc_plane(a, prm["d"], prm["sig_z"], prm["sig_lat"], float(M32[t]))
-                for i in range(1, nz - 1):
-                    for l in range(1, N - 1):
-                        c = n[i, l]
-                        if c < prm["ncc_min"] - eps:
-                            continue
-                        nb = n[i - 1:i + 2, l - 1:l + 2].copy()
-                        nb[1, 1] = -np.inf
-                        close = abs(c - prm["ncc_min"]) < eps or np.min(np.abs(nb - c)) < eps
-                        if close:
-                            amb.add((t, axis, b, i, l))
-    return amb
-
-
 def test_peaks_match_oracle_lists(S, oracle_A, prm_tiny):
+    """detection on the oracle's float32 amplitudes: keys equal outside the
+    oracle's near-tie pixels (3e-5 in NCC, 1e-6 M_t in amplitude: the same
+    float32 input on both sides), fields within the stated tolerances"""
+    import ulm_lists as UL
     A32, M32 = oracle_A
     L_o = O.localize2d(A32.astype(np.float64), M32.astype(np.float64), prm_tiny["d"], prm_tiny["sig_z"],
                        prm_tiny["sig_lat"], prm_tiny["alpha"], prm_tiny["ncc_min"])
@@ -132,18 +114,17 @@ def test_peaks_match_oracle_lists(S, oracle_A, prm_tiny):
     ko, kg = _key(L_o), _key(L_g)
     assert kg == sorted(kg), "GPU list not in (frame, axis, slab, iz, ilat) order"
     diff = set(ko) ^ set(kg)
-    if diff:
-        amb = _near_ties(A32, M32, prm_tiny)
-        assert diff <= amb, sorted(diff - amb)[:10]
-    common = sorted(set(ko) & set(kg))
+    amb = UL.near_ties(A32, M32, prm_tiny, eps_ncc=3e-5, eps_amp=1e-6)
+    assert diff <= amb, sorted(diff - amb)[:10]
+    print(f"\npeaks: {len(ko)} oracle entries, {len(diff)} differing, {len(amb)} near-tie pixels")
     io = {k: q for q, k in enumerate(ko)}
     ig = {k: q for q, k in enumerate(kg)}
-    for k in common:
+    for k in sorted(set(ko) & set(kg)):
         a, b = L_o[io[k]], L_g[ig[k]]
         assert abs(a["z"] - b["z"]) < 1e-3 and abs(a["lat"] - b["lat"]) < 1e-3
         assert abs(a["ncc"] - b["ncc"]) < 2e-5
         assert a["amp"] == b["amp"]          # A at the peak pixel, same float32 input
-    assert len(common) >= 0.99 * len(ko) and len(ko) > 20
+    assert len(ko) > 20
 
 
 def _to_gpu_list(L_o):
@@ -211,7 +192,13 @@ def test_pairing_hand_built_rules(S, tiny):
 
 def test_localize_end_to_end_on_oracle_planes(S, oracle_planes, prm_tiny, tiny):
     """The public ulm_localize call on the oracle's planes vs the oracle's
-    localiser on the same (complex64-rounded) planes."""
+    localiser on the same (complex64-rounded) planes: the 2D key lists equal
+    outside the oracle's near-tie pixels, the 3D pairs equal in every
+    sub-block group without a differing entry or a near-tie pairing decision
+    (tests/ulm_lists.py).  The GPU's amplitude is its own (FP32 XDoppler of
+    the planes, within 2e-6 of the oracle's), so the candidate margins are
+    3e-5 in NCC and 1e-5 M_t in amplitude."""
+    import ulm_lists as UL
     from paper_2511_21647_gb300.pipeline import list2d_numpy, list3d_numpy
     A_o, M_o, L2_o, L3_o = O.localize(oracle_planes.astype(np.complex128), prm_tiny["d"], prm_tiny["sig_z"],
                                       prm_tiny["sig_lat"], prm_tiny["alpha"], prm_tiny["ncc_min"], tiny.geom.P)
@@ -219,13 +206,10 @@ def test_localize_end_to_end_on_oracle_planes(S, oracle_planes, prm_tiny, tiny):
     assert S.sync_status() == 0
     L2 = list2d_numpy(out2d, int(n2d.item()))
     L3 = list3d_numpy(out3d, int(n3d.item()))
-    k2o, k2g = _key(L2_o), _key(L2)
-    same = len(set(k2o) & set(k2g))
-    assert same >= 0.98 * len(k2o), (same, len(k2o), len(k2g))
-    if k2o == k2g:
-        assert [(int(r["i_xz"]), int(r["i_yz"])) for r in L3] == [(int(r["i_xz"]), int(r["i_yz"])) for r in L3_o]
-    else:
-        assert abs(len(L3) - len(L3_o)) <= max(2, 0.05 * len(L3_o))
+    amb = UL.near_ties(A_o, M_o, prm_tiny, eps_ncc=3e-5, eps_amp=1e-5)
+    st = UL.compare(L2_o, L3_o, L2, L3, amb, tiny.geom.P, pos_tol=1e-3, ncc_tol=5e-5, amp_rtol=1e-5, tz=2e-3, tr=2e-5)
+    print(f"\nend to end (tiny): {st}")
+    assert st["n2d"] > 20 and st["n3d"] > 5
 
 
 def test_empty_input_gives_empty_lists(S, prm_tiny, tiny):

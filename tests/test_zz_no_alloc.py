@@ -98,3 +98,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lists):
     torch.cuda.synchronize()
     assert int(n3d.item()) == -7          # rejected before anything was enqueued
     assert s.sync_status() == 0
+
+
+def test_zero_capacity_after_a_full_call_gives_no_pairs(lists):
+    """cap2d = 0 with a non-zero count: no list entry may be read, so both
+    entry points report zero pairs, even right after a call that left a
+    matched first entry in the scratch."""
+    from paper_2511_21647_gb300 import rca
+    s, out2d, n2d, F = lists
+    cap2d = out2d.shape[0]
+    for fn in (rca.ulm_pair3d, rca.ulm_pair3d_noalloc):
+        _, n_full = _pair(fn, s, out2d, n2d, cap2d, F)
+        assert n_full > 0
+        _, n_zero = _pair(fn, s, out2d, n2d, 0, F)
+        assert n_zero == 0, fn.__name__
+        assert s.sync_status() == 0
