@@ -851,19 +851,42 @@ def batched_form(R, L, dev, stream, K):
         keep.append((geo, t))
     gen_s = time.time() - t_gen
     frames = sum(w.n_frames for w in ws)
-    b = R.rca_batch_create(h, items, L.RCA_F32, L.RCA_C32, L.RCA_C32, prm)
+    # launch shapes tuned per ensemble on its own IQ (Stage-1 row tile x
+    # distance chunk, Stage-2 plane-row tile), before the plan is built
+    t_tune = time.time()
+    shapes = {}
+    for w, it in zip(ws, items):
+        g = w.geom
+        iq = complex_buffer((w.n_frames, g.n_tx, g.ns, g.n_el), L.RCA_C32, dev)
+        R.rca_ingest(h, it["tables"], it["rf"], L.RCA_F32, None, w.n_frames, L.RCA_CLUTTER_MEAN, iq, L.RCA_C32)
+        shapes.setdefault(g.n_tx, set()).add(R.rca_autotune(h, it["tables"], iq, L.RCA_C32, w.n_frames))
+        del iq
+    tune_s = time.time() - t_tune
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    R.rca_batch_run(b, use_graph=True, h=h)
-    for _ in range(2):
-        R.rca_batch_run(b, use_graph=True, h=h)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(K):
-        R.rca_batch_run(b, use_graph=True, h=h)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / K
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    b = R.rca_batch_create(h, items, L.RCA_F32, L.RCA_C32, L.RCA_C32, prm)
+    ms_batch = timed(lambda: R.rca_batch_run(b, use_graph=True, h=h))
     st_batch = R.rca_sync_status(h)
+    R.rca_batch_destroy(b)
+    # the beamforming part alone: the persistent launch without the localisation branches
+    b = R.rca_batch_create(h, items, L.RCA_F32, L.RCA_C32, L.RCA_C32, None)
+    ms_batch_bf = timed(lambda: R.rca_batch_run(b, use_graph=True, h=h))
+
+    def seq_bf():
+        for it in items:
+            R.rca_beamform_projections(h, it["tables"], it["rf"], L.RCA_F32, None, it["n_frames"], R.bf_params(),
+                                       it["planes"], L.RCA_C32)
 
     def sequential():
         for it in items:
@@ -871,15 +894,8 @@ def batched_form(R, L, dev, stream, K):
                                        it["planes"], L.RCA_C32)
             R.ulm_localize(h, it["tables"], it["planes"], L.RCA_C32, it["n_frames"], prm, it["out2d"], it["cap2d"],
                            it["n2d"], it["out3d"], it["cap3d"], it["n3d"])
-    for _ in range(2):
-        sequential()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(K):
-        sequential()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1) / K
+    ms_seq = timed(sequential)
+    ms_seq_bf = timed(seq_bf)
     R.rca_batch_destroy(b)
     for geo, t in keep:
         R.rca_tables_destroy(t)
@@ -889,7 +905,11 @@ def batched_form(R, L, dev, stream, K):
             "ms_per_batch": round(ms_batch, 3), "value": round(frames / (ms_batch / 1e3), 1), "unit": "frames/s",
             "ms_per_300_frames": round(ms_batch * 300 / frames, 3),
             "sequential_ms_per_batch": round(ms_seq, 3), "speedup_vs_sequential": round(ms_seq / ms_batch, 3),
-            "graph": True, "status": st_batch, "generate_s": round(gen_s, 1)}
+            "beamform_only": {"ms_per_batch": round(ms_batch_bf, 3), "sequential_ms": round(ms_seq_bf, 3),
+                              "speedup_vs_sequential": round(ms_seq_bf / ms_batch_bf, 3)},
+            "tuned_shapes": {str(k): sorted(v) for k, v in sorted(shapes.items())},
+            "tuned_shapes_key": "n_tx: [(Stage-1 row tile, distance chunk, Stage-2 plane-row tile)]",
+            "tune_s": round(tune_s, 1), "graph": True, "status": st_batch, "generate_s": round(gen_s, 1)}
 
 
 def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):

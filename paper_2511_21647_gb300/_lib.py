@@ -10,6 +10,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librca.so")
+# RCA_LIBRARY=checked selects the bounds-checked build (see build.py)
+LIB_CHECKED_PATH = os.path.join(HERE, "_build", "librca_checked.so")
 
 RCA_MAX_K = 8
 ULM_PAIR3D_NOALLOC_MAX_2D = 1 << 19
@@ -153,11 +155,14 @@ _lock = threading.Lock()
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load librca.so and declare every entry point.  Raises if missing."""
+def load(path: str = None):
+    """Load librca.so (librca_checked.so when RCA_LIBRARY=checked) and declare
+    every entry point.  Raises if missing."""
     global _lib
     with _lock:
         if _lib is None:
+            if path is None:
+                path = LIB_CHECKED_PATH if os.environ.get("RCA_LIBRARY") == "checked" else LIB_PATH
             if not os.path.exists(path):
                 raise RuntimeError(f"librca not built ({path} missing); run `python -m paper_2511_21647_gb300.build`")
             L = C.CDLL(path)

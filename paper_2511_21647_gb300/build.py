@@ -2,6 +2,10 @@
 
 ``python -m paper_2511_21647_gb300.build`` compiles every translation unit
 under csrc/ with nvcc in parallel and links paper_2511_21647_gb300/_build/librca.so.
+``build(checked=True)`` links the checked variant _build/librca_checked.so
+(-DRCA_CHECKED: shared-memory ring slots, staged rows and queue indexes are
+bounds-checked and a violation sets RCA_ERR_BOUNDS in the status word); the
+binding loads it when RCA_LIBRARY=checked.
 """
 from __future__ import annotations
 
@@ -16,6 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librca.so")
+LIB_CHECKED = os.path.join(BUILD, "librca_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # translation units and their extra flags (the FP64 table and tracking
 # kernels keep every rounding as written: no fused multiply-add contraction)
@@ -53,24 +58,26 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-                     "-I", os.path.join(ROOT, "include"), *extra]
+                     "-I", os.path.join(ROOT, "include"), *(["-DRCA_CHECKED"] if checked else []), *extra]
 
     def compile_one(unit):
         src = os.path.join(CSRC, unit)
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(objdir, unit.replace(".cu", ".o"))
         cmd = [cc, "-c", src, "-o", obj, *common, *UNITS[unit]]
         if verbose:
             cmd += ["-Xptxas", "-v"]
@@ -85,14 +92,24 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if verbose:
         for _, err in results:
             sys.stderr.write(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", *ARCH, "-o", tmp, *[o for o, _ in results], "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> list:
+    """the release and the checked library, compiled concurrently"""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        futs = [ex.submit(build, force, False, (), c) for c in (False, True)]
+        return [f.result() for f in futs]
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    if "--checked" in sys.argv:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked=True))
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -244,7 +244,8 @@ extern "C" rca_status rca_geometry_destroy(rca_geometry* g)
 static void free_tables(rca_tables* t)
 {
     void* ptrs[] = {t->tx_f64, t->rx_f64, t->tx_q16, t->rx_q16, t->W, t->dmax, t->s2_shift, t->s2_sfl,
-                    t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin, t->s2_c2, t->dtx_q16, t->dtx_ph, t->mix,
+                    t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef, t->s2_tmin, t->s2_c2, t->s2_rot, t->s2_c2r,
+                    t->s2_coefr, t->s2_lw, t->dtx_q16, t->dtx_ph, t->mix,
                     t->s1.d_chunks, t->s1.d_rec32, t->s1.d_rec16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -340,7 +341,7 @@ extern "C" rca_status rca_reserve(rca_handle* h, const rca_geometry* g, int F)
     const GeomDev& gd = g->gd;
     const size_t nt = 2 * gd.K;
     rca_status st = RCA_OK;
-    const int nstrip = (gd.nz + DET_RS - 1) / DET_RS;
+    const int nstrip = (gd.nz + NCC_RS - 1) / NCC_RS;
     const size_t nslots = (size_t)F * 2 * gd.S * nstrip;
     struct {
         WsSlot s;
@@ -787,9 +788,9 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.mix = t->mix;
         E.sfl = t->s2_sfl;
         E.sfr = t->s2_sfr;
-        E.psi = t->s2_psi;
-        E.ec = t->s2_ec;
-        E.coef = t->s2_coef;
+        E.lw = t->s2_lw;
+        E.rot = t->s2_rot;
+        E.coef = t->s2_coefr;
         E.tmin = t->s2_tmin;
         E.T = t->T;
         E.zp = t->s2.zp;
@@ -797,7 +798,7 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         E.smin0 = t->s2.smin[0];
         E.smin1 = t->s2.smin[1];
         E.n_tiles2 = t->s2.n_tiles;
-        E.c2 = t->s2_c2;
+        E.c2 = t->s2_c2r;
         E.iA = t->s2_iA;
         E.iB = t->s2_iB;
         {

@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
         if (u >= total) break;
         const int4 SG = s_seg;
         const int stage = SG.x & 15, e = SG.x >> 4, loc = u - SG.y + SG.w;
+        // queue segment and ensemble of the unit (checked build)
+        if (!chk(SG.y <= u && loc >= 0 && e >= 0 && stage <= BS_STAGE2, status)) break;
         if (e != s_cur) {
             const int* src = reinterpret_cast<const int*>(ens + e);
             int* dst = reinterpret_cast<int*>(&sE);
@@ -99,7 +101,9 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
         }
         if (threadIdx.x == 0) {
             int ok = 1;
-            if (dep >= 0) {
+            // the counters the unit waits on and completes (checked build)
+            if (!chk(dep < n_counters && done < n_counters, status)) ok = 0;
+            if (ok && dep >= 0) {
                 const long long t0 = clock64();
                 while (ld_acquire(cnt + dep) < dep_target) {
                     if (*(volatile int*)abort_flag) {
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
             ok = stage1_body<TS, MAXR, false>(a0, a1, a2, smraw, bars, g, E.iq, E.rtab, E.rblk, E.dmax, E.chunks,
                                               E.zt, E.dc, E.n_tiles, E.nch, E.ring, E.slices, status);
         } else {
-            ok = stage2_body<TM, US>(a0, a1 >> 1, a1 & 1, a2, smraw, &bars[0], g, E.slices, E.sfl, E.sfr, E.psi, E.ec,
+            ok = stage2_body<TM, US>(a0, a1 >> 1, a1 & 1, a2, smraw, &bars[0], g, E.slices, E.sfl, E.sfr, E.lw, E.rot,
                                  E.coef, E.c2, E.tmin, E.T, E.iA, E.iB, E.zp, E.rows, E.smin0, E.smin1, E.planes, pt,
                                  status);
         }

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
 template <int TM, int US>
 __global__ void __launch_bounds__(S2_THREADS, 2) k_stage2(GeomDev g, const float2* __restrict__ slices,
                                                        const int* __restrict__ sfl, const float* __restrict__ sfr,
-                                                       const float2* __restrict__ psi, const float2* __restrict__ ec,
+                                                       const float4* __restrict__ lw, const float2* __restrict__ rot,
                                                        const float2* __restrict__ coef, const float2* __restrict__ c2,
                                                        const int* __restrict__ tmin, int T, int iA, int iB, int zp,
                                                        int rows, int smin0, int smin1, void* __restrict__ planes,
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(S2_THREADS, 2) k_stage2(GeomDev g, const float
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bar;
-    stage2_body<TM, US>(blockIdx.x, blockIdx.y, blockIdx.z & 1, blockIdx.z >> 1, smraw, &bar, g, slices, sfl, sfr, psi, ec,
+    stage2_body<TM, US>(blockIdx.x, blockIdx.y, blockIdx.z & 1, blockIdx.z >> 1, smraw, &bar, g, slices, sfl, sfr, lw, rot,
                     coef, c2, tmin, T, iA, iB, zp, rows, smin0, smin1, planes, pt, status);
 }
 
@@ -256,8 +256,8 @@ static rca_status stage2_launch(rca_handle* h, const rca_tables* t, const float2
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "stage2 smem attribute");
     dim3 grid(t->s2.n_tiles, (g.N + GW - 1) / GW, 2 * F);
-    kern<<<grid, S2_THREADS, smem, h->stream>>>(g, slices, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_coef,
-                                                t->s2_c2, t->s2_tmin, t->T, t->s2_iA, t->s2_iB, t->s2.zp, t->s2.rows,
+    kern<<<grid, S2_THREADS, smem, h->stream>>>(g, slices, t->s2_sfl, t->s2_sfr, t->s2_lw, t->s2_rot, t->s2_coefr,
+                                                t->s2_c2r, t->s2_tmin, t->T, t->s2_iA, t->s2_iB, t->s2.zp, t->s2.rows,
                                                 t->s2.smin[0], t->s2.smin[1], planes, (int)pt, h->d_status);
     return cuda_check(h, cudaGetLastError(), "stage2 kernel");
 }

@@ -388,12 +388,14 @@ __device__ __forceinline__ void s1_pixel(float (&A)[4], unsigned row, unsigned o
 template <typename TS, int MAXR, bool EXACT, bool PAIR, int XM, int YM>
 __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], float (&G)[MAXR][4], int d0, int d1, int cz, int zt,
                                              int l, int m, int Lx, int Ly, int row0, int nrow, unsigned rbase,
-                                             unsigned obase, unsigned wbase, int RS)
+                                             unsigned obase, unsigned wbase, int RS, int dc, unsigned rmax,
+                                             unsigned* __restrict__ status)
 {
     constexpr bool HALF = S1Rec<TS>::HALF;
     constexpr int RB = S1Rec<TS>::BYTES, ESZ = (int)sizeof(TS);
 #pragma unroll 1
     for (int d = d0; d < d1; ++d) {
+        if (!chk(d - cz >= 0 && d - cz < dc, status)) break;   // record block of the chunk
         const bool hx = XM == S1_FULL || (XM == S1_PRED && d <= Lx);
         const bool hy = YM == S1_FULL || (YM == S1_PRED && d <= Ly);
         // window offsets of the two mirror elements (records hold the row offset)
@@ -423,6 +425,8 @@ __device__ __forceinline__ void stage1_range(float (&H)[MAXR][4], float (&G)[MAX
                     // FP32-weight records hold offsets for 8-byte samples: halve for 4-byte ones
                     row = rowq[QUAD ? (j & 3) : 0] >> (ESZ == 4 ? 1 : 0);
                 }
+                // the two sample rows read lie inside the ring: row <= (ring - 1) RS
+                if (!chk(row <= rmax, status)) continue;
                 s1_pixel<TS, XM, YM>(H[j], row, ox, oy, RS, hx, hy, r0, r1, r2, r3);
                 if constexpr (PAIR) s1_pixel<TS, YM, XM>(G[j], row, mx, my, RS, hy, hx, r0, r1, r2, r3);
             }
@@ -492,6 +496,7 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
                 const int q = idx / v16, u = idx - q * v16, n = a + q;
                 if (n >= 0 && n < g.ns) continue;
                 const int sl = q < c1 ? sa + q : q - c1;
+                if (!chk(sl >= 0 && sl <= ring, status)) continue;
                 reinterpret_cast<uint4*>(rng + (size_t)sl * RS)[u] = make_uint4(0u, 0u, 0u, 0u);
                 if (sl == 0) reinterpret_cast<uint4*>(rng + (size_t)ring * RS)[u] = make_uint4(0u, 0u, 0u, 0u);
             }
@@ -503,6 +508,13 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
             const int lo2 = max(a + c1, 0), hi2 = max(lo2, min(a + cnt, g.ns));
             const int n0 = c1 < cnt ? a + c1 : (sa == 0 && cnt > 0 ? a : -1);
             const bool dup = n0 >= 0 && n0 < g.ns;
+            // both runs land inside slots [0, ring): the first from slot sa, the second from slot 0
+            if (!chk(sa >= 0 && (hi1 <= lo1 || sa + hi1 - a <= ring) && (hi2 <= lo2 || hi2 - (a + c1) <= ring) &&
+                         c >= 0 && c < nch, status)) {
+                // nothing is copied; the phase completes at once (results invalid, status set)
+                mbar_arrive_expect_tx(&bars[b], 0u);
+                return;
+            }
             const unsigned bytes = (unsigned)((hi1 - lo1) + (hi2 - lo2) + (dup ? 1 : 0)) * (unsigned)RS;
             mbar_arrive_expect_tx(&bars[b], bytes + (unsigned)rblk);
             if (hi1 > lo1)
@@ -558,7 +570,7 @@ __device__ __forceinline__ bool stage1_body(int tile, int k, int f, unsigned cha
             if (ye + 1 > d) nx = min(nx, ye + 1);
 #define RCA_S1_RANGE(XM, YM)                                                                                     \
     stage1_range<TS, MAXR, EXACT, PAIR, XM, YM>(H, G, d, nx, cc.z, zt, l, m, Lx, Ly, row0, nrow, rbase, obase, wbase, \
-                                                RS)
+                                                RS, dc, (unsigned)((ring - 1) * RS), status)
             switch (xm * 3 + ym) {
             case S1_FULL * 3 + S1_FULL: RCA_S1_RANGE(S1_FULL, S1_FULL); break;
             case S1_FULL * 3 + S1_PRED: RCA_S1_RANGE(S1_FULL, S1_PRED); break;
@@ -655,23 +667,26 @@ __device__ __forceinline__ uint64_t s2_join(uint64_t A1, uint64_t A2)
 template <int TT, int US, bool INTERIOR>
 __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, int ib, int lane, int gw, int fam,
                                               int f, int i0, int axT, const GeomDev& g, int T, int rows,
-                                              const uint64_t* __restrict__ sS64, const uint64_t* __restrict__ sEc64,
-                                              const uint64_t* __restrict__ sC2q, const int* __restrict__ sTb,
-                                              const float2* __restrict__ coef, void* __restrict__ planes, int pt,
-                                              int g0)
+                                              const uint64_t* __restrict__ sS64, const uint64_t* __restrict__ sC2q,
+                                              const int* __restrict__ sTb, const float2* __restrict__ coef,
+                                              void* __restrict__ planes, int pt, int g0, unsigned* __restrict__ status)
 {
     const int K = g.K, S = g.S, N = g.N;
     const int us = US > 0 ? US : g.us;
     constexpr int TMX = TT > 0 ? TT : 16;
     const int nT = TT > 0 ? TT : T;
-    uint64_t O1[S2_RH], O2[S2_RH];   // out = (O1.x - O2.y, O1.y + O2.x)
+    // the slices are carrier-rotated, so the taps carry each row's carrier:
+    // the sum over transmissions and taps accumulates straight into
+    // out = (O1.x - O2.y, O1.y + O2.x)
+    uint64_t O1[S2_RH], O2[S2_RH];
 #pragma unroll
     for (int q = 0; q < S2_RH; ++q) O1[q] = O2[q] = 0ull;
+    const int qlast = min(q0 + S2_RH, nrow) - 1;       // last plane row of the task read below
     for (int kk = 0; kk < K; ++kk) {
         const int tb = sTb[kk * S + b];
+        if (!chk(tb >= 0 && tb + us * qlast + nT - 1 < rows, status)) continue;   // staged window rows
         // this lane's column in transmission kk from the window row of plane row q0
         const uint64_t* col = sS64 + (size_t)(kk * rows + tb + us * q0) * 32 + lane;
-        const uint64_t* ep = sEc64 + 2 * (kk * S2_ZP + q0);
         const uint64_t* cp = sC2q + 2 * (size_t)(kk * S + b) * T;
         if constexpr (TT > 0 && US > 0 && INTERIOR) {
             uint64_t cx[TT], cy[TT], v[TT];
@@ -687,15 +702,11 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
 #pragma unroll
                     for (int t = 0; t < TT; ++t) v[t] = t + US < TT ? v[t + US] : col[(US * q + t) * 32];
                 }
-                uint64_t A1 = f2_mul(cx[0], v[0]), A2 = f2_mul(cy[0], v[0]);
 #pragma unroll
-                for (int t = 1; t < TT; ++t) {
-                    A1 = f2_fma(cx[t], v[t], A1);
-                    A2 = f2_fma(cy[t], v[t], A2);
+                for (int t = 0; t < TT; ++t) {
+                    O1[q] = f2_fma(cx[t], v[t], O1[q]);
+                    O2[q] = f2_fma(cy[t], v[t], O2[q]);
                 }
-                const uint64_t y = s2_join(A1, A2);
-                O1[q] = f2_fma(ep[2 * q], y, O1[q]);
-                O2[q] = f2_fma(ep[2 * q + 1], y, O2[q]);
             }
         } else {
             // taps read per use (a run-time tap count would hold up to 32 coefficient registers)
@@ -703,18 +714,14 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
             for (int q = 0; q < S2_RH; ++q) {
                 const int ii = q0 + q;
                 if (INTERIOR || (ii >= ia && ii < ib)) {
-                    uint64_t A1 = 0ull, A2 = 0ull;
 #pragma unroll
                     for (int t = 0; t < TMX; ++t) {
                         if (TT > 0 || t < nT) {
                             const uint64_t v = col[(us * q + t) * 32];
-                            A1 = f2_fma(cp[2 * t], v, A1);
-                            A2 = f2_fma(cp[2 * t + 1], v, A2);
+                            O1[q] = f2_fma(cp[2 * t], v, O1[q]);
+                            O2[q] = f2_fma(cp[2 * t + 1], v, O2[q]);
                         }
                     }
-                    const uint64_t y = s2_join(A1, A2);
-                    O1[q] = f2_fma(ep[2 * q], y, O1[q]);
-                    O2[q] = f2_fma(ep[2 * q + 1], y, O2[q]);
                 } else if (ii < nrow) {
                     // rows near the slice ends: exact per-row taps (carrier included)
                     const float2* cf = coef + (((size_t)(fam * K + kk) * S + b) * g.nz + i0 + ii) * T;
@@ -742,9 +749,9 @@ __device__ __forceinline__ void s2_transverse(int b, int q0, int nrow, int ia, i
 template <int US, bool INTERIOR>
 __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int ia, int ib, int fam, int f, int i0,
                                            int axL, int rlo, int grp, int SG, const GeomDev& g, int rows,
-                                           const uint64_t* __restrict__ sEc64, const float4* __restrict__ sLw,
-                                           const int* __restrict__ sSh, const uint64_t* __restrict__ sSum64,
-                                           const float* __restrict__ sfr, void* __restrict__ planes, int pt)
+                                           const float4* __restrict__ sLw, const int* __restrict__ sSh,
+                                           const uint64_t* __restrict__ sSum64, const float* __restrict__ sfr,
+                                           void* __restrict__ planes, int pt, unsigned* __restrict__ status)
 {
     const int K = g.K, S = g.S, N = g.N;
     const int us = US > 0 ? US : g.us;
@@ -752,13 +759,14 @@ __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int 
 #pragma unroll
     for (int q = 0; q < S2_RH; ++q) O1[q] = O2[q] = 0ull;
     for (int kk = 0; kk < K; ++kk) {
-        const float4 w = sLw[kk * N + u];            // a = psi (1 - fr), b = psi fr
+        const float4 w = sLw[kk * N + u];            // a, b: interpolation weights with the carrier folded in
         const uint64_t ax = f2_pack(w.x, w.x), ay = f2_pack(w.y, w.y);
         const uint64_t bx = f2_pack(w.z, w.z), by = f2_pack(w.w, w.w);
         const int sh = sSh[kk * N + u];
+        // the two slab-sum rows of the task's plane rows lie inside the window
+        if (!chk(sh >= 0 && sh + us * (min(q0 + S2_RH, nrow) - 1) + 1 < rows, status)) continue;
         const float fr = INTERIOR ? 0.f : __ldg(sfr + (size_t)(fam * K + kk) * N + u);
         const uint64_t* src = sSum64 + (size_t)(kk * SG + sb) * rows + sh + us * q0;
-        const uint64_t* ep = sEc64 + 2 * (kk * S2_ZP + q0);
 #pragma unroll
         for (int q = 0; q < S2_RH; ++q) {
             const int ii = q0 + q;
@@ -771,11 +779,8 @@ __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int 
             }
             if (valid) {
                 const uint64_t s0 = src[us * q], s1 = src[us * q + 1];
-                const uint64_t A1 = f2_fma(bx, s1, f2_mul(ax, s0));
-                const uint64_t A2 = f2_fma(by, s1, f2_mul(ay, s0));
-                const uint64_t y = s2_join(A1, A2);
-                O1[q] = f2_fma(ep[2 * q], y, O1[q]);
-                O2[q] = f2_fma(ep[2 * q + 1], y, O2[q]);
+                O1[q] = f2_fma(bx, s1, f2_fma(ax, s0, O1[q]));
+                O2[q] = f2_fma(by, s1, f2_fma(ay, s0, O2[q]));
             }
         }
     }
@@ -791,7 +796,7 @@ template <int TT, int US>
 __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, unsigned char* __restrict__ smraw,
                                             uint64_t* barp, const GeomDev& g, const float2* __restrict__ slices,
                                             const int* __restrict__ sfl, const float* __restrict__ sfr,
-                                            const float2* __restrict__ psi, const float2* __restrict__ ec,
+                                            const float4* __restrict__ lw, const float2* __restrict__ rot,
                                             const float2* __restrict__ coef, const float2* __restrict__ c2,
                                             const int* __restrict__ tmin, int T, int iA, int iB, int zp, int rows,
                                             int smin0, int smin1, void* __restrict__ planes, int pt,
@@ -810,8 +815,7 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
     const int smin = fam ? smin1 : smin0;
     const int rlo = us * i0 + smin;                    // slice row of window row 0
     float2* sS = reinterpret_cast<float2*>(smraw);                    // [K][rows][32]
-    float4* sEc = reinterpret_cast<float4*>(sS + (size_t)K * rows * 32);  // [K][S2_ZP] {x, x, y, y}
-    float4* sLw = sEc + (size_t)K * S2_ZP;                             // [K][N] {psi(1-fr), psi fr}
+    float4* sLw = reinterpret_cast<float4*>(sS + (size_t)K * rows * 32); // [K][N] {a, b}
     float4* sC2 = sLw + (size_t)K * N;                                 // [K][S][T] {x, x, y, y}
     float2* sSum = reinterpret_cast<float2*>(sC2 + (size_t)K * S * T); // [K][SG][rows]
     int* sSh = reinterpret_cast<int*>(sSum + (size_t)K * SG * rows);   // [K][N] floor shift - smin
@@ -848,27 +852,25 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
         }
     }
     // per-CTA tables while the copies are in flight
-    for (int idx = threadIdx.x; idx < K * S2_ZP; idx += blockDim.x) {
-        const int kk = idx / S2_ZP, ii = idx - kk * S2_ZP;
-        const float2 e = __ldg(ec + (size_t)(fam * K + kk) * g.nz + min(i0 + ii, g.nz - 1));
-        sEc[idx] = make_float4(e.x, e.x, e.y, e.y);
-    }
     for (int idx = threadIdx.x; idx < K * S * T; idx += blockDim.x) {
         const float2 c = __ldg(c2 + (size_t)fam * K * S * T + idx);
         sC2[idx] = make_float4(c.x, c.x, c.y, c.y);
     }
     for (int idx = threadIdx.x; idx < K * N; idx += blockDim.x) {
         const int k = fam * K + idx / N, u = idx % N;
-        const float2 ps = __ldg(psi + (size_t)k * N + u);
-        const float fr = __ldg(sfr + (size_t)k * N + u);
-        sLw[idx] = make_float4(ps.x * (1.0f - fr), ps.y * (1.0f - fr), ps.x * fr, ps.y * fr);
+        sLw[idx] = __ldg(lw + (size_t)k * N + u);
         sSh[idx] = __ldg(sfl + (size_t)k * N + u) - smin;
     }
     for (int idx = threadIdx.x; idx < K * S; idx += blockDim.x) sTb[idx] = __ldg(tmin + fam * K * S + idx) - smin;
     if (!cta_wait_copies(&bar, 0, status)) return false;
-    // slab sums of the group's slabs: one thread per (k, window row, slab); for
-    // a power-of-two P the pixels are visited in a row-rotated order so that
-    // the lanes of a warp (consecutive slabs, then rows) spread over the banks
+    // carrier rotation of the staged slice rows: w = v rot[k][r] (rows outside
+    // the slice and columns past the group are zero and stay zero)
+    // carrier rotation and slab sums of the group's slabs, one thread per
+    // (k, window row, slab): each staged value of the slab becomes w = v
+    // rot[k][r] in place (zero rows stay zero) and the rotated values are
+    // summed; for a power-of-two P the pixels are visited in a row-rotated
+    // order so that the lanes of a warp (consecutive slabs, then rows) spread
+    // over the banks
     {
         const int nsum = K * rows * sg;
         const unsigned magic = sg > 1 ? 0xffffffffu / (unsigned)sg + 1u : 0u;   // idx / sg for idx < 2^16
@@ -876,15 +878,20 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
         for (int idx = threadIdx.x; idx < nsum; idx += blockDim.x) {
             const int rk = sg == 1 ? idx : (int)__umulhi((unsigned)idx, magic);   // nsum == 0 when sg == 0
             const int sb = idx - rk * sg;
-            const float2* px = sS + (size_t)rk * 32 + sb * P;
-            uint64_t a = 0ull;
-            if (pow2) {
-                for (int j = 0; j < P; ++j) a = f2_add(a, reinterpret_cast<const uint64_t*>(px)[(j + rk) & (P - 1)]);
-            } else {
-                for (int j = 0; j < P; ++j) a = f2_add(a, reinterpret_cast<const uint64_t*>(px)[j]);
-            }
             const int kk = rk / rows, rr = rk - kk * rows;
-            reinterpret_cast<uint64_t*>(sSum)[((size_t)kk * SG + sb) * rows + rr] = a;
+            const int r = min(max(rlo + rr, 0), g.nzs - 1);      // rows outside the slice hold zeros
+            const float2 e = __ldg(rot + (size_t)(fam * K + kk) * g.nzs + r);
+            float2* px = sS + (size_t)rk * 32 + sb * P;
+            float2 a = make_float2(0.f, 0.f);
+            for (int j0 = 0; j0 < P; ++j0) {
+                const int j = pow2 ? (j0 + rk) & (P - 1) : j0;
+                const float2 v = px[j];
+                const float2 w = make_float2(fmaf(v.x, e.x, -v.y * e.y), fmaf(v.x, e.y, v.y * e.x));
+                px[j] = w;
+                a.x += w.x;
+                a.y += w.y;
+            }
+            sSum[((size_t)kk * SG + sb) * rows + rr] = a;
         }
     }
     __syncthreads();
@@ -899,29 +906,28 @@ __device__ __forceinline__ bool stage2_body(int tile, int grp, int fam, int f, u
     const int LU = (N + 31) >> 5;
     const int nTt = S * H, nTl = sg * LU * H;
     const uint64_t* sS64 = reinterpret_cast<const uint64_t*>(sS);
-    const uint64_t* sEc64 = reinterpret_cast<const uint64_t*>(sEc);
     const uint64_t* sC2q = reinterpret_cast<const uint64_t*>(sC2);
     const uint64_t* sSum64 = reinterpret_cast<const uint64_t*>(sSum);
     for (int task = warp; task < nTt + nTl; task += nwarp) {
         if (task < nTt) {
             const int b = H == 2 ? task >> 1 : task, q0 = H == 2 ? (task & 1) * S2_RH : 0;
             if (interior)
-                s2_transverse<TT, US, true>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sS64, sEc64,
-                                            sC2q, sTb, coef, planes, pt, g0);
+                s2_transverse<TT, US, true>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sS64, sC2q,
+                                            sTb, coef, planes, pt, g0, status);
             else
-                s2_transverse<TT, US, false>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sS64, sEc64,
-                                             sC2q, sTb, coef, planes, pt, g0);
+                s2_transverse<TT, US, false>(b, q0, nrow, ia, ib, lane, gw, fam, f, i0, axT, g, T, rows, sS64, sC2q,
+                                             sTb, coef, planes, pt, g0, status);
         } else {
             const int o = task - nTt;
             const int hq = H == 2 ? o & 1 : 0, rest = H == 2 ? o >> 1 : o;
             const int sb = rest / LU, u = (rest - sb * LU) * 32 + lane;
             if (u < N) {
                 if (interior)
-                    s2_lateral<US, true>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sEc64,
-                                         sLw, sSh, sSum64, sfr, planes, pt);
+                    s2_lateral<US, true>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sLw,
+                                         sSh, sSum64, sfr, planes, pt, status);
                 else
-                    s2_lateral<US, false>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows,
-                                          sEc64, sLw, sSh, sSum64, sfr, planes, pt);
+                    s2_lateral<US, false>(sb, u, hq * S2_RH, nrow, ia, ib, fam, f, i0, axL, rlo, grp, SG, g, rows, sLw,
+                                          sSh, sSum64, sfr, planes, pt, status);
             }
         }
     }

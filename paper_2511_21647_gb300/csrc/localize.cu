@@ -64,255 +64,342 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
 }
 
 // ---------------------------------------------------------------------------
-// NCC + regional peaks.  CTA = (row strip of DET_RS rows, plane).  NCC via
+// NCC + regional peaks.  CTA = (row strip of NCC_RS rows, plane).  NCC via
 // separable 1D correlations (Fig. 1g):
 //   s1 = box(A), s2 = box(A^2), sg = (g_z x g_l) * A,
 //   NCC = (sg - mu_G s1) / sqrt((s2 - s1^2 / d^2) * ss_G),
 // computed on the strip plus one row above and below for the 3x3 test.
 // Candidates are compacted in raster order into a fixed-capacity slot of
 // the strip; the true count is kept.
+//
+// Box sums by split points: for a run of B <= d consecutive outputs every
+// window contains the run's last first-row m, so
+//   box(r) = Suf(r) + Pre(r + d - 1),  Suf(r) = x_r + ... + x_{m-1},
+//   Pre(k) = x_m + ... + x_k,
+// about three adds per output instead of d, and every output is the sum of
+// two partial sums over its own window only (no running sum carries the
+// rounding of values that have left the window).  The Gaussian-weighted sums
+// keep their d taps.
+//
+// Vertical pass first, on column pairs (one 64-bit shared load gives two
+// columns of an input row; thread task = column pair x VB output rows); its
+// three sums are stored transposed into row pairs, so the horizontal pass
+// works on two output rows at once (thread task = row pair x HB output
+// columns).  Thread-to-data maps keep both passes free of bank conflicts:
+// consecutive lanes take consecutive column pairs in the vertical pass and
+// consecutive row pairs (row-pair stride of N + 1 pairs) in the horizontal
+// pass.
 // ---------------------------------------------------------------------------
-// Separable NCC on packed pairs.  Vertical pass first, on column pairs
-// (one 64-bit shared load gives two columns of an input row): per output row
-// the box sum, the box sum of squares and the g_z-weighted sum.  The sums are
-// stored transposed into row pairs, so the horizontal pass works on two
-// output rows at once (box sums and the g_l-weighted sum along the row).
-// Thread-to-data maps keep both passes free of bank conflicts: consecutive
-// lanes take consecutive column pairs in the vertical pass and consecutive
-// row pairs (row-pair stride of N + 1 pairs) in the horizontal pass.
-#define DET_RB 4    // output rows per thread in the vertical pass (one column pair)
-#define DET_CB 4    // output columns per thread in the horizontal pass (one row pair)
+#define NCC_THREADS 256
 
-template <int H>
-__global__ void __launch_bounds__(256, 3) k_detect(const float* __restrict__ A, const float* __restrict__ Mf, int S,
-                                                int nz, int N, NccConst nc, ulm_loc2d* __restrict__ cand,
-                                                int* __restrict__ cnt, float* __restrict__ ncc_out,
-                                                unsigned* __restrict__ status)
+// float2 columns of one padded vertical-sum row pair (see k_detect)
+__host__ __device__ inline int det_npad(int N, int H, int HB)
+{
+    const int w = (N + HB - 1) / HB * HB + 2 * H;
+    return w | 1;
+}
+__host__ __device__ inline int det_hb(int H) { return H >= 4 ? 8 : 2 * H; }
+
+// split-point box sums of NB consecutive outputs from the NB + 2H inputs
+// in[0 ..]: out[r] = in[r] + ... + in[r + 2H]  (NB <= 2H + 1)
+template <int H, int NB, typename LOAD>
+__device__ __forceinline__ void split_box(LOAD in, uint64_t (&out)[NB])
+{
+    static_assert(NB >= 1 && NB <= 2 * H + 1, "a run of outputs must share a split row");
+    constexpr int m = NB - 1;
+    uint64_t suf[NB];
+    if constexpr (m >= 1) {
+        suf[m - 1] = in(m - 1);
+#pragma unroll
+        for (int k = m - 2; k >= 0; --k) suf[k] = f2_add(in(k), suf[k + 1]);
+    }
+    uint64_t pre = in(m);
+#pragma unroll
+    for (int k = m + 1; k <= m + 2 * H; ++k) {
+        pre = f2_add(pre, in(k));
+        const int r = k - 2 * H;
+        if (r >= 0) out[r] = r < m ? f2_add(suf[r], pre) : pre;
+    }
+}
+
+template <int H, int NC>
+__global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restrict__ A, const float* __restrict__ Mf,
+                                                          int S, int nz, int Nrt, int nplanes, NccConst nc,
+                                                          ulm_loc2d* __restrict__ cand, int* __restrict__ cnt,
+                                                          float* __restrict__ ncc_out, unsigned* __restrict__ status)
 {
     constexpr int D = 2 * H + 1;
-    constexpr int RN = DET_RS + 2;          // NCC rows: the strip and one row above and below
+    constexpr int RN = NCC_RS + 2;          // NCC rows: the strip and one row above and below
     constexpr int RP = RN / 2;              // row pairs
-    static_assert(RN % DET_RB == 0 && DET_RB % 2 == 0, "row blocks must tile the NCC rows in pairs");
+    constexpr int VB = H >= 2 ? 4 : 2;      // output rows per vertical task
+    constexpr int HB = H >= 4 ? 8 : 2 * H;  // output columns per horizontal task (det_hb)
+    constexpr int NW = (NCC_RS * 256 + 31) / 32;   // bitmap words of the strip's pixels (N <= 256)
+    static_assert(RN % VB == 0 && VB % 2 == 0 && VB <= D, "vertical runs must tile the NCC rows in pairs");
+    const int N = NC > 0 ? NC : Nrt;        // lateral pixels (compile-time for the usual widths)
     extern __shared__ __align__(128) float sm[];
-    const int strip = blockIdx.x, plane = blockIdx.y;
-    const int nstrip = gridDim.x;
-    const int t = plane / (2 * S), axis = (plane / S) % 2, b = plane % S;
-    const int i0 = strip * DET_RS;
+    const int nstrip = (nz + NCC_RS - 1) / NCC_RS;
+    const int items = nplanes * nstrip;
     const int rin = RN + 2 * H;
-    const int VS = (N + 1) * 2;             // floats per row pair of a vertical-sum array
-    const int NS = N + 1;                   // NCC row stride (odd: conflict-light column writes)
-    float* sA = sm;                         // [rin][N] amplitude rows i0-1-H ...
-    float* sV = sA + max((size_t)rin * N, (size_t)RN * NS);  // [3][RP][N + 1][2] vertical sums (row pairs)
-    float* sN = sA;                         // [RN][NS] NCC, over the amplitude rows once the vertical pass is done
-    __shared__ int wsum[32];
+    // columns of a padded vertical-sum row pair: column c at c + H, zero pads on
+    // both sides, room for the last horizontal block's overhang, odd (conflict-free)
+    const int NPAD = det_npad(N, H, HB);
+    const int VS = 2 * NPAD;                // floats per row pair of a vertical-sum array
+    const int NS = N + 1;                   // NCC row stride
+    const size_t abuf = max((size_t)rin * N, (size_t)RN * NS);
+    // sm + bb abuf (bb = 0, 1): [rin][N] amplitude rows i0-1-H ..., double-buffered
+    float* sV = sm + 2 * abuf;              // [3][RP][NPAD][2]; column c at c + H
+    __shared__ unsigned bits[NW];           // candidate pixels of the strip, raster order
+    __shared__ int wsum[NCC_THREADS / 32];
     __shared__ int base_count;
-    __shared__ uint64_t bar;
-    const float* Ap = A + (size_t)plane * nz * N;
-    const float Mt = Mf[t];
+    __shared__ uint64_t bar[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
     {
-        // rows [i0-1-H, i0+DET_RS+1+H) of the plane: zero outside, one bulk copy inside
-        const int rlo = i0 - 1 - H;
-        const int lo = max(rlo, 0), hi = max(lo, min(rlo + rin, nz));
-        if (threadIdx.x == 0) {
-            mbar_init(&bar, 1);
-            mbar_fence_init();
+        const int npad = NPAD - N;          // H on the left, the rest on the right
+        for (int idx = threadIdx.x; idx < 3 * RP * npad; idx += blockDim.x) {
+            const int ar = idx / npad, q = idx - ar * npad;
+            const int col = q < H ? q : N + q;
+            reinterpret_cast<float2*>(sV)[(size_t)ar * NPAD + col] = make_float2(0.f, 0.f);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // rows [i0-1-H, i0+NCC_RS+1+H) of item `it`'s plane into buffer bb: zero
+    // outside the plane (all threads), one bulk copy inside (thread 0)
+    auto fetch = [&](int it, int bb) {
+        const int plane = it / nstrip, strip = it - plane * nstrip;
+        const int rlo = strip * NCC_RS - 1 - H;
+        const int lo = max(rlo, 0), hi = max(lo, min(rlo + rin, nz));
         const int z0 = min(lo - rlo, rin), z1 = hi - rlo;
+        float* sA = sm + bb * abuf;
         for (int idx = threadIdx.x; idx < z0 * N; idx += blockDim.x) sA[idx] = 0.f;
         for (int idx = threadIdx.x; idx < (rin - z1) * N; idx += blockDim.x) sA[(size_t)z1 * N + idx] = 0.f;
         if (threadIdx.x == 0) {
             fence_proxy_async();
             const unsigned bytes = (unsigned)((hi - lo) * N * sizeof(float));
-            mbar_arrive_expect_tx(&bar, bytes);
-            if (bytes) bulk_g2s(sA + (size_t)(lo - rlo) * N, Ap + (size_t)lo * N, bytes, &bar);
+            mbar_arrive_expect_tx(&bar[bb], bytes);
+            if (bytes)
+                bulk_g2s(sA + (size_t)(lo - rlo) * N, A + ((size_t)plane * nz + lo) * N, bytes, &bar[bb]);
         }
-        if (!cta_wait_copies(&bar, 0, status)) return;
+    };
+    // packed Gaussian taps, held for every item
+    uint64_t gz[D], gl[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        gz[q] = f2_pack(nc.gz[q], nc.gz[q]);
+        gl[q] = f2_pack(nc.gl[q], nc.gl[q]);
     }
-    // ---- vertical pass: thread = (column pair, DET_RB output rows)
-    {
-        uint64_t gz[D];
+    int it = blockIdx.x;
+    if (it < items) fetch(it, 0);
+    for (int k = 0; it < items; it += gridDim.x, ++k) {
+        const int bb = k & 1;
+        const int next = it + gridDim.x;
+        // the other buffer was released by the barrier that ended the previous item
+        if (next < items) fetch(next, bb ^ 1);
+        if (!cta_wait_copies(&bar[bb], (unsigned)(k >> 1) & 1u, status)) {
+            if (next < items) mbar_wait_bounded(&bar[bb ^ 1], (unsigned)((k + 1) >> 1) & 1u);
+            return;
+        }
+        float* sA = sm + bb * abuf;
+        float* sN = sA;                     // NCC rows over the amplitude rows once the vertical pass is done
+        const int plane = it / nstrip, strip = it - plane * nstrip;
+        const int t = plane / (2 * S), axis = (plane / S) % 2, b = plane % S;
+        const int i0 = strip * NCC_RS;
+        const float* Ap = A + (size_t)plane * nz * N;
+        const float Mt = Mf[t];
+        for (int idx = threadIdx.x; idx < NW; idx += blockDim.x) bits[idx] = 0u;
+        // ---- vertical pass: thread = (column pair, VB output rows)
+        {
+            const int NP = N / 2;
+            const unsigned sAa = smem_u32(sA), sVa = smem_u32(sV);
+            for (int task = threadIdx.x; task < NP * (RN / VB); task += blockDim.x) {
+                const int cp = task % NP, rb = task / NP;
+                const int ro0 = rb * VB;
+                // NCC rows ro0 .. ro0 + VB - 1 use amplitude rows ro0 .. ro0 + VB - 1 + 2H
+                uint64_t x[VB + 2 * H];
+                const unsigned src = sAa + (unsigned)((ro0 * N + 2 * cp) * 4);
 #pragma unroll
-        for (int q = 0; q < D; ++q) gz[q] = f2_pack(nc.gz[q], nc.gz[q]);
-        const int NP = N / 2;
-        const unsigned sAa = smem_u32(sA), sVa = smem_u32(sV);
-        for (int task = threadIdx.x; task < NP * (RN / DET_RB); task += blockDim.x) {
-            const int cp = task % NP, rb = task / NP;
-            const int ro0 = rb * DET_RB;
-            uint64_t v1[DET_RB], v2[DET_RB], vg[DET_RB];
+                for (int m = 0; m < VB + 2 * H; ++m) x[m] = lds_u64(src + (unsigned)(m * N * 4));
+                uint64_t v1[VB], v2[VB], vg[VB];
+                split_box<H, VB>([&](int q) { return x[q]; }, v1);
+                split_box<H, VB>([&](int q) { return f2_mul(x[q], x[q]); }, v2);
 #pragma unroll
-            for (int j = 0; j < DET_RB; ++j) v1[j] = v2[j] = vg[j] = 0ull;
-            const unsigned src = sAa + (unsigned)((ro0 * N + 2 * cp) * 4);
+                for (int r = 0; r < VB; ++r) {
+                    uint64_t a = f2_mul(gz[0], x[r]);
 #pragma unroll
-            for (int m = 0; m < DET_RB + 2 * H; ++m) {
-                const uint64_t x = lds_u64(src + (unsigned)(m * N * 4));
-                const uint64_t x2 = f2_mul(x, x);
+                    for (int q = 1; q < D; ++q) a = f2_fma(gz[q], x[r + q], a);
+                    vg[r] = a;
+                }
+                // transpose 2 x 2 blocks into row pairs: [arr][rp][H + column][row parity]
+                const unsigned dst0 = sVa + (unsigned)(((ro0 / 2) * VS + 2 * (2 * cp + H)) * 4);
 #pragma unroll
-                for (int j = 0; j < DET_RB; ++j) {
-                    const int q = m - j;
-                    if (q >= 0 && q < D) {
-                        v1[j] = f2_add(v1[j], x);
-                        v2[j] = f2_add(v2[j], x2);
-                        vg[j] = f2_fma(gz[q], x, vg[j]);
+                for (int j = 0; j < VB; j += 2) {
+                    const uint64_t* arrs[3] = {v1, v2, vg};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float2 r0 = f2_unpack(arrs[a][j]), r1 = f2_unpack(arrs[a][j + 1]);
+                        const unsigned dst = dst0 + (unsigned)(((a * RP + j / 2) * VS) * 4);
+                        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst), "f"(r0.x), "f"(r1.x) : "memory");
+                        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst + 8u), "f"(r0.y), "f"(r1.y) : "memory");
                     }
                 }
             }
-            // transpose 2 x 2 blocks into row pairs: [arr][rp][column][row parity]
-#pragma unroll
-            for (int j = 0; j < DET_RB; j += 2) {
-                const int rp = (ro0 + j) / 2;
-                const uint64_t* arrs[3] = {v1, v2, vg};
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float2 r0 = f2_unpack(arrs[a][j]), r1 = f2_unpack(arrs[a][j + 1]);
-                    // row-pair stride 2 (N + 1) floats keeps the horizontal pass conflict-free
-                    // but aligns pairs to 8 bytes only: two 64-bit stores
-                    const unsigned dst = sVa + (unsigned)(((a * RP + rp) * VS + 4 * cp) * 4);
-                    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst), "f"(r0.x), "f"(r1.x) : "memory");
-                    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst + 8u), "f"(r0.y), "f"(r1.y) : "memory");
-                }
-            }
         }
-    }
-    __syncthreads();
-    // ---- horizontal pass + NCC: thread = (row pair, DET_CB output columns);
-    // the amplitude rows are no longer read, so the NCC rows take their place
-    {
-        const float flat = nc.flat_coef * Mt * Mt;
-        const float inv_d2 = 1.0f / (float)(D * D);
-        const int ncb = (N + DET_CB - 1) / DET_CB;
-        uint64_t gl[D];
+        __syncthreads();
+        // ---- horizontal pass + NCC: thread = (row pair, HB output columns);
+        // the amplitude rows are no longer read, so the NCC rows take their place
+        {
+            const float flat = nc.flat_coef * Mt * Mt;
+            const float inv_d2 = 1.0f / (float)(D * D);
+            const int ncb = (N + HB - 1) / HB;
+            const uint64_t nid2 = f2_pack(-inv_d2, -inv_d2), nmu = f2_pack(-nc.muG, -nc.muG);
+            const unsigned sVa = smem_u32(sV);
+            for (int task = threadIdx.x; task < RP * ncb; task += blockDim.x) {
+                const int rp = task % RP, cb = task / RP;
+                const int c0 = cb * HB;
+                // padded input columns c0 - H .. c0 + HB - 1 + H start at pad index c0; past N they
+                // read the right pad (zero) or feed only outputs past N
+                const unsigned at = sVa + (unsigned)((rp * VS + 2 * c0) * 4);
+                uint64_t s1[HB], s2[HB], sg[HB];
+                {
+                    uint64_t a[HB + 2 * H];
 #pragma unroll
-        for (int q = 0; q < D; ++q) gl[q] = f2_pack(nc.gl[q], nc.gl[q]);
-        const uint64_t nid2 = f2_pack(-inv_d2, -inv_d2), nmu = f2_pack(-nc.muG, -nc.muG);
-        const unsigned sVa = smem_u32(sV);
-        for (int task = threadIdx.x; task < RP * ncb; task += blockDim.x) {
-            const int rp = task % RP, cb = task / RP;
-            const int c0 = cb * DET_CB;
-            uint64_t s1[DET_CB], s2[DET_CB], sg[DET_CB];
+                    for (int m = 0; m < HB + 2 * H; ++m) a[m] = lds_u64(at + (unsigned)(m * 8));
+                    split_box<H, HB>([&](int q) { return a[q]; }, s1);
 #pragma unroll
-            for (int j = 0; j < DET_CB; ++j) s1[j] = s2[j] = sg[j] = 0ull;
+                    for (int m = 0; m < HB + 2 * H; ++m) a[m] = lds_u64(at + (unsigned)(RP * VS * 4 + m * 8));
+                    split_box<H, HB>([&](int q) { return a[q]; }, s2);
 #pragma unroll
-            for (int m = 0; m < DET_CB + 2 * H; ++m) {
-                const int c = min(max(c0 - H + m, 0), N - 1);   // border outputs are zeroed below
-                const unsigned at = sVa + (unsigned)((rp * VS + 2 * c) * 4);
-                const uint64_t a1 = lds_u64(at), a2 = lds_u64(at + (unsigned)(RP * VS * 4)),
-                               ag = lds_u64(at + (unsigned)(2 * RP * VS * 4));
+                    for (int m = 0; m < HB + 2 * H; ++m) a[m] = lds_u64(at + (unsigned)(2 * RP * VS * 4 + m * 8));
 #pragma unroll
-                for (int j = 0; j < DET_CB; ++j) {
-                    const int q = m - j;
-                    if (q >= 0 && q < D) {
-                        s1[j] = f2_add(s1[j], a1);
-                        s2[j] = f2_add(s2[j], a2);
-                        sg[j] = f2_fma(gl[q], ag, sg[j]);
+                    for (int r = 0; r < HB; ++r) {
+                        uint64_t g = f2_mul(gl[0], a[r]);
+#pragma unroll
+                        for (int q = 1; q < D; ++q) g = f2_fma(gl[q], a[r + q], g);
+                        sg[r] = g;
+                    }
+                }
+                const int ia = i0 - 1 + 2 * rp;    // plane row of the pair's first row
+                const bool row0 = ia >= H && ia < nz - H && Mt > 0.f;
+                const bool row1 = ia + 1 >= H && ia + 1 < nz - H && Mt > 0.f;
+                float* nrow = sN + (2 * rp) * NS + c0;
+#pragma unroll
+                for (int j = 0; j < HB; ++j) {
+                    const int c = c0 + j;
+                    if (c >= N) break;
+                    // ssA = s2 - s1^2 / d^2, numerator = sg - mu_G s1 (both rows of the pair)
+                    const float2 ss = f2_unpack(f2_fma(f2_mul(s1[j], s1[j]), nid2, s2[j]));
+                    const float2 nu = f2_unpack(f2_fma(nmu, s1[j], sg[j]));
+                    const bool colok = c >= H && c < N - H;
+                    const float v0 = (colok && row0 && ss.x > flat) ? nu.x * nc.inv_ssG_sqrt * rsqrtf(ss.x) : 0.f;
+                    const float v1 = (colok && row1 && ss.y > flat) ? nu.y * nc.inv_ssG_sqrt * rsqrtf(ss.y) : 0.f;
+                    nrow[j] = v0;
+                    nrow[NS + j] = v1;
+                    if (ncc_out) {
+                        if (2 * rp >= 1 && 2 * rp <= NCC_RS && ia < nz) ncc_out[((size_t)plane * nz + ia) * N + c] = v0;
+                        if (2 * rp + 1 <= NCC_RS && ia + 1 < nz) ncc_out[((size_t)plane * nz + ia + 1) * N + c] = v1;
                     }
                 }
             }
-            const int ia = i0 - 1 + 2 * rp;    // plane row of the pair's first row
-#pragma unroll
-            for (int j = 0; j < DET_CB; ++j) {
-                const int c = c0 + j;
-                if (c >= N) continue;
-                // ssA = s2 - s1^2 / d^2, numerator = sg - mu_G s1 (both rows of the pair)
-                const float2 ss = f2_unpack(f2_fma(f2_mul(s1[j], s1[j]), nid2, s2[j]));
-                const float2 nu = f2_unpack(f2_fma(nmu, s1[j], sg[j]));
-                const bool colok = c >= H && c < N - H && Mt > 0.f;
-                float v[2] = {0.f, 0.f};
-                if (colok && ia >= H && ia < nz - H && ss.x > flat) v[0] = nu.x * nc.inv_ssG_sqrt * rsqrtf(ss.x);
-                if (colok && ia + 1 >= H && ia + 1 < nz - H && ss.y > flat)
-                    v[1] = nu.y * nc.inv_ssG_sqrt * rsqrtf(ss.y);
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const int ro = 2 * rp + pr;
-                    sN[ro * NS + c] = v[pr];
-                    if (ncc_out && ro >= 1 && ro <= DET_RS && ia + pr < nz)
-                        ncc_out[((size_t)plane * nz + ia + pr) * N + c] = v[pr];
-                }
-            }
         }
-    }
-    __syncthreads();
-    // ---- peaks: each thread tests a contiguous run of pixels (raster order) once,
-    // one block-wide exclusive scan of the per-thread counts places them
-    const float athr = nc.alpha * Mt;
-    ulm_loc2d* slot = cand + ((size_t)plane * nstrip + strip) * CAND_CAP;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int npx = DET_RS * N;
-    const int per = (npx + blockDim.x - 1) / blockDim.x;   // <= 32 for N <= 256
-    const int p0 = threadIdx.x * per, p1 = min(npx, p0 + per);
-    unsigned mask = 0u;
-    int mine = 0;
-    {
-        int ro = 1 + p0 / N, l = p0 - (ro - 1) * N;
-        for (int p = p0; p < p1; ++p) {
-            const int i = i0 - 1 + ro;
-            if (i >= 1 && i < nz - 1 && l >= 1 && l < N - 1) {
-                const float c = sN[ro * NS + l];
-                if (c >= nc.ncc_min && __ldg(Ap + (size_t)i * N + l) >= athr) {
+        __syncthreads();
+        // ---- peaks: test every strip pixel (thread = column, rows in steps), mark
+        // the candidates in a raster-order bitmap, then compact the bitmap words
+        // (consecutive words per thread, a block-wide exclusive scan of their
+        // counts) so the strip's candidates come out in raster order
+        const float athr = nc.alpha * Mt;
+        {
+            const int RG = NCC_THREADS / N > 0 ? NCC_THREADS / N : 1;   // row groups (N <= 256)
+            const int l = threadIdx.x % N, rg = threadIdx.x / N;
+            // NCC rows whose plane row i = i0 - 1 + ro lies in [1, nz - 2]
+            const int ro_lo = max(1, 2 - i0), ro_hi = min(NCC_RS, nz - 1 - i0);
+            if (rg < RG && l >= 1 && l < N - 1) {
+                int ro = ro_lo + rg;
+                const float* np_ = sN + ro * NS + l;
+                for (; ro <= ro_hi; ro += RG, np_ += RG * NS) {
+                    const float c = *np_;
+                    const int i = i0 - 1 + ro;
+                    if (!(c >= nc.ncc_min)) continue;
+                    if (!(__ldg(Ap + (size_t)i * N + l) >= athr)) continue;
                     bool pk = true;
 #pragma unroll
                     for (int a = -1; a <= 1; ++a)
 #pragma unroll
-                        for (int bb = -1; bb <= 1; ++bb) {
-                            if (a == 0 && bb == 0) continue;
-                            const float q = sN[(ro + a) * NS + l + bb];
-                            const bool earlier = (a < 0) || (a == 0 && bb < 0);
+                        for (int bq = -1; bq <= 1; ++bq) {
+                            if (a == 0 && bq == 0) continue;
+                            const float q = sN[(ro + a) * NS + l + bq];
+                            const bool earlier = (a < 0) || (a == 0 && bq < 0);
                             pk = pk && (earlier ? (c > q) : (c >= q));
                         }
                     if (pk) {
-                        mask |= 1u << (p - p0);
-                        ++mine;
+                        const int p = (ro - 1) * N + l;
+                        atomicOr(&bits[p >> 5], 1u << (p & 31));
                     }
                 }
             }
-            if (++l == N) {
-                l = 0;
-                ++ro;
+        }
+        __syncthreads();
+        ulm_loc2d* slot = cand + (size_t)it * CAND_CAP;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        // each thread compacts wpt consecutive bitmap words (wpt = 2 only when N > 273)
+        const int nwords = (NCC_RS * N + 31) / 32;
+        const int wpt = (nwords + NCC_THREADS - 1) / NCC_THREADS;
+        const int w0 = threadIdx.x * wpt;
+        unsigned long long mask = 0ull;
+        if (w0 < nwords) mask = bits[w0];
+        if (wpt == 2 && w0 + 1 < nwords) mask |= (unsigned long long)bits[w0 + 1] << 32;
+        const int mine = __popcll(mask);
+        int x = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        int before = x - mine;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        while (mask) {
+            const int bit = __ffsll(mask) - 1;
+            mask &= mask - 1;
+            if (before < CAND_CAP) {
+                const int p = w0 * 32 + bit;
+                const int ro = 1 + p / N, l = p - (ro - 1) * N, i = i0 - 1 + ro;
+                const float c = sN[ro * NS + l];
+                auto para = [](float fm, float f0, float fp) {
+                    const float den = fm - 2.f * f0 + fp;
+                    if (den >= 0.f) return 0.f;
+                    const float dl = (fm - fp) / (2.f * den);
+                    return fminf(0.5f, fmaxf(-0.5f, dl));
+                };
+                ulm_loc2d e;
+                e.frame = t;
+                e.axis = axis;
+                e.slab = b;
+                e.iz = i;
+                e.ilat = l;
+                e.z = (float)i + para(sN[(ro - 1) * NS + l], c, sN[(ro + 1) * NS + l]);
+                e.lat = (float)l + para(sN[ro * NS + l - 1], c, sN[ro * NS + l + 1]);
+                e.ncc = c;
+                e.amp = __ldg(Ap + (size_t)i * N + l);
+                e.reserved = 0;
+                slot[before] = e;
             }
+            ++before;
         }
-    }
-    int x = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    int before = x - mine;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    while (mask) {
-        const int bit = __ffs(mask) - 1;
-        mask &= mask - 1;
-        if (before < CAND_CAP) {
-            const int p = p0 + bit;
-            const int ro = 1 + p / N, l = p - (ro - 1) * N, i = i0 - 1 + ro;
-            const float c = sN[ro * NS + l];
-            auto para = [](float fm, float f0, float fp) {
-                const float den = fm - 2.f * f0 + fp;
-                if (den >= 0.f) return 0.f;
-                const float dl = (fm - fp) / (2.f * den);
-                return fminf(0.5f, fmaxf(-0.5f, dl));
-            };
-            ulm_loc2d e;
-            e.frame = t;
-            e.axis = axis;
-            e.slab = b;
-            e.iz = i;
-            e.ilat = l;
-            e.z = (float)i + para(sN[(ro - 1) * NS + l], c, sN[(ro + 1) * NS + l]);
-            e.lat = (float)l + para(sN[ro * NS + l - 1], c, sN[ro * NS + l + 1]);
-            e.ncc = c;
-            e.amp = __ldg(Ap + (size_t)i * N + l);
-            e.reserved = 0;
-            slot[before] = e;
+        if (threadIdx.x == blockDim.x - 1) base_count = before;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cnt[it] = base_count;
+            if (base_count > CAND_CAP) atomicOr(status, ST_CAPACITY);
         }
-        ++before;
+        // the next iteration fetches into this buffer and rewrites the bitmap
+        __syncthreads();
     }
-    if (threadIdx.x == blockDim.x - 1) base_count = before;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        cnt[(size_t)plane * nstrip + strip] = base_count;
-        if (base_count > CAND_CAP) atomicOr(status, ST_CAPACITY);
+        mbar_inval(&bar[0]);
+        mbar_inval(&bar[1]);
     }
 }
 
@@ -733,7 +820,7 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     nc.alpha = prm->alpha;
     nc.ncc_min = prm->ncc_min;
 
-    const int nstrip = (g.nz + DET_RS - 1) / DET_RS;
+    const int nstrip = (g.nz + NCC_RS - 1) / NCC_RS;
     const int nplanes = F * 2 * g.S;
     const int nslots = nplanes * nstrip;
     rca_status st = RCA_OK;
@@ -743,18 +830,32 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     if (!cnt) return st;
     int* off = (int*)ws_get(h, WS_SCAN, (size_t)(nslots + 1) * sizeof(int), &st);
     if (!off) return st;
-    const int rin = DET_RS + 2 + 2 * hh;
-    // amplitude rows (later the NCC rows, stride N + 1) + three vertical-sum arrays of row pairs
-    size_t smem = (std::max((size_t)rin * g.N, (size_t)(DET_RS + 2) * (g.N + 1)) +
-                   (size_t)3 * ((DET_RS + 2) / 2) * (g.N + 1) * 2) * sizeof(float);
-    dim3 grid(nstrip, nplanes);
+    if (g.N % 2 != 0 || g.N > 256) return set_error(h, RCA_ERR_UNSUPPORTED, "NCC detection needs an even N <= 256");
+    const int rin = NCC_RS + 2 + 2 * hh;
+    // two buffers of amplitude rows (later the NCC rows, stride N + 1) + three
+    // padded vertical-sum arrays of row pairs
+    size_t smem = (2 * std::max((size_t)rin * g.N, (size_t)(NCC_RS + 2) * (g.N + 1)) +
+                   (size_t)3 * ((NCC_RS + 2) / 2) * det_npad(g.N, hh, det_hb(hh)) * 2) * sizeof(float);
+    // persistent CTAs (two per SM, each walking (plane, strip) items with the
+    // next item's rows in flight), never more CTAs than items
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    dim3 grid((unsigned)std::max(1, std::min(nslots, 2 * sms)));
     cudaError_t e = cudaSuccess;
     switch (hh) {
+#define RCA_DETECT_LAUNCH(HV, NV)                                                                          \
+    do {                                                                                                   \
+        e = cudaFuncSetAttribute(k_detect<HV, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return cuda_check(h, e, "detect smem attribute");                          \
+        k_detect<HV, NV><<<grid, NCC_THREADS, smem, h->stream>>>(A, M, g.S, g.nz, g.N, nplanes, nc, cand, cnt, \
+                                                                 ncc_out, h->d_status);                   \
+    } while (0)
 #define RCA_DETECT_CASE(HV)                                                                                \
     case HV:                                                                                               \
-        e = cudaFuncSetAttribute(k_detect<HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-        if (e != cudaSuccess) return cuda_check(h, e, "detect smem attribute");                          \
-        k_detect<HV><<<grid, 256, smem, h->stream>>>(A, M, g.S, g.nz, g.N, nc, cand, cnt, ncc_out, h->d_status); \
+        if (g.N == 128) RCA_DETECT_LAUNCH(HV, 128);                                                        \
+        else if (g.N == 32) RCA_DETECT_LAUNCH(HV, 32);                                                     \
+        else RCA_DETECT_LAUNCH(HV, 0);                                                                     \
         break;
         RCA_DETECT_CASE(1)
         RCA_DETECT_CASE(2)
@@ -764,6 +865,7 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
         RCA_DETECT_CASE(6)
         RCA_DETECT_CASE(7)
 #undef RCA_DETECT_CASE
+#undef RCA_DETECT_LAUNCH
     default: return set_error(h, RCA_ERR_INVALID_ARG, "NCC kernel length out of range");
     }
     long long* part = (long long*)ws_get(h, WS_N2D, (size_t)2 * 1024 * sizeof(long long), &st);

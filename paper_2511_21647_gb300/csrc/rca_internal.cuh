@@ -129,6 +129,15 @@ struct rca_tables {
     // inside the slice)
     float2* s2_c2 = nullptr;    // [2K][S][T]
     int s2_iA = 0, s2_iB = -1;
+    // Stage 2 on carrier-rotated slices w_r = v_r rot[k][r] (rot: the carrier
+    // phase of tau_c at slice row r without its constant part; tau_c is
+    // linear in depth, so each output's carrier becomes a constant factor of
+    // the taps and no longer multiplies the output): the same taps and
+    // lateral weights times that factor
+    float2* s2_rot = nullptr;   // [2K][nzs] exp(j 2 pi fc (1 + cos th_k) z_r / c)
+    float2* s2_c2r = nullptr;   // [2K][S][T] c2 kappa_k exp(-j beta_k (tmin + t))
+    float2* s2_coefr = nullptr; // [2K][S][nz][T] coef conj(rot) at each tap's slice row
+    float4* s2_lw = nullptr;    // [2K][N] {a, b}: lateral interpolation weights with the carrier folded in
     // direct (conventional 3D) tables
     int* dtx_q16 = nullptr;     // [2K][N][nz] transmit delay at transverse u, plane depth
     float2* dtx_ph = nullptr;   // [2K][N][nz] exp(j 2 pi fc (tau_tx + z / c))
@@ -190,8 +199,7 @@ inline __host__ __device__ size_t s2_smem_bytes(int K, int S, int N, int P, int 
 {
     const int GW = s2_group_width(P), SG = GW > 0 ? GW / P : 1;
     return (size_t)K * rows * 32 * 8          // slice columns [K][rows][32]
-           + (size_t)K * S2_ZP * 16           // carrier pairs [K][ZP] {x, x, y, y}
-           + (size_t)K * N * 16               // lateral weights [K][N] {psi (1 - fr), psi fr}
+           + (size_t)K * N * 16               // lateral weights [K][N] {a, b}
            + (size_t)K * S * T * 16           // row-independent taps [K][S][T] {x, x, y, y}
            + (size_t)K * SG * rows * 8        // slab sums [K][SG][rows]
            + (size_t)K * N * 4 + (size_t)K * S * 4;  // shift rows [K][N], tap rows [K][S]
@@ -209,8 +217,9 @@ void plan_stage2(rca_tables* t, int zp);
 // helpers
 // ---------------------------------------------------------------------------
 #define RCA_MAX_NCC_D 15
-#define CAND_CAP 64       // 2D candidates per (plane, row strip)
-#define DET_RS 30         // rows per detect strip (the NCC rows, one above and below, pair up)
+#define CAND_CAP 96       // 2D candidates per (plane, row strip)
+#define DET_RS 30         // rows per strip of the heatmap peak search (ulm_detect_map)
+#define NCC_RS 30         // rows per strip of the NCC detection (+ one row above and below: 32 = 8 x 4)
 
 struct NccConst {
     int d, h;
@@ -329,6 +338,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Checked build (compiled with -DRCA_CHECKED, library librca_checked.so):
+// index checks on shared-memory ring slots, staged rows and queue indexes
+// that record ST_BOUNDS in the status word and skip the access instead of
+// trapping.  In the release build chk() is constant true and compiles away.
+#ifdef RCA_CHECKED
+#define RCA_CHECKED_BUILD 1
+#else
+#define RCA_CHECKED_BUILD 0
+#endif
+__device__ __forceinline__ bool chk(bool ok, unsigned* status)
+{
+    if constexpr (RCA_CHECKED_BUILD) {
+        if (!ok) atomicOr(status, ST_BOUNDS);
+        return ok;
+    }
+    return true;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase)
@@ -481,8 +508,8 @@ struct BatchEns {
     const float2* mix;
     const int* sfl;
     const float* sfr;
-    const float2* psi;
-    const float2* ec;
+    const float4* lw;           // Stage-2 tables for carrier-rotated slices (rca_tables::s2_lw, s2_rot,
+    const float2* rot;          // s2_coefr, s2_c2r)
     const float2* coef;
     const int* tmin;
     int T, zp, rows, smin0, smin1, n_tiles2;

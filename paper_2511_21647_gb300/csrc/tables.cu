@@ -90,7 +90,16 @@ __global__ void k_tables_das(GeomDev g, double* tx_f64, double* rx_f64, int* tx_
 }
 
 // Stage-2 per-(k, u) shift and carrier, per-(k, i) carrier.
-__global__ void k_tables_s2(GeomDev g, double* shift, int* sfl, float* sfr, float2* psi, float2* ec)
+// Stage-2 shift, lateral weights and carriers.  With rot[k][r] = exp(j 2 pi
+// fc (1 + cos th_k) z_r / c) at slice row r and kappa_k the constant carrier
+// phase exp(j 2 pi fc (L/2) |sin th_k| / c), the carrier of plane row i is
+// ec[k][i] = kappa_k rot[k][us i]; the lateral-slab weights of transverse
+// position u on the rotated slab sums (slice rows us i + sfl, us i + sfl + 1)
+// are a = (1 - fr) exp(j ph), b = fr exp(j (ph - beta_k)),
+// ph = 2 pi fc ((1 + cos th_k)(dz_k(u) - sfl dz / us) + (L/2)|sin th_k|) / c,
+// beta_k = 2 pi fc (1 + cos th_k)(dz / us) / c.
+__global__ void k_tables_s2(GeomDev g, double* shift, int* sfl, float* sfr, float2* psi, float2* ec, float2* rot,
+                            float4* lw)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     int nt = 2 * g.K;
@@ -100,21 +109,35 @@ __global__ void k_tables_s2(GeomDev g, double* shift, int* sfl, float* sfr, floa
         double sh = u * g.sin_th[k] / (1.0 + g.cos_th[k]);
         double s = sh * (double)g.us / g.dz;
         double fl = floor(s);
+        double fr = s - fl;
         shift[idx] = s;
         sfl[idx] = (int)fl;
-        sfr[idx] = (float)(s - fl);
+        sfr[idx] = (float)fr;
         psi[idx] = cis(TWO_PI_D * g.fc * ((1.0 + g.cos_th[k]) * sh / g.c));
+        double ph = TWO_PI_D * g.fc * ((1.0 + g.cos_th[k]) * (sh - fl * g.dz / (double)g.us) + 0.5 * g.L * fabs(g.sin_th[k])) / g.c;
+        double beta = TWO_PI_D * g.fc * (1.0 + g.cos_th[k]) * (g.dz / (double)g.us) / g.c;
+        double sa, ca, sb, cb;
+        sincos(ph, &sa, &ca);
+        sincos(ph - beta, &sb, &cb);
+        lw[idx] = make_float4((float)((1.0 - fr) * ca), (float)((1.0 - fr) * sa), (float)(fr * cb), (float)(fr * sb));
     }
     if (idx < nt * g.nz) {
         int k = idx / g.nz, i = idx % g.nz;
         ec[idx] = cis(TWO_PI_D * g.fc * tau_c(g, k, plane_z(g, i)));
+    }
+    if (idx < nt * g.nzs) {
+        int k = idx / g.nzs, r = idx % g.nzs;
+        rot[idx] = cis(TWO_PI_D * g.fc * (1.0 + g.cos_th[k]) * slice_z(g, r) / g.c);
     }
 }
 
 // Transverse-slab sum coefficients: for plane row i of slab b,
 //   sum_{u in slab} valid(zeta) exp(j 2 pi fc tau_c,k(z_i + dz_k(u))) lerp_weights(zeta)
 // gathered onto slice rows us*i + tmin[k][b] + t, t < T.
-__global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, int T, float2* coef,
+// coefr: the same taps for the carrier-rotated slices, each contribution at
+// slice row n times conj(rot[k][n]): the phase 2 pi fc ((1 + cos th_k)
+// (z_i + dz_k(u) - z_n) + (L/2)|sin th_k|) / c.
+__global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, int T, float2* coef, float2* coefr,
                               unsigned* status)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,8 +146,8 @@ __global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, i
     int i = idx % g.nz;
     int b = (idx / g.nz) % g.S;
     int k = idx / (g.nz * g.S);
-    double accr[16], acci[16];
-    for (int t = 0; t < T; ++t) accr[t] = acci[t] = 0.0;
+    double accr[16], acci[16], rotr[16], roti[16];
+    for (int t = 0; t < T; ++t) accr[t] = acci[t] = rotr[t] = roti[t] = 0.0;
     int base = g.us * i + tmin[k * g.S + b];
     for (int m = b * g.P; m < (b + 1) * g.P; ++m) {
         double s = shift[(size_t)k * g.N + m];
@@ -150,15 +173,35 @@ __global__ void k_tables_coef(GeomDev g, const double* shift, const int* tmin, i
             accr[t + 1] += fr * cs;
             acci[t + 1] += fr * sn;
         }
+        // rotated: z_i + dz_k(u) - z_n = (fr - j) dz / us at slice rows n0 + j
+        const double kap = 0.5 * g.L * fabs(g.sin_th[k]);
+        const double a1 = 1.0 + g.cos_th[k];
+        const double step = g.dz / (double)g.us;
+        double s0, c0;
+        sincos(TWO_PI_D * g.fc * (a1 * fr * step + kap) / g.c, &s0, &c0);
+        rotr[t] += (1.0 - fr) * c0;
+        roti[t] += (1.0 - fr) * s0;
+        if (fr > 0.0) {
+            double s1, c1;
+            sincos(TWO_PI_D * g.fc * (a1 * (fr - 1.0) * step + kap) / g.c, &s1, &c1);
+            rotr[t + 1] += fr * c1;
+            roti[t + 1] += fr * s1;
+        }
     }
-    for (int t = 0; t < T; ++t) coef[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
+    for (int t = 0; t < T; ++t) {
+        coef[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
+        coefr[(size_t)idx * T + t] = make_float2((float)rotr[t], (float)roti[t]);
+    }
 }
 
 // Row-independent transverse-slab taps: for slab b,
 //   c2[k][b][t] = sum_{u in slab} exp(j 2 pi fc (1 + cos th_k) dz_k(u) / c) lerp_weights,
 // so that coef[k][b][i][t] = ec[k][i] c2[k][b][t] wherever every shifted row
 // of the slab lies inside the slice (the carrier phase of tau_c is linear in z).
-__global__ void k_tables_coef2(GeomDev g, const double* shift, const int* tmin, int T, float2* c2, unsigned* status)
+// c2r = c2 kappa_k exp(-j beta_k (tmin + t)): the taps on the carrier-rotated
+// slices, ec[k][i] conj(rot[k][us i + tmin + t]) being independent of i.
+__global__ void k_tables_coef2(GeomDev g, const double* shift, const int* tmin, int T, float2* c2, float2* c2r,
+                               unsigned* status)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     int nt = 2 * g.K;
@@ -185,7 +228,14 @@ __global__ void k_tables_coef2(GeomDev g, const double* shift, const int* tmin, 
             acci[t + 1] += fr * sn;
         }
     }
-    for (int t = 0; t < T; ++t) c2[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
+    const double kap = TWO_PI_D * g.fc * 0.5 * g.L * fabs(g.sin_th[k]) / g.c;
+    const double beta = TWO_PI_D * g.fc * (1.0 + g.cos_th[k]) * (g.dz / (double)g.us) / g.c;
+    for (int t = 0; t < T; ++t) {
+        c2[(size_t)idx * T + t] = make_float2((float)accr[t], (float)acci[t]);
+        double sn, cs;
+        sincos(kap - beta * (double)(tmin[idx] + t), &sn, &cs);
+        c2r[(size_t)idx * T + t] = make_float2((float)(accr[t] * cs - acci[t] * sn), (float)(accr[t] * sn + acci[t] * cs));
+    }
 }
 
 // Conventional-DAS transmit tables at every transverse position and plane row.
@@ -260,6 +310,8 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     t->s2_sfr = dalloc<float>(h, (size_t)nt * g.N, &st);
     t->s2_psi = dalloc<float2>(h, (size_t)nt * g.N, &st);
     t->s2_ec = dalloc<float2>(h, (size_t)nt * g.nz, &st);
+    t->s2_rot = dalloc<float2>(h, (size_t)nt * g.nzs, &st);
+    t->s2_lw = dalloc<float4>(h, (size_t)nt * g.N, &st);
     t->s2_tmin = dalloc<int>(h, (size_t)nt * g.S, &st);
     t->dtx_q16 = dalloc<int>(h, (size_t)nt * g.N * g.nz, &st);
     t->dtx_ph = dalloc<float2>(h, (size_t)nt * g.N * g.nz, &st);
@@ -271,8 +323,9 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
     const int B = 256;
     k_tables_das<<<(g.nzs * g.N + B - 1) / B, B, 0, s>>>(g, t->tx_f64, t->rx_f64, t->tx_q16, t->rx_q16, t->W,
                                                           t->dmax);
-    int n2 = std::max(nt * g.N, nt * g.nz);
-    k_tables_s2<<<(n2 + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec);
+    int n2 = std::max({nt * g.N, nt * g.nz, nt * g.nzs});
+    k_tables_s2<<<(n2 + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_sfl, t->s2_sfr, t->s2_psi, t->s2_ec, t->s2_rot,
+                                               t->s2_lw);
     k_tables_direct<<<(nt * g.N * g.nz + B - 1) / B, B, 0, s>>>(g, t->dtx_q16, t->dtx_ph);
     k_tables_mix<<<(g.ns + B - 1) / B, B, 0, s>>>(g, t->mix);
     if ((st = cuda_check(h, cudaGetLastError(), "table kernels")) != RCA_OK) return st;
@@ -313,14 +366,17 @@ rca_status launch_tables(rca_handle* h, rca_tables* t)
         t->s2.smax[fam] = hi + 1;
     }
     t->s2_coef = dalloc<float2>(h, (size_t)nt * g.S * g.nz * T, &st);
+    t->s2_coefr = dalloc<float2>(h, (size_t)nt * g.S * g.nz * T, &st);
     if (st != RCA_OK) return st;
     cudaMemcpyAsync(t->s2_tmin, tmin.data(), tmin.size() * 4, cudaMemcpyHostToDevice, s);
     k_tables_coef<<<(nt * g.S * g.nz + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_tmin, T, t->s2_coef,
-                                                                 h->d_status);
+                                                                 t->s2_coefr, h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "coef kernel")) != RCA_OK) return st;
     t->s2_c2 = dalloc<float2>(h, (size_t)nt * g.S * T, &st);
+    t->s2_c2r = dalloc<float2>(h, (size_t)nt * g.S * T, &st);
     if (st != RCA_OK) return st;
-    k_tables_coef2<<<(nt * g.S + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_tmin, T, t->s2_c2, h->d_status);
+    k_tables_coef2<<<(nt * g.S + B - 1) / B, B, 0, s>>>(g, t->s2_shift, t->s2_tmin, T, t->s2_c2, t->s2_c2r,
+                                                          h->d_status);
     if ((st = cuda_check(h, cudaGetLastError(), "coef2 kernel")) != RCA_OK) return st;
     // plane rows whose shifted slice rows (floor(shift) .. floor(shift) + 1
     // around us * i) all lie inside [0, nzs - 1]

@@ -258,8 +258,17 @@ def test_paper_scale_localisation_on_oracle_frame(paper):
     M_in = torch.zeros(F, device="cuda")
     M_in[f] = float(M32)
     p = rca.make_ulm_params(**prm)
-    out, n2d, _ = s.detect2d(A_in, M_in, p, cap2d=1 << 16)
+    out, n2d, ncc = s.detect2d(A_in, M_in, p, cap2d=1 << 16, want_ncc=True)
     assert s.sync_status() == 0
+    # the separable NCC with the paper's 11-tap kernels against the oracle's brute 2D form
+    ncc_f = ncc[f].cpu().numpy()
+    del ncc
+    worst = 0.0
+    for ax in range(2):
+        for sb in (0, 7, 15):
+            ref = O.ncc_plane(A32[ax, sb].astype(np.float64), prm["d"], prm["sig_z"], prm["sig_lat"], float(M32))
+            worst = max(worst, float(np.max(np.abs(ncc_f[ax, sb] - ref))))
+    assert worst < 2e-5, worst
     L_g = list2d_numpy(out, int(n2d.item()))
     assert np.all(L_g["frame"] == f)
     L_o = O.localize2d(A32[None].astype(np.float64), np.array([float(M32)]), prm["d"], prm["sig_z"],
