@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=0, help="override the ensemble length (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision / batched / learned forms")
     ap.add_argument("--no-next-rows", action="store_true", help="skip tracking, separation, motion estimation and the SVD filter")
+    ap.add_argument("--cnn-profile", action="store_true",
+                    help="profiling aid: the learned network (untrained weights) on the ensemble's planes only")
     return ap.parse_args()
 
 
@@ -248,6 +250,20 @@ def main():
         step()
     torch.cuda.synchronize()
     dev_status = R.rca_sync_status(h)
+    if args.cnn_profile:
+        # the network's forward pass over every plane of the ensemble, twice
+        # (untrained weights: the kernels' work does not depend on them)
+        c = R.ulm_cnn_create(h, max_pixels=1 << 24, seed=1)
+        fc = 16
+        heat = torch.empty((fc * 2 * g.n_slab, 4 * g.nz, 4 * g.n_el), dtype=torch.float32, device=dev)
+        for _ in range(2):
+            for f0 in range(0, F - fc + 1, fc):
+                R.ulm_cnn_forward(c, A[f0:f0 + fc], M[f0:f0 + fc], 2 * g.n_slab, fc * 2 * g.n_slab, g.nz, g.n_el, heat)
+        torch.cuda.synchronize()
+        R.ulm_cnn_destroy(c)
+        emit({"cnn_profile": "done", "frames": F, "status": R.rca_sync_status(h)}, rank)
+        sess.close()
+        return
 
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
