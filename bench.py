@@ -324,7 +324,7 @@ def main():
                                "best of scalar and packed, %.0f MHz median SM clock); derived 152 x 128 x 2 x "
                                "sm_max_mhz = %.1f" % (fp32["sm_mhz"] or 0, fp32_derived_tflops),
                 "limiter": "shared-memory data path: each term reads two complex FP32 samples (16 B); "
-                           "83 % of L1/shared throughput in profiles/kernels_paper_40frames_full.md"}
+                           "83 % of L1/shared throughput in profiles/stage1_paper_40frames.md"}
     else:
         ach = bytes_alg[dominant] / (stage_ms[dominant] / 1e3) / 1e9
         roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
@@ -340,7 +340,7 @@ def main():
             src = open(os.path.join(ROOT, ent["source"]), "rb").read()
             if hashlib.sha256(src).hexdigest()[:16] == ent["source_sha256_16"]:
                 roof["traffic"] = int(ent["dram_bytes_per_frame"] * F)
-                roof["traffic_source"] = "profiles/kernels_paper_40frames_full.md, scaled by frames"
+                roof["traffic_source"] = "profiles/traffic.json (" + ent.get("profile", "ncu capture") + "), scaled by frames"
     except (OSError, ValueError, KeyError):
         pass
     stage_roof = {}
