@@ -3,7 +3,8 @@ its kernels check every shared-memory ring slot and record block of Stage 1,
 every staged window row of Stage 2 and every queue segment and counter index
 of the persistent batched launch, and record RCA_ERR_BOUNDS in the status
 word instead of trapping.  On the tiny ensemble (one-call beamformer with
-the paired and unpaired Stage-1 kernels, localisation) and on a batch of
+the paired and unpaired Stage-1 kernels at 32, 64 and 128 elements,
+localisation) and on a batch of
 uneven ensembles (persistent launch, also as a CUDA graph) every call must
 return RCA_OK with a clean status word and outputs bit-identical to the
 release build's.  Each build runs in a fresh process (RCA_LIBRARY selects
@@ -31,7 +32,7 @@ out, status = {}, []
 w = workload("tiny")
 G = generate(w)
 prm = rca.make_ulm_params(d=5, sig_z=0.807, sig_lat=1.4495, alpha=0.1, ncc_min=0.5)
-for n_el in (32, 64):
+for n_el in (32, 64, 128):
     g = dataclasses.replace(w.geom, n_el=n_el) if n_el != 32 else w.geom
     ww = dataclasses.replace(w, geom=g, n_frames=16)
     rf = generate(ww).rf.cuda() if n_el != 32 else G.rf.cuda()
