@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--workload", default="paper")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "reduced"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the tables' default Stage-1 / Stage-2 launch shapes (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=4)
     ap.add_argument("--frames", type=int, default=0, help="override the ensemble length (profiling runs)")
@@ -246,6 +248,15 @@ def main():
         R.ulm_pair3d(h, t, out2d, n2d, cap2d, F, out3d, cap3d, n3d)
         mark(6)
 
+    # Stage-1 (row tile x distance chunk) and Stage-2 (plane-row tile) launch
+    # shapes timed on this ensemble's IQ by the library's autotuner (part of
+    # the set-up, outside the timed region)
+    shapes = None
+    if not args.no_autotune:
+        R.rca_ingest(h, t, rf_dev, rf_t, scale, F, L.RCA_CLUTTER_MEAN, iq, iq_t)
+        zt_, dc_, zp_ = R.rca_autotune(h, t, iq, iq_t, F)
+        shapes = {"stage1_row_tile": zt_, "stage1_distance_chunk": dc_, "stage2_plane_rows": zp_,
+                  "source": "rca_autotune on this ensemble's IQ"}
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -430,7 +441,8 @@ def main():
     forms = None
     if rank == 0 and not args.no_forms and not reduced and not args.frames:
         forms = {}
-        forms["reduced"] = reduced_form(R, L, sess, rf, F, prm, max(3, args.warmup), K, stream)
+        forms["reduced"] = reduced_form(R, L, sess, rf, F, prm, max(3, args.warmup), K, stream,
+                                        autotune=not args.no_autotune)
         forms["batched"] = batched_form(R, L, dev, stream, K)
         forms["learned"] = learned_form(R, L, sess, planes, F, g, dev, stream, peaks)
     next_rows = rank == 0 and not args.no_next_rows and not reduced
@@ -462,6 +474,7 @@ def main():
             "dtype": "i16/f16/bf16+f32acc" if reduced else "f32",
             "data": "synthetic (seeded point scatterers; paper's in-vivo / Field II data unavailable)",
             "config": workload_config(w, F, args.precision, world),
+            "launch_shapes": shapes,
             "stages": stage_roof,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -781,14 +794,23 @@ def tracking_step(R, L, sess, out3d, n3d, cap3d, F, stream, K):
             "kernels": 7, "status": R.rca_sync_status(sess.h)}
 
 
-def reduced_form(R, L, sess, rf, F, prm, W, K, stream):
+def reduced_form(R, L, sess0, rf, F, prm, W, K, stream, autotune=True):
     """Same ensemble, int16 channel data + per-channel scale, FP16 IQ, BF16
-    planes, FP32 accumulation: ms per ensemble through the public calls."""
+    planes, FP32 accumulation: ms per ensemble through the public calls (own
+    tables, launch shapes tuned on its FP16 IQ)."""
     import torch
-    from paper_2511_21647_gb300.pipeline import complex_buffer
+    from paper_2511_21647_gb300.pipeline import RcaSession, complex_buffer
     from synth import quantize_int16
     q, scale = quantize_int16(rf)
     q, scale = q.contiguous(), scale.contiguous()
+    sess = RcaSession(sess0.geom, device=rf.device.index or 0)
+    R.rca_reserve(sess.h, sess.g, F)
+    shapes = None
+    if autotune:
+        iq0 = complex_buffer(sess.iq_shape(F), L.RCA_C16F, rf.device)
+        R.rca_ingest(sess.h, sess.t, q, L.RCA_I16, scale, F, L.RCA_CLUTTER_MEAN, iq0, L.RCA_C16F)
+        shapes = R.rca_autotune(sess.h, sess.t, iq0, L.RCA_C16F, F)
+        del iq0
     planes = complex_buffer(sess.planes_shape(F), L.RCA_C16BF, rf.device)
     cap2d, cap3d = 1 << 21, 1 << 19
     bufs = sess.loc_buffers(cap2d, cap3d)
@@ -833,11 +855,14 @@ def reduced_form(R, L, sess, rf, F, prm, W, K, stream):
             for q_, name in enumerate(("ingest", "stage1", "stage2")):
                 st_ms[name] += se[q_].elapsed_time(se[q_ + 1]) / K
     del iq, sl
-    return {"ms_per_ensemble": round(ms, 3), "value": round(F / (ms / 1e3), 1), "unit": "frames/s",
-            "beamform_ms": round(sum(bf) / K, 3), "localise_ms": round(sum(lo) / K, 3),
-            "stages_ms": {k: round(v, 3) for k, v in st_ms.items()},
-            "dtype": "int16 RF + per-channel scale, FP16 IQ, BF16 planes, FP32 accumulation",
-            "n3d": int(bufs[3].item()), "status": R.rca_sync_status(sess.h)}
+    out = {"ms_per_ensemble": round(ms, 3), "value": round(F / (ms / 1e3), 1), "unit": "frames/s",
+           "beamform_ms": round(sum(bf) / K, 3), "localise_ms": round(sum(lo) / K, 3),
+           "stages_ms": {k: round(v, 3) for k, v in st_ms.items()},
+           "launch_shapes": list(shapes) if shapes else None,
+           "dtype": "int16 RF + per-channel scale, FP16 IQ, BF16 planes, FP32 accumulation",
+           "n3d": int(bufs[3].item()), "status": R.rca_sync_status(sess.h)}
+    sess.close()
+    return out
 
 
 def batched_form(R, L, dev, stream, K):

@@ -140,7 +140,7 @@ __device__ __forceinline__ void mean_body(int bx, const void* __restrict__ rf, i
 // DM_OB consecutive samples of one element from a register window, so every
 // staged sample is read DM_OB + 30 times per DM_OB outputs instead of 17 times
 // per output.
-#define DM_OB 8             // consecutive outputs per thread
+#define DM_OB 16            // consecutive outputs per thread
 // four consecutive channel samples n .. n + 3 (n a multiple of 4) as floats
 template <int RT>
 __device__ __forceinline__ float4 rf_quad(const void* __restrict__ rf, size_t i)
@@ -177,16 +177,26 @@ __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __res
                        (reinterpret_cast<uintptr_t>(mean) & 15) == 0;
     if (quads) {
         // whole aligned quads n0-16+4q .. n0-13+4q (q < NQ): each inside or outside [0, ns).
-        // Items (element, quad) in element-major order, two per thread in flight:
-        // both items' loads are issued before either is converted and stored.
+        // Items (element, quad) in blocks of 4 elements x 4 quads per 16 consecutive
+        // threads: a half-warp's four stores of sample j then hit 16 different bank
+        // pairs (element rows 159 = 15 mod 16 float2 apart, quads 4 apart), and
+        // its loads are four 64-byte runs.  Two items per thread in flight: both
+        // items' loads are issued before either is converted and stored.
         constexpr int NQ = (DM_NT + 32) / 4;
         constexpr int ITEMS = DM_NE * NQ;
+        static_assert(NQ % 4 == 0 && DM_NE % 4 == 0, "4 x 4 item blocks");
+        auto item = [](int idx, int& el, int& q) {
+            const int grp = idx >> 4, sub = idx & 15;
+            el = (grp % (DM_NE / 4)) * 4 + (sub >> 2);
+            q = (grp / (DM_NE / 4)) * 4 + (sub & 3);
+        };
         for (int i0 = threadIdx.x; i0 < ITEMS; i0 += 2 * blockDim.x) {
             float4 r[2], mu[2], ma[2], mb[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int idx = i0 + u * blockDim.x;
-                const int el = idx / NQ, q = idx - el * NQ;
+                int el, q;
+                item(idx, el, q);
                 const int e = e0 + el, nb = n0 - 16 + 4 * q;
                 r[u] = mu[u] = ma[u] = mb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (idx < ITEMS && nb >= 0 && nb < ns && e < E) {
@@ -200,7 +210,8 @@ __device__ __forceinline__ void demod_body(int bx, int by, int bz, float2* __res
             for (int u = 0; u < 2; ++u) {
                 const int idx = i0 + u * blockDim.x;
                 if (idx >= ITEMS) continue;
-                const int el = idx / NQ, q = idx - el * NQ;
+                int el, q;
+                item(idx, el, q);
                 const int e = e0 + el;
                 const float sc = (rf_t == RCA_I16 && e < E) ? scale[k * E + e] : 1.f;
                 const float x0 = r[u].x * sc - mu[u].x, x1 = r[u].y * sc - mu[u].y;
