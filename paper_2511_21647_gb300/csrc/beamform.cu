@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256, 2) k_stage1(GeomDev g, const void* __rest
 }
 
 template <int TM, int US>
-__global__ void __launch_bounds__(S2_THREADS, 2) k_stage2(GeomDev g, const float2* __restrict__ slices,
+__global__ void __launch_bounds__(S2_THREADS, 3) k_stage2(GeomDev g, const float2* __restrict__ slices,
                                                        const int* __restrict__ sfl, const float* __restrict__ sfr,
                                                        const float4* __restrict__ lw, const float2* __restrict__ rot,
                                                        const float2* __restrict__ coef, const float2* __restrict__ c2,

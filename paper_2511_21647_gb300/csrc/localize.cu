@@ -836,18 +836,20 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     // padded vertical-sum arrays of row pairs
     size_t smem = (2 * std::max((size_t)rin * g.N, (size_t)(NCC_RS + 2) * (g.N + 1)) +
                    (size_t)3 * ((NCC_RS + 2) / 2) * det_npad(g.N, hh, det_hb(hh)) * 2) * sizeof(float);
-    // persistent CTAs (two per SM, each walking (plane, strip) items with the
-    // next item's rows in flight), never more CTAs than items
+    // persistent CTAs (as many as fit on an SM, each walking (plane, strip)
+    // items with the next item's rows in flight), never more CTAs than items
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    dim3 grid((unsigned)std::max(1, std::min(nslots, 2 * sms)));
     cudaError_t e = cudaSuccess;
     switch (hh) {
 #define RCA_DETECT_LAUNCH(HV, NV)                                                                          \
     do {                                                                                                   \
         e = cudaFuncSetAttribute(k_detect<HV, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return cuda_check(h, e, "detect smem attribute");                          \
+        int per_sm = 0;                                                                                    \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect<HV, NV>, NCC_THREADS, smem);       \
+        const dim3 grid((unsigned)std::max(1, std::min(nslots, std::max(1, per_sm) * sms)));               \
         k_detect<HV, NV><<<grid, NCC_THREADS, smem, h->stream>>>(A, M, g.S, g.nz, g.N, nplanes, nc, cand, cnt, \
                                                                  ncc_out, h->d_status);                   \
     } while (0)
