@@ -775,12 +775,17 @@ rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes
     const size_t npx = 2 * (size_t)g.S * plane_sz;
     if (F > 48 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "more than 49152 frames in one call");
     cudaMemsetAsync(M, 0, sizeof(float) * F, h->stream);
-    // enough blocks to fill the GPU: split the frames when the planes are small
+    // Every block walks all frames of its chunk, so the last wave of blocks
+    // sets the tail: split the frames into chunks until the grid holds at
+    // least eight waves of resident blocks (each chunk re-reads one frame;
+    // at least 16 frames per chunk)
     const unsigned pblocks = (unsigned)((npx + 255) / 256);
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int want = std::max(1, (int)((4u * (unsigned)sms + pblocks - 1) / pblocks));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enhance, 256, (size_t)std::min(F, 16) * sizeof(unsigned));
+    const unsigned resident = (unsigned)(std::max(1, per_sm) * sms);
+    const int want = std::max(1, (int)((8u * resident + pblocks - 1) / pblocks));
     const int nchunk = std::min(want, std::max(1, F / 16));
     const int tf = (F + nchunk - 1) / nchunk;
     const size_t smem = (size_t)tf * sizeof(unsigned);
