@@ -607,7 +607,8 @@ typedef struct {
 
 /* Plan a batch of n ensembles of uneven frame counts and transmission sets.
  * Beamforming of the whole batch (mean clutter removal, demodulation,
- * Stage 1, Stage 2 + projection) runs as ONE persistent launch: a device
+ * Stage 1, Stage 2 + projection) runs by default as ONE persistent launch
+ * (see rca_batch_set_mode for one launch per stage instead): a device
  * work queue of units, ordered so that every unit only waits for earlier
  * ones through per-ensemble completion counters (bounded waits: a wait that
  * runs out sets RCA_ERR_TIMEOUT in the status word and stops the launch).
@@ -629,6 +630,18 @@ rca_status rca_batch_run(rca_batch* b, int use_graph);
  * repeated batches build the plan once and run it (optionally as a graph). */
 rca_status rca_beamform_projections_batched(rca_handle* h, int n, const rca_batch_item* items, rca_dtype rf_dtype,
                                             rca_dtype planes_dtype, const ulm_params* prm);
+
+/* Launch mode of later runs.  RCA_BATCH_PERSISTENT (the default): the whole
+ * beamforming as one persistent launch with the dependency-ordered queue
+ * described at rca_batch_create.  RCA_BATCH_STAGED: one launch per stage
+ * (mean, demodulation, Stage 1, Stage 2), each over the units of that stage
+ * of every ensemble, sized by that stage's shared memory; the stream orders
+ * the stages, so no unit waits.  Same bodies, same results bit for bit.
+ * Discards a captured graph (the next rca_batch_run with use_graph captures
+ * again).  Errors: INVALID_ARG. */
+#define RCA_BATCH_PERSISTENT 0
+#define RCA_BATCH_STAGED 1
+rca_status rca_batch_set_mode(rca_batch* b, int mode);
 
 /* Bound of every dependency wait in the persistent launch, in SM clock
  * cycles (default ~4e9).  block_ensemble >= 0 makes that ensemble's Stage-1

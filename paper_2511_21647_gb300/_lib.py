@@ -31,6 +31,7 @@ RCA_ERR_BOUNDS = 7
 RCA_F32, RCA_I16, RCA_F16, RCA_C32, RCA_C16F, RCA_C16BF = range(6)
 
 RCA_MODE_TWO_STAGE, RCA_MODE_DIRECT = 0, 1
+RCA_BATCH_PERSISTENT, RCA_BATCH_STAGED = 0, 1
 RCA_CLUTTER_NONE, RCA_CLUTTER_MEAN, RCA_CLUTTER_SVD = 0, 1, 2
 ULM_ENH_XDOPPLER, ULM_ENH_COHERENT = 0, 1
 
@@ -145,6 +146,7 @@ SIGNATURES = {
     "rca_batch_create": (_S, [_P, _I, C.POINTER(rca_batch_item), _I, _I, _I, C.POINTER(ulm_params), C.POINTER(_P)]),
     "rca_beamform_projections_batched": (_S, [_P, _I, C.POINTER(rca_batch_item), _I, _I, C.POINTER(ulm_params)]),
     "rca_batch_run": (_S, [_P, _I]),
+    "rca_batch_set_mode": (_S, [_P, _I]),
     "rca_batch_set_wait_limit": (_S, [_P, C.c_longlong, _I]),
     "rca_batch_destroy": (_S, [_P]),
     "rca_autotune": (_S, [_P, _P, _P, _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),

@@ -703,6 +703,7 @@ static void batch_free(rca_batch* b)
         if (p) cudaFree(p);
     if (b->d_ens) cudaFree(b->d_ens);
     if (b->d_segs) cudaFree(b->d_segs);
+    if (b->d_ssegs) cudaFree(b->d_ssegs);
     if (b->d_cnt) cudaFree(b->d_cnt);
 }
 
@@ -878,6 +879,30 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
         (void)nt;
     }
     b->total = unit;
+    // staged mode: per stage, every ensemble's units of that stage in one segment each
+    std::vector<int4> ssegs;
+    size_t s1max = 0, s2max = 0;
+    for (int e = 0; e < n; ++e) {
+        s1max = std::max(s1max, stage1_smem_bytes(items[e].tables, b->ens[e].zt, b->ens[e].dc, b->ens[e].ring, esz));
+        s2max = std::max(s2max, stage2_smem_bytes(items[e].tables, b->ens[e].zp));
+    }
+    for (int stage = BS_MEAN; stage <= BS_STAGE2; ++stage) {
+        b->sseg0[stage] = (int)ssegs.size();
+        int u = 0;
+        for (int e = 0; e < n; ++e) {
+            const BatchEns& E = b->ens[e];
+            const int cntu = stage == BS_MEAN ? E.nA : stage == BS_DEMOD ? E.nB : stage == BS_STAGE1 ? E.nC : E.nD;
+            if (cntu <= 0) continue;
+            ssegs.push_back(make_int4(stage | (e << 4), u, cntu, 0));
+            u += cntu;
+        }
+        b->stotal[stage] = u;
+    }
+    b->sseg0[4] = (int)ssegs.size();
+    b->ssmem[BS_MEAN] = 0;
+    b->ssmem[BS_DEMOD] = (size_t)32 * 159 * 8;
+    b->ssmem[BS_STAGE1] = s1max;
+    b->ssmem[BS_STAGE2] = s2max;
     b->n_counters = counters;
     b->maxr = maxr;
     b->tmax = tmax;
@@ -885,13 +910,15 @@ extern "C" rca_status rca_batch_create(rca_handle* h, int n, const rca_batch_ite
     b->smem = smem;
     if (cudaMalloc(&b->d_ens, sizeof(BatchEns) * n) != cudaSuccess ||
         cudaMalloc(&b->d_segs, sizeof(int4) * b->segs.size()) != cudaSuccess ||
-        cudaMalloc(&b->d_cnt, sizeof(int) * (counters + 2)) != cudaSuccess) {
+        cudaMalloc(&b->d_cnt, sizeof(int) * (counters + 2)) != cudaSuccess ||
+        cudaMalloc(&b->d_ssegs, sizeof(int4) * ssegs.size()) != cudaSuccess) {
         batch_free(b);
         delete b;
         return set_error(h, RCA_ERR_CUDA, "batch descriptor cudaMalloc failed");
     }
     cudaMemcpy(b->d_ens, b->ens.data(), sizeof(BatchEns) * n, cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_segs, b->segs.data(), sizeof(int4) * b->segs.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_ssegs, ssegs.data(), sizeof(int4) * ssegs.size(), cudaMemcpyHostToDevice);
     if (prm) {
         b->localise = true;
         b->prm = *prm;
@@ -988,6 +1015,18 @@ extern "C" rca_status rca_batch_run(rca_batch* b, int use_graph)
         return RCA_OK;  // the warm-up run already produced this run's results
     }
     return cuda_check(h, cudaGraphLaunch(b->exec, h->stream), "graph launch");
+}
+
+extern "C" rca_status rca_batch_set_mode(rca_batch* b, int mode)
+{
+    if (!b || (mode != RCA_BATCH_PERSISTENT && mode != RCA_BATCH_STAGED)) return RCA_ERR_INVALID_ARG;
+    DeviceGuard dg(b->h->device);
+    b->mode = mode;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return RCA_OK;
 }
 
 extern "C" rca_status rca_batch_set_wait_limit(rca_batch* b, long long cycles, int block_ensemble)

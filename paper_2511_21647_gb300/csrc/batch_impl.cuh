@@ -14,7 +14,9 @@ namespace {
 // as the standalone kernel, and publishes its completion.  Units only wait
 // on units earlier in the queue, which were taken by CTAs already running,
 // so the queue always drains.  A wait that runs out sets ST_TIMEOUT and an
-// abort flag that stops every CTA at its next unit.
+// abort flag that stops every CTA at its next unit.  nowait != 0 (staged
+// mode: the queue holds the units of one stage, whose inputs earlier
+// launches on the stream completed) skips the waits and the counters.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
@@ -28,7 +30,7 @@ template <typename TS, int MAXR, int TM, int US>
 __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ ens, const int4* __restrict__ segs,
                                                  int nseg, int total, int* __restrict__ cnt, int n_counters,
                                                  long long wait_limit, Fir fir, int rf_t, int iq_t, int pt,
-                                                 unsigned* __restrict__ status)
+                                                 int nowait, unsigned* __restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bars[2];
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
             int ok = 1;
             // the counters the unit waits on and completes (checked build)
             if (!chk(dep < n_counters && done < n_counters, status)) ok = 0;
-            if (ok && dep >= 0) {
+            if (ok && dep >= 0 && !nowait) {
                 const long long t0 = clock64();
                 while (ld_acquire(cnt + dep) < dep_target) {
                     if (*(volatile int*)abort_flag) {
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchEns* __restrict__ e
             }
             if (!ok) {
                 atomicExch(abort_flag, 1);
-            } else if (done >= 0) {
+            } else if (done >= 0 && !nowait) {
                 __threadfence();
                 atomicAdd(cnt + done, 1);
             }
@@ -185,10 +187,30 @@ static rca_status batch_launch(rca_handle* h, rca_batch* b)
     }
     Fir fir;
     for (int q = 0; q < 31; ++q) fir.h[q] = b->fir[q];
+    if (b->mode == RCA_BATCH_STAGED) {
+        // one launch per stage, each sized by its own shared memory
+        for (int s = BS_MEAN; s <= BS_STAGE2; ++s) {
+            if (b->stotal[s] == 0) continue;
+            if (b->sgrid[s] == 0) {
+                int per_sm = 0, dev = 0, sms = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, b->ssmem[s]);
+                b->sgrid[s] = std::max(1, std::min(b->stotal[s], std::max(1, per_sm) * sms));
+            }
+            cudaMemsetAsync(b->d_cnt + b->n_counters, 0, sizeof(int) * 2, h->stream);
+            kern<<<b->sgrid[s], 256, b->ssmem[s], h->stream>>>(
+                b->d_ens, b->d_ssegs + b->sseg0[s], b->sseg0[s + 1] - b->sseg0[s], b->stotal[s], b->d_cnt,
+                b->n_counters, b->wait_limit, fir, (int)b->rf_t, (int)b->iq_t, (int)b->pl_t, 1, h->d_status);
+            rca_status st = cuda_check(h, cudaGetLastError(), "batch stage kernel");
+            if (st != RCA_OK) return st;
+        }
+        return RCA_OK;
+    }
     cudaMemsetAsync(b->d_cnt, 0, sizeof(int) * (b->n_counters + 2), h->stream);
     kern<<<b->grid, 256, b->smem, h->stream>>>(b->d_ens, b->d_segs, (int)b->segs.size(), b->total, b->d_cnt,
                                                b->n_counters, b->wait_limit, fir, (int)b->rf_t, (int)b->iq_t,
-                                               (int)b->pl_t, h->d_status);
+                                               (int)b->pl_t, 0, h->d_status);
     return cuda_check(h, cudaGetLastError(), "batch kernel");
 }
 

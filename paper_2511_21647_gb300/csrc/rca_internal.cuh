@@ -539,6 +539,15 @@ struct rca_batch {
     bool us2 = true;              // every ensemble has two slice rows per plane row
     size_t smem = 0;
     int grid = 0;
+    // launch mode: RCA_BATCH_PERSISTENT (one launch, dependency-ordered queue)
+    // or RCA_BATCH_STAGED (one launch per stage over every ensemble's units
+    // of that stage; stream order replaces the dependency waits)
+    int mode = 0;
+    int4* d_ssegs = nullptr;      // staged mode: segments of stage s at [sseg0[s], sseg0[s + 1]), units from 0
+    int sseg0[5] = {0, 0, 0, 0, 0};
+    int stotal[4] = {0, 0, 0, 0}; // units per stage
+    size_t ssmem[4] = {0, 0, 0, 0};
+    int sgrid[4] = {0, 0, 0, 0};
     // optional localisation
     bool localise = false;
     ulm_params prm{};

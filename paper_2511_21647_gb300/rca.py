@@ -298,6 +298,10 @@ def rca_batch_run(b, use_graph=False, h=None):
     _check(L.load().rca_batch_run(b, int(bool(use_graph))), h, "rca_batch_run")
 
 
+def rca_batch_set_mode(b, mode):
+    _check(L.load().rca_batch_set_mode(b, int(mode)), None, "rca_batch_set_mode")
+
+
 def rca_batch_set_wait_limit(b, cycles, block_ensemble=-1):
     _check(L.load().rca_batch_set_wait_limit(b, int(cycles), int(block_ensemble)), None, "rca_batch_set_wait_limit")
 

@@ -1,5 +1,6 @@
 """Batched form: uneven ensembles (frame counts, 2K in {2, 4, 8}) in one
-persistent launch, optionally replayed as a CUDA graph; the launch-shape
+persistent launch or one launch per stage, optionally replayed as a CUDA
+graph; the launch-shape
 autotuner; and the bounded-wait failure path of the persistent queue (a
 host-built dependency that never completes must end the launch with
 RCA_ERR_TIMEOUT, and the handle must stay usable)."""
@@ -86,6 +87,33 @@ def test_persistent_batch_matches_oracle_and_single_calls(handle, ensembles):
                                          rca.bf_params(), single, L.RCA_C32)
             torch.cuda.synchronize()
             assert torch.equal(single, it["planes"]), w.name   # same bodies, same order: bit-identical
+    finally:
+        rca.rca_batch_destroy(b)
+        free(keep)
+
+
+def test_staged_mode_equals_persistent_launch(handle, ensembles):
+    """one launch per stage (no dependency waits) gives the persistent
+    launch's planes bit for bit, plain and replayed as a graph"""
+    from paper_2511_21647_gb300 import _lib as L
+    from paper_2511_21647_gb300 import rca
+    items, keep = make_items(handle, ensembles)
+    b = rca.rca_batch_create(handle, items, L.RCA_F32, L.RCA_C32, L.RCA_C32)
+    try:
+        rca.rca_batch_run(b, use_graph=False, h=handle)
+        torch.cuda.synchronize()
+        ref = [it["planes"].clone() for it in items]
+        for use_graph in (False, True, True):
+            rca.rca_batch_set_mode(b, L.RCA_BATCH_STAGED)
+            for it in items:
+                it["planes"].zero_()
+            rca.rca_batch_run(b, use_graph=use_graph, h=handle)
+            torch.cuda.synchronize()
+            assert rca.rca_sync_status(handle) == L.RCA_OK
+            for q, it in enumerate(items):
+                assert torch.equal(ref[q], it["planes"]), (use_graph, q)
+        with pytest.raises(rca.RcaError):
+            rca.rca_batch_set_mode(b, 7)
     finally:
         rca.rca_batch_destroy(b)
         free(keep)
