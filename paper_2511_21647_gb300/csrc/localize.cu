@@ -18,9 +18,22 @@ namespace {
 // max, shared-memory atomicMax per frame, one global atomicMax per block and
 // frame at the end (non-negative floats order like their bits).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes, int pt, int F, int S,
-                                                 size_t plane_sz, int enh, int tf, float* __restrict__ A,
-                                                 unsigned* __restrict__ M)
+// plane element i of compile-time dtype PT as float2 (read-only path)
+template <int PT>
+__device__ __forceinline__ float2 ld_plane(const void* __restrict__ p, size_t i)
+{
+    if constexpr (PT == RCA_C32) {
+        return __ldg(reinterpret_cast<const float2*>(p) + i);
+    } else {
+        const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p) + i);
+        if constexpr (PT == RCA_C16F) return __half22float2(*reinterpret_cast<const __half2*>(&u));
+        else return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+    }
+}
+
+template <int PT>
+__global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes, int F, int S, size_t plane_sz,
+                                                 int enh, int tf, float* __restrict__ A, unsigned* __restrict__ M)
 {
     extern __shared__ unsigned mx[];  // [tf] maxima of this chunk's frames
     const int t0 = blockIdx.y * tf, t1 = min(F, t0 + tf);
@@ -28,21 +41,32 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
     __syncthreads();
     const size_t per_axis = (size_t)S * plane_sz;
     const size_t npx = 2 * per_axis;
+    const size_t FS = 2 * npx;                       // elements per frame: [axis][family][S][nz][N]
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = p < npx;
     const size_t axis = act ? p / per_axis : 0, rest = act ? p % per_axis : 0;
     const int lane = threadIdx.x & 31;
-    auto at = [&](int t, int fam) { return (((size_t)t * 2 + axis) * 2 + fam) * per_axis + rest; };
+    // element of the RC plane of frame t is t FS + oR; its CR plane lies per_axis further
+    const size_t oR = axis * 2 * per_axis + rest;
     auto ld = [&](int t, int fam) {
-        return (act && t < F) ? load_c(planes, at(t, fam), pt) : make_float2(0.f, 0.f);
+        return (act && t < F) ? ld_plane<PT>(planes, (size_t)t * FS + oR + (fam ? per_axis : 0))
+                              : make_float2(0.f, 0.f);
     };
     auto xq = [](float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); };
     float2 r0 = ld(t0, 0), c0 = ld(t0, 1), r1 = ld(t0 + 1, 0), c1 = ld(t0 + 1, 1);
     float2 r2 = ld(t0 + 2, 0), c2 = ld(t0 + 2, 1);
     float2 qm = make_float2(0.f, 0.f);
     if (t0 > 0 && enh == ULM_ENH_XDOPPLER) qm = xq(ld(t0 - 1, 0), ld(t0 - 1, 1));
+    // prefetch index of frame t + 3 and output pointer of frame t, advanced per frame
+    size_t i3 = (size_t)(t0 + 3) * FS + oR;
+    float* out = A + (size_t)t0 * npx + p;
     for (int t = t0; t < t1; ++t) {
-        const float2 r3 = ld(t + 3, 0), c3 = ld(t + 3, 1);  // prefetch
+        float2 r3 = make_float2(0.f, 0.f), c3 = r3;
+        if (act && t + 3 < F) {
+            r3 = ld_plane<PT>(planes, i3);
+            c3 = ld_plane<PT>(planes, i3 + per_axis);
+        }
+        i3 += FS;
         float a;
         if (enh == ULM_ENH_XDOPPLER) {
             const float2 q0 = xq(r0, c0), qp = xq(r1, c1);
@@ -53,10 +77,11 @@ __global__ void __launch_bounds__(256) k_enhance(const void* __restrict__ planes
             const float re = r0.x + c0.x, im = r0.y + c0.y;
             a = sqrtf(re * re + im * im);
         }
-        if (act) __stcs(A + (size_t)t * npx + p, a);
-        float m = act ? a : 0.f;
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) atomicMax(mx + (t - t0), __float_as_uint(m));
+        if (act) __stcs(out, a);
+        out += npx;
+        // warp maximum on the bits (non-negative floats order like their bits)
+        const unsigned m = __reduce_max_sync(0xffffffffu, act ? __float_as_uint(a) : 0u);
+        if (lane == 0) atomicMax(mx + (t - t0), m);
         r0 = r1; c0 = c1; r1 = r2; c1 = c2; r2 = r3; c2 = c3;
     }
     __syncthreads();
@@ -783,17 +808,17 @@ rca_status launch_enhance(rca_handle* h, const rca_tables* t, const void* planes
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enhance, 256, (size_t)std::min(F, 16) * sizeof(unsigned));
+    auto kern = pt == RCA_C32 ? k_enhance<RCA_C32> : pt == RCA_C16F ? k_enhance<RCA_C16F> : k_enhance<RCA_C16BF>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, (size_t)std::min(F, 16) * sizeof(unsigned));
     const unsigned resident = (unsigned)(std::max(1, per_sm) * sms);
     const int want = std::max(1, (int)((8u * resident + pblocks - 1) / pblocks));
     const int nchunk = std::min(want, std::max(1, F / 16));
     const int tf = (F + nchunk - 1) / nchunk;
     const size_t smem = (size_t)tf * sizeof(unsigned);
-    cudaError_t e = cudaFuncSetAttribute(k_enhance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "enhance smem attribute");
     dim3 grid(pblocks, (unsigned)((F + tf - 1) / tf));
-    k_enhance<<<grid, 256, smem, h->stream>>>(planes, (int)pt, F, g.S, plane_sz, enh, tf, A,
-                                              reinterpret_cast<unsigned*>(M));
+    kern<<<grid, 256, smem, h->stream>>>(planes, F, g.S, plane_sz, enh, tf, A, reinterpret_cast<unsigned*>(M));
     return cuda_check(h, cudaGetLastError(), "enhance kernel");
 }
 
