@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
     constexpr int D = 2 * H + 1;
     constexpr int RN = NCC_RS + 2;          // NCC rows: the strip and one row above and below
     constexpr int RP = RN / 2;              // row pairs
-    constexpr int VB = H >= 2 ? 4 : 2;      // output rows per vertical task
+    constexpr int VB = H >= 4 ? 8 : (H >= 2 ? 4 : 2);   // output rows per vertical task
     constexpr int HB = H >= 4 ? 8 : 2 * H;  // output columns per horizontal task (det_hb)
     constexpr int NW = (NCC_RS * 256 + 31) / 32;   // bitmap words of the strip's pixels (N <= 256)
     static_assert(RN % VB == 0 && VB % 2 == 0 && VB <= D, "vertical runs must tile the NCC rows in pairs");
