@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
     const size_t abuf = max((size_t)rin * N, (size_t)RN * NS);
     // sm + bb abuf (bb = 0, 1): [rin][N] amplitude rows i0-1-H ..., double-buffered
     float* sV = sm + 2 * abuf;              // [3][RP][NPAD][2]; column c at c + H
+    // [RN][N] flags A >= alpha M_t of the NCC rows' pixels, set by the vertical pass
+    // (which holds the amplitudes), so that no phase after it reads global memory
+    unsigned char* aflag = reinterpret_cast<unsigned char*>(sV + (size_t)3 * RP * NPAD * 2);
     __shared__ unsigned bits[NW];           // candidate pixels of the strip, raster order
     __shared__ int wsum[NCC_THREADS / 32];
     __shared__ int base_count;
@@ -232,8 +235,8 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
         const int plane = it / nstrip, strip = it - plane * nstrip;
         const int t = plane / (2 * S), axis = (plane / S) % 2, b = plane % S;
         const int i0 = strip * NCC_RS;
-        const float* Ap = A + (size_t)plane * nz * N;
         const float Mt = Mf[t];
+        const float athr = nc.alpha * Mt;
         for (int idx = threadIdx.x; idx < NW; idx += blockDim.x) bits[idx] = 0u;
         // ---- vertical pass: thread = (column pair, VB output rows)
         {
@@ -247,6 +250,13 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
                 const unsigned src = sAa + (unsigned)((ro0 * N + 2 * cp) * 4);
 #pragma unroll
                 for (int m = 0; m < VB + 2 * H; ++m) x[m] = lds_u64(src + (unsigned)(m * N * 4));
+#pragma unroll
+                for (int r = 0; r < VB; ++r) {
+                    // the centre amplitude of NCC row ro0 + r, both columns of the pair
+                    const float2 ac = f2_unpack(x[r + H]);
+                    const unsigned short fl = (unsigned short)((ac.x >= athr ? 1u : 0u) | (ac.y >= athr ? 0x100u : 0u));
+                    *reinterpret_cast<unsigned short*>(aflag + (ro0 + r) * N + 2 * cp) = fl;
+                }
                 uint64_t v1[VB], v2[VB], vg[VB];
                 split_box<H, VB>([&](int q) { return x[q]; }, v1);
                 split_box<H, VB>([&](int q) { return f2_mul(x[q], x[q]); }, v2);
@@ -334,7 +344,6 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
         // the candidates in a raster-order bitmap, then compact the bitmap words
         // (consecutive words per thread, a block-wide exclusive scan of their
         // counts) so the strip's candidates come out in raster order
-        const float athr = nc.alpha * Mt;
         {
             const int RG = NCC_THREADS / N > 0 ? NCC_THREADS / N : 1;   // row groups (N <= 256)
             const int l = threadIdx.x % N, rg = threadIdx.x / N;
@@ -345,10 +354,8 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
                 const float* np_ = sN + ro * NS + l;
                 for (; ro <= ro_hi; ro += RG, np_ += RG * NS) {
                     const float c = *np_;
-                    const int i = i0 - 1 + ro;
                     if (!(c >= nc.ncc_min)) continue;
-                    if (!(__ldg(Ap + (size_t)i * N + l) >= athr)) continue;
-                    bool pk = true;
+                    bool pk = aflag[ro * N + l] != 0;
 #pragma unroll
                     for (int a = -1; a <= 1; ++a)
 #pragma unroll
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
                 e.z = (float)i + para(sN[(ro - 1) * NS + l], c, sN[(ro + 1) * NS + l]);
                 e.lat = (float)l + para(sN[ro * NS + l - 1], c, sN[ro * NS + l + 1]);
                 e.ncc = c;
-                e.amp = __ldg(Ap + (size_t)i * N + l);
+                e.amp = 0.f;        // filled from A by the gather (no global load in this phase)
                 e.reserved = 0;
                 slot[before] = e;
             }
@@ -647,8 +654,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int* __restri
 }
 
 // Copy each strip's kept candidates to their place in the output list.
+// A non-null: each entry's amplitude is read here from A [plane][nz][N] at its
+// pixel (the detection kernel leaves it to this highly parallel pass)
 __global__ void k_gather(const ulm_loc2d* __restrict__ cand, const int* __restrict__ cnt, const int* __restrict__ off,
-                         int nslots, ulm_loc2d* __restrict__ out, int cap, unsigned* __restrict__ status)
+                         int nslots, ulm_loc2d* __restrict__ out, int cap, const float* __restrict__ A, int S, int nz,
+                         int N, unsigned* __restrict__ status)
 {
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= nslots) return;
@@ -656,8 +666,13 @@ __global__ void k_gather(const ulm_loc2d* __restrict__ cand, const int* __restri
     const int c = min(cnt[s], CAND_CAP);
     for (int r = lane; r < c; r += 32) {
         int dst = off[s] + r;
-        if (dst < cap) out[dst] = cand[(size_t)s * CAND_CAP + r];
-        else atomicOr(status, ST_CAPACITY);
+        if (dst < cap) {
+            ulm_loc2d e = cand[(size_t)s * CAND_CAP + r];
+            if (A) e.amp = __ldg(A + (((size_t)(e.frame * 2 + e.axis) * S + e.slab) * nz + e.iz) * N + e.ilat);
+            out[dst] = e;
+        } else {
+            atomicOr(status, ST_CAPACITY);
+        }
     }
 }
 
@@ -864,8 +879,10 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     const int rin = NCC_RS + 2 + 2 * hh;
     // two buffers of amplitude rows (later the NCC rows, stride N + 1) + three
     // padded vertical-sum arrays of row pairs
+    // + the amplitude flags of the NCC rows ([NCC_RS + 2][N] bytes)
     size_t smem = (2 * std::max((size_t)rin * g.N, (size_t)(NCC_RS + 2) * (g.N + 1)) +
-                   (size_t)3 * ((NCC_RS + 2) / 2) * det_npad(g.N, hh, det_hb(hh)) * 2) * sizeof(float);
+                   (size_t)3 * ((NCC_RS + 2) / 2) * det_npad(g.N, hh, det_hb(hh)) * 2) * sizeof(float) +
+                  (size_t)(NCC_RS + 2) * g.N;
     // persistent CTAs (as many as fit on an SM, each walking (plane, strip)
     // items with the next item's rows in flight), never more CTAs than items
     int dev = 0, sms = 0;
@@ -903,7 +920,8 @@ rca_status launch_detect2d(rca_handle* h, const rca_tables* t, const float* A, c
     long long* part = (long long*)ws_get(h, WS_N2D, (size_t)2 * 1024 * sizeof(long long), &st);
     if (!part) return st;
     if ((st = device_scan(h, cnt, nslots, nullptr, CAND_CAP, off, n2d, part)) != RCA_OK) return st;
-    k_gather<<<(nslots + 7) / 8, 256, 0, h->stream>>>(cand, cnt, off, nslots, out, cap, h->d_status);
+    k_gather<<<(nslots + 7) / 8, 256, 0, h->stream>>>(cand, cnt, off, nslots, out, cap, A, g.S, g.nz, g.N,
+                                                      h->d_status);
     if (plane_off) k_strip_to_plane<<<(nplanes + 1 + 255) / 256, 256, 0, h->stream>>>(off, nstrip, nplanes, plane_off);
     return cuda_check(h, cudaGetLastError(), "detect kernels");
 }
@@ -1045,6 +1063,7 @@ rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* ma
     dim3 grid(nstrip, nplanes);
     k_detect_map<<<grid, 256, smem, h->stream>>>(map, up, A, M, g.S, g.nz, g.N, score_min, alpha, cand, cnt, h->d_status);
     if ((st = device_scan(h, cnt, nslots, nullptr, CAND_CAP, off, n2d, part)) != RCA_OK) return st;
-    k_gather<<<(nslots + 7) / 8, 256, 0, h->stream>>>(cand, cnt, off, nslots, out, cap, h->d_status);
+    k_gather<<<(nslots + 7) / 8, 256, 0, h->stream>>>(cand, cnt, off, nslots, out, cap, nullptr, 0, 0, 0,
+                                                      h->d_status);
     return cuda_check(h, cudaGetLastError(), "detect_map kernels");
 }
