@@ -706,14 +706,27 @@ __global__ void k_list_plane_offsets(const ulm_loc2d* __restrict__ L, const int*
 // XZ / YZ eligibility and cost in double precision: same frame and
 // sub-block, |dz| <= 1 pixel, ratio I_xz / I_yz in [0.9, 1.11];
 // cost max(I) / min(I) (orders pairs like |ln ratio|).
+// The decisions are those of FP64 arithmetic on the FP32 inputs (the oracle's).
+// GB300's FP64 rate is low, so each test is first taken in FP32 where that
+// provably gives the same answer (rounding to nearest is monotonic, so
+// fl32(e) > 1 implies e > 1 and fl32(e) < 1 implies e < 1; a ratio more than
+// 0.01 inside or outside a bound is on the same side in FP64), and in FP64
+// only when the FP32 value sits at the bound.
 __device__ __forceinline__ bool pair_ok(const ulm_loc2d& x, const ulm_loc2d& y, int P, double* cost)
 {
     if (x.frame != y.frame) return false;
     if (x.ilat / P != y.slab || y.ilat / P != x.slab) return false;
-    if (fabs((double)x.z - (double)y.z) > 1.0) return false;
-    double ax = x.amp, ay = y.amp;
-    double r = ax / ay;
-    if (!(r >= 0.9 && r <= 1.11)) return false;
+    const float dz = fabsf(x.z - y.z);
+    if (dz > 1.0f) return false;
+    if (dz == 1.0f && fabs((double)x.z - (double)y.z) > 1.0) return false;
+    const float r32 = x.amp / y.amp;
+    const bool lo_sure = r32 >= 0.91f, hi_sure = r32 <= 1.10f;
+    if (r32 <= 0.89f || r32 >= 1.12f || !(r32 == r32)) return false;
+    const double ax = x.amp, ay = y.amp;
+    if (!(lo_sure && hi_sure)) {
+        const double r = ax / ay;
+        if (!(r >= 0.9 && r <= 1.11)) return false;
+    }
     *cost = ax > ay ? ax / ay : ay / ax;
     return true;
 }
