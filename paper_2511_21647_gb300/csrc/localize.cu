@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
     unsigned char* aflag = reinterpret_cast<unsigned char*>(sV + (size_t)3 * RP * NPAD * 2);
     __shared__ unsigned bits[NW];           // candidate pixels of the strip, raster order
     __shared__ int wsum[NCC_THREADS / 32];
-    __shared__ int base_count;
     __shared__ uint64_t bar[2];
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -352,6 +351,7 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
             if (rg < RG && l >= 1 && l < N - 1) {
                 int ro = ro_lo + rg;
                 const float* np_ = sN + ro * NS + l;
+#pragma unroll 3
                 for (; ro <= ro_hi; ro += RG, np_ += RG * NS) {
                     const float c = *np_;
                     if (!(c >= nc.ncc_min)) continue;
@@ -420,11 +420,10 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
             }
             ++before;
         }
-        if (threadIdx.x == blockDim.x - 1) base_count = before;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            cnt[it] = base_count;
-            if (base_count > CAND_CAP) atomicOr(status, ST_CAPACITY);
+        // the last thread's running index is the strip's count
+        if (threadIdx.x == blockDim.x - 1) {
+            cnt[it] = before;
+            if (before > CAND_CAP) atomicOr(status, ST_CAPACITY);
         }
         // the next iteration fetches into this buffer and rewrites the bitmap
         __syncthreads();
