@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
             if (rg < RG && l >= 1 && l < N - 1) {
                 int ro = ro_lo + rg;
                 const float* np_ = sN + ro * NS + l;
-#pragma unroll 3
+#pragma unroll 5
                 for (; ro <= ro_hi; ro += RG, np_ += RG * NS) {
                     const float c = *np_;
                     if (!(c >= nc.ncc_min)) continue;
