@@ -801,6 +801,7 @@ __device__ __forceinline__ void s2_lateral(int sb, int u, int q0, int nrow, int 
     uint64_t O1[S2_RH], O2[S2_RH];
 #pragma unroll
     for (int q = 0; q < S2_RH; ++q) O1[q] = O2[q] = 0ull;
+#pragma unroll 2
     for (int kk = 0; kk < K; ++kk) {
         const float4 w = sLw[kk * N + u];            // a, b: interpolation weights with the carrier folded in
         const uint64_t ax = f2_pack(w.x, w.x), ay = f2_pack(w.y, w.y);
