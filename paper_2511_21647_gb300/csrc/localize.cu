@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
         for (int idx = threadIdx.x; idx < (rin - z1) * N; idx += blockDim.x) sA[(size_t)z1 * N + idx] = 0.f;
         if (threadIdx.x == 0) {
             fence_proxy_async();
-            const unsigned bytes = (unsigned)((hi - lo) * N * sizeof(float));
+            // the copied rows land inside the buffer's rin rows (checked build; else nothing is copied)
+            const bool in = chk(lo >= rlo && hi - rlo <= rin && plane < nplanes, status);
+            const unsigned bytes = in ? (unsigned)((hi - lo) * N * sizeof(float)) : 0u;
             mbar_arrive_expect_tx(&bar[bb], bytes);
             if (bytes)
                 bulk_g2s(sA + (size_t)(lo - rlo) * N, A + ((size_t)plane * nz + lo) * N, bytes, &bar[bb]);
@@ -254,7 +256,8 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
                     // the centre amplitude of NCC row ro0 + r, both columns of the pair
                     const float2 ac = f2_unpack(x[r + H]);
                     const unsigned short fl = (unsigned short)((ac.x >= athr ? 1u : 0u) | (ac.y >= athr ? 0x100u : 0u));
-                    *reinterpret_cast<unsigned short*>(aflag + (ro0 + r) * N + 2 * cp) = fl;
+                    if (chk((ro0 + r) * N + 2 * cp + 1 < RN * N, status))
+                        *reinterpret_cast<unsigned short*>(aflag + (ro0 + r) * N + 2 * cp) = fl;
                 }
                 uint64_t v1[VB], v2[VB], vg[VB];
                 split_box<H, VB>([&](int q) { return x[q]; }, v1);
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(NCC_THREADS, 2) k_detect(const float* __restri
                         }
                     if (pk) {
                         const int p = (ro - 1) * N + l;
-                        atomicOr(&bits[p >> 5], 1u << (p & 31));
+                        if (chk(p >= 0 && (p >> 5) < NW && ro + 1 < RN, status)) atomicOr(&bits[p >> 5], 1u << (p & 31));
                     }
                 }
             }
@@ -667,7 +670,8 @@ __global__ void k_gather(const ulm_loc2d* __restrict__ cand, const int* __restri
         int dst = off[s] + r;
         if (dst < cap) {
             ulm_loc2d e = cand[(size_t)s * CAND_CAP + r];
-            if (A) e.amp = __ldg(A + (((size_t)(e.frame * 2 + e.axis) * S + e.slab) * nz + e.iz) * N + e.ilat);
+            if (A && chk(e.iz >= 0 && e.iz < nz && e.ilat >= 0 && e.ilat < N && e.slab >= 0 && e.slab < S, status))
+                e.amp = __ldg(A + (((size_t)(e.frame * 2 + e.axis) * S + e.slab) * nz + e.iz) * N + e.ilat);
             out[dst] = e;
         } else {
             atomicOr(status, ST_CAPACITY);

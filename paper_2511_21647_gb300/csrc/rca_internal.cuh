@@ -341,7 +341,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 
 // Checked build (compiled with -DRCA_CHECKED, library librca_checked.so):
-// index checks on shared-memory ring slots, staged rows and queue indexes
+// index checks on shared-memory ring slots, staged rows, detection strip
+// rows, flag and candidate-bitmap indexes, gathered pixels and queue indexes
 // that record ST_BOUNDS in the status word and skip the access instead of
 // trapping.  In the release build chk() is constant true and compiles away.
 #ifdef RCA_CHECKED

@@ -1,7 +1,8 @@
 """The bounds-checked build (librca_checked.so, compiled with -DRCA_CHECKED):
 its kernels check every shared-memory ring slot and record block of Stage 1,
-every staged window row of Stage 2 and every queue segment and counter index
-of the persistent batched launch, and record RCA_ERR_BOUNDS in the status
+every staged window row of Stage 2, the strip rows, flag and bitmap indexes
+of the NCC detection and the pixels its gather reads, and every queue segment
+and counter index of the persistent batched launch, and record RCA_ERR_BOUNDS in the status
 word instead of trapping.  On the tiny ensemble (one-call beamformer with
 the paired and unpaired Stage-1 kernels at 32, 64 and 128 elements,
 localisation) and on a batch of
