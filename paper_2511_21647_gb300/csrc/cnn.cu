@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
     constexpr unsigned TMEM_COLS = 64;                  // two 32-column accumulators
     extern __shared__ __align__(16) unsigned char smtc[];
     unsigned char* sB = smtc;                           // [9][KC][NG][8][8] bf16
-    unsigned char* sA = smtc + 9 * TAPB;                // [2][KC][18][10][8] bf16
+    unsigned char* sA = smtc + 9 * TAPB;                // [3][KC][18][10][8] bf16
     __shared__ uint64_t bars[2];
     __shared__ unsigned s_tmem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -240,26 +240,37 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
         i0 = (tij / tiles_j) * CONV_TH;
         j0 = (tij % tiles_j) * CONV_TW;
     };
-    // halo tile of `tile` into buffer `buf`: 8-channel chunk kc of pixel (row yr, column xg)
+    // halo tile of `tile` into buffer `buf` by 16-byte cp.async copies (zero-filled
+    // outside the plane), one commit group per call (empty when tile >= ntiles):
+    // 8-channel chunk kc of pixel (row yr, column xg)
     auto load = [&](int tile, int buf) {
-        int b, i0, j0;
-        coords(tile, b, i0, j0);
-        unsigned char* dst = sA + buf * ABYTES;
-        for (int q = threadIdx.x; q < TC_HALO_R * TC_HALO_C * KC; q += blockDim.x) {
-            const int kc = q % KC, p = q / KC, xg = p % TC_HALO_C, yr = p / TC_HALO_C;
-            const int ii = i0 - 1 + yr, jj = j0 - 1 + xg;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (ii >= 0 && ii < H && jj >= 0 && jj < W)
-                v = reinterpret_cast<const uint4*>(x + (((size_t)b * H + ii) * W + jj) * CIN)[kc];
-            *reinterpret_cast<uint4*>(dst + (kc * TC_HALO_C + xg) * TC_CM_BYTES + yr * 16) = v;
+        if (tile < ntiles) {
+            int b, i0, j0;
+            coords(tile, b, i0, j0);
+            const unsigned dst = sAa + (unsigned)(buf * ABYTES);
+            for (int q = threadIdx.x; q < TC_HALO_R * TC_HALO_C * KC; q += blockDim.x) {
+                const int kc = q % KC, p = q / KC, xg = p % TC_HALO_C, yr = p / TC_HALO_C;
+                const int ii = i0 - 1 + yr, jj = j0 - 1 + xg;
+                const bool in = ii >= 0 && ii < H && jj >= 0 && jj < W;
+                const void* src = in ? (const void*)(x + (((size_t)b * H + ii) * W + jj) * CIN + kc * 8) : (const void*)x;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                                 dst + (unsigned)((kc * TC_HALO_C + xg) * TC_CM_BYTES + yr * 16)),
+                             "l"(src), "r"(in ? 16u : 0u)
+                             : "memory");
+            }
         }
-        // generic-proxy writes of the tile before the tensor cores read it
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // this thread's copies of every group but the newest are done; then the
+    // generic-proxy writes are ordered before the tensor cores read the tile
+    auto wait_older = [&]() {
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         fence_proxy_async();
     };
-    // the 9 x CIN / 16 MMAs of buffer `buf` into accumulator `buf` (one thread)
-    auto issue = [&](int buf) {
+    // the 9 x CIN / 16 MMAs of halo buffer `ab` into accumulator `buf` (one thread)
+    auto issue = [&](int ab, int buf) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned aB = sAa + buf * ABYTES, dcol = tmem + (unsigned)(32 * buf);
+        const unsigned aB = sAa + ab * ABYTES, dcol = tmem + (unsigned)(32 * buf);
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int dy = t / 3, dx = t % 3;
@@ -275,23 +286,28 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
                          smem_u32(&bars[buf]))
                      : "memory");
     };
-    // software pipeline: the load and MMAs of tile k + 1 run while tile k's epilogue drains
+    // software pipeline over three halo buffers and two accumulators: the copies
+    // of tile k + 2 and the MMAs of tile k + 1 run while tile k's epilogue drains
     unsigned phase = 0;   // bit b: parity of the next completion of bars[b]
     bool ok = true;
     int tile = blockIdx.x;
+    load(tile, 0);
+    load(tile + gridDim.x, 1);
     if (tile < ntiles) {
-        load(tile, 0);
+        wait_older();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (threadIdx.x == 0) issue(0);
+        if (threadIdx.x == 0) issue(0, 0);
     }
     for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
         const int cur = k & 1, nxt = cur ^ 1;
         const int ntile = tile + gridDim.x;
-        if (ntile < ntiles) load(ntile, nxt);
+        // buffer (k + 2) mod 3 held tile k - 1, whose MMAs completed before its epilogue
+        load(ntile + gridDim.x, (k + 2) % 3);
+        wait_older();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (ntile < ntiles && threadIdx.x == 0) issue(nxt);
+        if (ntile < ntiles && threadIdx.x == 0) issue((k + 1) % 3, nxt);
         // bounded wait for tile k's accumulators
         if (!mbar_wait_bounded(&bars[cur], (phase >> cur) & 1u)) ok = false;
         if (__syncthreads_or(!ok)) {
@@ -299,6 +315,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
             // the MMAs in flight finish (bounded) before the accumulators are freed
             mbar_wait_bounded(&bars[cur], (phase >> cur) & 1u);
             if (ntile < ntiles) mbar_wait_bounded(&bars[nxt], (phase >> nxt) & 1u);
+            asm volatile("cp.async.wait_all;" ::: "memory");
             break;
         }
         phase ^= 1u << cur;
@@ -351,6 +368,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_inval(&bars[0]);
@@ -650,8 +668,8 @@ template <int CIN, int COUT, int MODE>
 static rca_status conv_launch(ulm_cnn* c, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
                               const __nv_bfloat16* mask, int B, int H, int W, void* out)
 {
-    // weights of the nine taps + two halo tiles
-    constexpr size_t smem = (size_t)9 * CIN * COUT * 2 + (size_t)2 * (CIN / 8) * TC_HALO_C * TC_CM_BYTES;
+    // weights of the nine taps + three halo tiles
+    constexpr size_t smem = (size_t)9 * CIN * COUT * 2 + (size_t)3 * (CIN / 8) * TC_HALO_C * TC_CM_BYTES;
     static_assert(smem <= 100 * 1024, "conv tile exceeds its shared-memory budget");
     auto kern = k_conv_tc<CIN, COUT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
