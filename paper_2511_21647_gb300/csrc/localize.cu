@@ -449,7 +449,6 @@ __global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ ma
 {
     extern __shared__ __align__(128) float smf[];
     __shared__ int wsum[32];
-    __shared__ int base_count;
     __shared__ uint64_t bar;
     const int H4 = nz * up, W4 = N * up;
     const int strip = blockIdx.x, plane = blockIdx.y, nstrip = gridDim.x;
@@ -481,14 +480,19 @@ __global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ ma
     ulm_loc2d* slot = cand + ((size_t)plane * nstrip + strip) * CAND_CAP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npx = DET_RS * W4;
-    const int per = (npx + blockDim.x - 1) / blockDim.x;
-    const int p0 = threadIdx.x * per, p1 = min(npx, p0 + per);
-    auto is_peak = [&](int p, float& c) {
-        const int ro = 1 + p / W4, j = p % W4;
+    const int nwords = (npx + 31) / 32;
+    // candidate bitmap of the strip's pixels in raster order (cleared, then set by
+    // the test: consecutive lanes take consecutive pixels, conflict-free on the rows)
+    unsigned* bits = reinterpret_cast<unsigned*>(smf + (size_t)rin * W4);
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    for (int p = threadIdx.x; p < npx; p += blockDim.x) {
+        const int ro = 1 + p / W4, j = p - (ro - 1) * W4;
         const int i = i0 - 1 + ro;
-        if (i < 1 || i >= H4 - 1 || j < 1 || j >= W4 - 1) return false;
-        c = smf[ro * W4 + j];
-        if (!(c >= score_min) || !(Ap[(size_t)(i / up) * N + j / up] >= athr)) return false;
+        if (i < 1 || i >= H4 - 1 || j < 1 || j >= W4 - 1) continue;
+        const float c = smf[ro * W4 + j];
+        if (!(c >= score_min)) continue;
+        bool pk = true;
 #pragma unroll
         for (int a = -1; a <= 1; ++a)
 #pragma unroll
@@ -496,15 +500,17 @@ __global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ ma
                 if (a == 0 && bb == 0) continue;
                 const float q = smf[(ro + a) * W4 + j + bb];
                 const bool earlier = (a < 0) || (a == 0 && bb < 0);
-                if (earlier ? !(c > q) : !(c >= q)) return false;
+                pk = pk && (earlier ? (c > q) : (c >= q));
             }
-        return true;
-    };
-    int mine = 0;
-    for (int p = p0; p < p1; ++p) {
-        float c;
-        mine += is_peak(p, c) ? 1 : 0;
+        // the amplitude (global memory) only for regional maxima
+        if (pk && Ap[(size_t)(i / up) * N + j / up] >= athr) atomicOr(&bits[p >> 5], 1u << (p & 31));
     }
+    __syncthreads();
+    // compaction: consecutive bitmap words per thread, a block-wide exclusive scan of their counts
+    const int wpt = (nwords + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * wpt, w1 = min(nwords, w0 + wpt);
+    int mine = 0;
+    for (int w = w0; w < w1; ++w) mine += __popc(bits[w]);
     int x = mine;
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -514,13 +520,16 @@ __global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ ma
     __syncthreads();
     int before = x - mine;
     for (int w = 0; w < warp; ++w) before += wsum[w];
-    if (mine) {
-        const float half = 0.5f * (float)(up - 1), inv = 1.f / (float)up;
-        for (int p = p0; p < p1; ++p) {
-            float c;
-            if (!is_peak(p, c)) continue;
+    const float half = 0.5f * (float)(up - 1), inv = 1.f / (float)up;
+    for (int w = w0; w < w1; ++w) {
+        unsigned m = bits[w];
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
             if (before < CAND_CAP) {
-                const int ro = 1 + p / W4, j = p % W4, i = i0 - 1 + ro;
+                const int p = w * 32 + bit;
+                const int ro = 1 + p / W4, j = p - (ro - 1) * W4, i = i0 - 1 + ro;
+                const float c = smf[ro * W4 + j];
                 auto para = [](float fm, float f0, float fp) {
                     const float den = fm - 2.f * f0 + fp;
                     if (den >= 0.f) return 0.f;
@@ -543,11 +552,10 @@ __global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ ma
             ++before;
         }
     }
-    if (threadIdx.x == blockDim.x - 1) base_count = before;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cnt[(size_t)plane * nstrip + strip] = base_count;
-        if (base_count > CAND_CAP) atomicOr(status, ST_CAPACITY);
+    // the last thread's running index is the strip's count
+    if (threadIdx.x == blockDim.x - 1) {
+        cnt[(size_t)plane * nstrip + strip] = before;
+        if (before > CAND_CAP) atomicOr(status, ST_CAPACITY);
     }
 }
 
@@ -1072,7 +1080,8 @@ rca_status launch_detect_map(rca_handle* h, const rca_tables* t, const float* ma
     if (!off) return st;
     long long* part = (long long*)ws_get(h, WS_N2D, (size_t)2 * 1024 * sizeof(long long), &st);
     if (!part) return st;
-    const size_t smem = (size_t)(DET_RS + 2) * W4 * sizeof(float);
+    // the strip's rows plus the candidate bitmap of its pixels
+    const size_t smem = (size_t)(DET_RS + 2) * W4 * sizeof(float) + (size_t)((DET_RS * W4 + 31) / 32) * sizeof(unsigned);
     if (smem > 200 * 1024) return set_error(h, RCA_ERR_UNSUPPORTED, "map rows of %d fine pixels exceed shared memory", W4);
     cudaError_t e = cudaFuncSetAttribute(k_detect_map, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "detect_map smem attribute");
