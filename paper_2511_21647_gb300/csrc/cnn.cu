@@ -104,8 +104,10 @@ __global__ void k_conv1_fwd(const float* __restrict__ x, const float* __restrict
         const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
         v[t] = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? x[((size_t)b * H + ii) * W + jj] : 0.f;
     }
-    unsigned* out = reinterpret_cast<unsigned*>(y + p * CNN_C);
-#pragma unroll 4
+    // all CNN_C outputs in registers, written as 16-byte vectors (the pixel's
+    // 2 CNN_C bytes in CNN_C / 8 stores instead of CNN_C / 2)
+    unsigned pk[CNN_C / 2];
+#pragma unroll
     for (int o = 0; o < CNN_C; o += 2) {
         float a0 = sb[o], a1 = sb[o + 1];
 #pragma unroll
@@ -113,8 +115,11 @@ __global__ void k_conv1_fwd(const float* __restrict__ x, const float* __restrict
             a0 = fmaf(sw[o * 9 + t], v[t], a0);
             a1 = fmaf(sw[(o + 1) * 9 + t], v[t], a1);
         }
-        out[o / 2] = pack_bf2(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
+        pk[o / 2] = pack_bf2(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
     }
+    uint4* out = reinterpret_cast<uint4*>(y + p * CNN_C);
+#pragma unroll
+    for (int q = 0; q < CNN_C / 8; ++q) out[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
 }
 
 // ---------------------------------------------------------------------------
