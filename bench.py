@@ -1008,7 +1008,8 @@ def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):
     l3 = torch.zeros((cap, 10), dtype=torch.int32, device=dev)
     n2 = torch.zeros(1, dtype=torch.int32, device=dev)
     n3 = torch.zeros(1, dtype=torch.int32, device=dev)
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    split = {"peaks_ms": 0.0, "pair_ms": 0.0, "n2d": 0}
 
     def infer(timing):
         cnn_ms = 0.0
@@ -1019,11 +1020,15 @@ def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):
             R.ulm_cnn_forward(c, a, m, 2 * S, P, g.nz, g.n_el, heat)
             e[1].record(stream)
             R.ulm_detect_map(h, sess.t, heat, 4, a, m, fc, 0.3, 0.1, l2, cap, n2)
-            R.ulm_pair3d(h, sess.t, l2, n2, cap, fc, l3, cap, n3)
             e[2].record(stream)
+            R.ulm_pair3d(h, sess.t, l2, n2, cap, fc, l3, cap, n3)
+            e[3].record(stream)
             if timing:
                 torch.cuda.synchronize()
                 cnn_ms += e[0].elapsed_time(e[1])
+                split["peaks_ms"] += e[1].elapsed_time(e[2])
+                split["pair_ms"] += e[2].elapsed_time(e[3])
+                split["n2d"] += int(n2.item())
         return cnn_ms
 
     infer(False)
@@ -1052,6 +1057,9 @@ def learned_form(R, L, sess, planes, F, g, dev, stream, peaks):
             "train_steps": steps, "batch": 64, "loss_first_last": [hist[0][1], hist[-1][1]],
             "dataset_s": round(build_s, 1), "train_s": round(train_s, 1), "eval_tiny": ev,
             "paper_frames": frames, "localise_ms_per_300_frames": round(total_ms * 300 / frames, 3),
+            "heatmap_peaks_ms_per_300_frames": round(split["peaks_ms"] * 300 / frames, 3),
+            "pairing_ms_per_300_frames": round(split["pair_ms"] * 300 / frames, 3),
+            "n2d_per_300_frames": int(split["n2d"] * 300 / frames),
             "cnn_ms_per_300_frames": round(cnn_ms * 300 / frames, 3),
             "cnn_roofline": {"bound": "hbm", "achieved": round(cnn_gbs, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(cnn_gbs / hbm, 4), "bytes_per_pixel": 460,

@@ -486,24 +486,28 @@ __global__ void __launch_bounds__(256) k_detect_map(const float* __restrict__ ma
     unsigned* bits = reinterpret_cast<unsigned*>(smf + (size_t)rin * W4);
     for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0u;
     __syncthreads();
-    for (int p = threadIdx.x; p < npx; p += blockDim.x) {
-        const int ro = 1 + p / W4, j = p - (ro - 1) * W4;
-        const int i = i0 - 1 + ro;
-        if (i < 1 || i >= H4 - 1 || j < 1 || j >= W4 - 1) continue;
-        const float c = smf[ro * W4 + j];
-        if (!(c >= score_min)) continue;
-        bool pk = true;
+    // rows in turn, consecutive lanes on consecutive columns (no division per pixel)
+    const int ro_lo = max(1, 2 - i0), ro_hi = min(DET_RS, H4 - 1 - i0);   // rows with 1 <= i <= H4 - 2
+    for (int ro = ro_lo; ro <= ro_hi; ++ro) {
+#pragma unroll 2
+        for (int j = threadIdx.x; j < W4; j += blockDim.x) {
+            const int i = i0 - 1 + ro, p = (ro - 1) * W4 + j;
+            if (j < 1 || j >= W4 - 1) continue;
+            const float c = smf[ro * W4 + j];
+            if (!(c >= score_min)) continue;
+            bool pk = true;
 #pragma unroll
-        for (int a = -1; a <= 1; ++a)
+            for (int a = -1; a <= 1; ++a)
 #pragma unroll
-            for (int bb = -1; bb <= 1; ++bb) {
-                if (a == 0 && bb == 0) continue;
-                const float q = smf[(ro + a) * W4 + j + bb];
-                const bool earlier = (a < 0) || (a == 0 && bb < 0);
-                pk = pk && (earlier ? (c > q) : (c >= q));
-            }
-        // the amplitude (global memory) only for regional maxima
-        if (pk && Ap[(size_t)(i / up) * N + j / up] >= athr) atomicOr(&bits[p >> 5], 1u << (p & 31));
+                for (int bb = -1; bb <= 1; ++bb) {
+                    if (a == 0 && bb == 0) continue;
+                    const float q = smf[(ro + a) * W4 + j + bb];
+                    const bool earlier = (a < 0) || (a == 0 && bb < 0);
+                    pk = pk && (earlier ? (c > q) : (c >= q));
+                }
+            // the amplitude (global memory) only for regional maxima
+            if (pk && Ap[(size_t)(i / up) * N + j / up] >= athr) atomicOr(&bits[p >> 5], 1u << (p & 31));
+        }
     }
     __syncthreads();
     // compaction: consecutive bitmap words per thread, a block-wide exclusive scan of their counts
