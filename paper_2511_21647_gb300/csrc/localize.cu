@@ -730,7 +730,9 @@ __global__ void k_list_plane_offsets(const ulm_loc2d* __restrict__ L, const int*
 __device__ __forceinline__ bool pair_ok(const ulm_loc2d& x, const ulm_loc2d& y, int P, double* cost)
 {
     if (x.frame != y.frame) return false;
-    if (x.ilat / P != y.slab || y.ilat / P != x.slab) return false;
+    // x.ilat / P == y.slab and y.ilat / P == x.slab (non-negative indexes), without divisions
+    const int xl = y.slab * P, yl = x.slab * P;
+    if (x.ilat < xl || x.ilat >= xl + P || y.ilat < yl || y.ilat >= yl + P) return false;
     const float dz = fabsf(x.z - y.z);
     if (dz > 1.0f) return false;
     if (dz == 1.0f && fabs((double)x.z - (double)y.z) > 1.0) return false;
