@@ -299,7 +299,14 @@ def synth_rf(g: RcaGeometry, pos: torch.Tensor, amp: torch.Tensor, *,
         ok = (tt.abs() <= half) & (n >= 0) & (n <= ns - 1)
         val = torch.where(ok, val * a[:, None, None, :, None], torch.zeros((), device=dev, dtype=dt))
         idx = base[..., None, None] + torch.where(ok, n, torch.zeros((), device=dev, dtype=dt)).long()
-        rf.index_add_(0, idx.reshape(-1), val.reshape(-1))
+        if dev.type == "cuda":
+            # one scatterer per call: its windows never share a sample (entries outside
+            # a window add zero), so the atomic adds of a call do not collide and the
+            # sum does not depend on their order -- the same RF on every run
+            for q in range(idx.shape[3]):
+                rf.index_add_(0, idx[:, :, :, q].reshape(-1), val[:, :, :, q].reshape(-1))
+        else:
+            rf.index_add_(0, idx.reshape(-1), val.reshape(-1))
     return rf.view(F, nt, E, ns)
 
 
@@ -318,7 +325,9 @@ def generate(w: RcaWorkload, device: str = "cpu", dtype=torch.float64,
     g = w.geom
     fields = scatterer_fields(w)
     F = w.n_frames
-    fb = frame_batch or 1
+    # frames per synthesis call: on the GPU 32 by default (the per-scatterer
+    # accumulation there issues one call per scatterer and batch)
+    fb = frame_batch or (32 if str(device).startswith("cuda") else 1)
     out = torch.empty((F, g.n_tx, g.n_el, g.ns), dtype=torch.float32, device=device)
     ss_mb = 0.0
     for f0 in range(0, F, fb):
